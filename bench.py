@@ -1,0 +1,407 @@
+"""Benchmark of the SMC-sampler hot path on GB300.
+
+Default workload (one JSON line): one SMC iteration per step -- move, reweight,
+LSE/N_eff, estimate, systematic resampling and redistribute (Algorithm 2,
+lines 3-10) -- at the resample+redistribute microbenchmark's largest size:
+N = 2^24 particles of D = 16 FP32 coordinates, Gaussian target, resampling at
+every iteration (the worst case of Sec. 5.2).  value = particle-iterations/s.
+The line also carries the redistribute stage's GB/s against the measured HBM
+peak, the roofline of the dominant kernel, an end-to-end figure through the
+C-ABI with host buffers, and the CPU oracle's rate on a bounded sample.
+
+--workload redistribute prints one line per case of the resample+redistribute
+microbenchmark (N in {2^16, 2^20, 2^24}, s in {0.5, 2, 8}, one-hot).
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+Multi-GPU (torchrun): independent replicas, one sampler per GPU, no collective
+on the data path; value = all ranks' particle-iterations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-iters/s"
+STAGES = ["move_reweight", "max_mean_finalize", "quantise_reduce", "quantise_finalize", "systematic_scan",
+          "redistribute", "commit"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="iteration", choices=["iteration", "redistribute"])
+    p.add_argument("--n", type=int, default=1 << 24)
+    p.add_argument("--d", type=int, default=16)
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- environment
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples with host timestamps."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        inside = [p for (t, p) in self.samples if t0 <= t <= t1]
+        note = "samples inside the timed region"
+        if not inside and self.samples:
+            # timed region shorter than the sampling period: nearest samples
+            mid = 0.5 * (t0 + t1)
+            inside = [min(self.samples, key=lambda s: abs(s[0] - mid))[1]]
+            note = "nearest sample (timed region shorter than the 100 ms sampling period)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "note": "nvidia-smi unavailable"}
+        sm = [float(p[1]) for p in inside if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for p in inside if p[2].replace(".", "").isdigit()]
+        reasons = sorted({names[j] for p in inside for j in range(4) if p[4 + j].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside), "note": note}
+
+
+# ----------------------------------------------------------------- CPU baseline (oracle)
+def oracle_iteration_rate(n_sample: int, iters: int, d: int, seed: int = 0):
+    """The FP64 oracle's Algorithm 2 iteration (move, reweight, LSE/N_eff,
+    estimate, resample, redistribute, reset) on n_sample particles."""
+    from oracle import oracle as O
+    from paper_1905_10252_gb300 import inputs
+
+    mu, Sigma = inputs.gaussian_target(d, seed=16)
+    tgt = O.Target.gauss(mu, Sigma)
+    x, lw, lp = O.init(tgt, n_sample, seed, 2.0, ubits=24)
+    t0 = time.perf_counter()
+    for t in range(1, iters + 1):
+        x1 = O.move(x, seed, t, 0.5, ubits=24)
+        lw, lp = O.reweight(tgt, x, x1, lp, lw, 0.5)
+        m, lse, ess = O.lse_ess(lw)
+        O.estimate(x1, lw, lse, with_cov=False)
+        r = O.resample(lw, seed, t, O.RESAMPLE_ALWAYS)
+        x = O.redistribute(r["ncopies"], x1)
+        lp = O.redistribute(r["ncopies"], lp)
+        lw = np.full(n_sample, O.reset_logw(n_sample))
+    dt = time.perf_counter() - t0
+    return n_sample * iters / dt, dt
+
+
+def cpu_baseline(d: int):
+    n_sample, iters = 1 << 20, 6
+    rate, dt = oracle_iteration_rate(n_sample, iters, d)
+    return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} iterations of N={n_sample} (D={d}, FP64, single thread), {dt:.1f} s",
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return
+    d = args.d
+    # each step is one oracle iteration on a sample sized so that warmup+steps
+    # take about a minute in all
+    per = 1.6e-6
+    n_sample = int(max(1024, min(1 << 18, 60.0 / max(1, args.steps + args.warmup) / per)))
+    from oracle import oracle as O
+    from paper_1905_10252_gb300 import inputs
+
+    mu, Sigma = inputs.gaussian_target(d, seed=16)
+    tgt = O.Target.gauss(mu, Sigma)
+    x, lw, lp = O.init(tgt, n_sample, 0, 2.0, ubits=24)
+    times = []
+    for t in range(1, args.warmup + args.steps + 1):
+        t0 = time.perf_counter()
+        x1 = O.move(x, 0, t, 0.5, ubits=24)
+        lw, lp = O.reweight(tgt, x, x1, lp, lw, 0.5)
+        m, lse, ess = O.lse_ess(lw)
+        O.estimate(x1, lw, lse, with_cov=False)
+        r = O.resample(lw, 0, t, O.RESAMPLE_ALWAYS)
+        x = O.redistribute(r["ncopies"], x1)
+        lp = O.redistribute(r["ncopies"], lp)
+        lw = np.full(n_sample, O.reset_logw(n_sample))
+        if t > args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n_sample * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"smc-iteration gauss N=2^24 (sampled: N={n_sample}) D={d} resample-every-iteration"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": f"N={n_sample} particles per step, FP64 oracle, single thread"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def algorithmic_bytes(n: int, d: int, esize: int, survivors: float):
+    """Per-launch algorithmic bytes of each stage (see the measurement section
+    of the design notes): reads + writes the definition of the stage needs."""
+    row = d * esize
+    return {
+        # read x, log pi, log w; write x, log pi, log w
+        "move_reweight": n * (2 * row + 2 * esize + 2 * 8),
+        # read log w
+        "quantise_reduce": n * 8,
+        # read log w, write the exclusive offsets (the ncopies information)
+        "systematic_scan": n * (8 + 4),
+        # read ncopies (as offsets), the distinct surviving rows + log pi, write
+        # N rows + log pi, reset N log-weights
+        "redistribute": n * 4 + survivors * (row + esize) + n * (row + esize) + n * 8,
+    }
+
+
+def run_iteration(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    from paper_1905_10252_gb300 import build as B
+
+    B.build()
+    from paper_1905_10252_gb300 import inputs, native
+
+    n, d = args.n, args.d
+    mu, Sigma = inputs.gaussian_target(d, seed=16)
+    S = native.Sampler(n, d, dtype=torch.float32, seed=rank, mu=mu, sigma=Sigma, step=0.5, init_scale=2.0,
+                       resample_mode=native.RESAMPLE_ALWAYS)
+    stream = S.stream
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        S.step_profile()
+    torch.cuda.synchronize()
+    n_prof = min(K, 400)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(n_prof)]
+    for row in ev:
+        for e in row:
+            e.record(stream)  # creates the event
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_host0 = time.time()
+    start.record(stream)
+    for k in range(K):
+        S.step_profile(ev[k] if k < n_prof else None)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    t_host1 = time.time()
+    if ws > 1:
+        dist.barrier()
+    time.sleep(0.15)
+    clocks.stop()
+    total_ms = start.elapsed_time(stop)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    per_stage = {name: [] for name in STAGES}
+    for row in ev:
+        for j, name in enumerate(STAGES):
+            per_stage[name].append(row[j].elapsed_time(row[j + 1]))
+    stage_ms = {k: float(np.mean(v)) for k, v in per_stage.items()}
+    st = S.stats()
+    survivors = float(st["survivors"])
+    byt = algorithmic_bytes(n, d, 4, survivors)
+    peak, peak_kind = peaks()
+    dominant = max(stage_ms, key=stage_ms.get)
+
+    def roof(name):
+        if name not in byt:
+            return None
+        gbs = byt[name] / (stage_ms[name] * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": int(byt[name]), "ms_per_launch": round(stage_ms[name], 5)}
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # particle state, one iteration, D2H of the estimate and its statistics
+    e2e = None
+    if args.e2e_steps > 0:
+        x_h = S.current()[0].cpu().pin_memory()
+        lp_h = S.current()[1].cpu().pin_memory()
+        lw_h = S.logw.cpu().pin_memory()
+        mean_d = torch.empty(d, dtype=torch.float64, device="cuda")
+        mean_h = torch.empty(d, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cur = S.current()
+        which = 0 if cur[0].data_ptr() == S.x.data_ptr() else 1
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            xs, lps = (S.x, S.logpi) if which == 0 else (S.x_alt, S.logpi_alt)
+            with torch.cuda.stream(stream):
+                xs.copy_(x_h, non_blocking=True)
+                lps.copy_(lp_h, non_blocking=True)
+                S.logw.copy_(lw_h, non_blocking=True)
+            S.step_profile(mean=mean_d)
+            with torch.cuda.stream(stream):
+                mean_h.copy_(mean_d, non_blocking=True)
+            which ^= 1  # resampling at every iteration swaps the buffers
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        e2e = {"value": n * args.e2e_steps / (e_ms * 1e-3), "unit": METRIC,
+               "h2d_bytes_per_step": int(x_h.nbytes + lp_h.nbytes + lw_h.nbytes),
+               "d2h_bytes_per_step": int(mean_h.nbytes), "ms_per_step": e_ms / args.e2e_steps}
+    S.sync()
+    value = n * K * ws / (total_ms * 1e-3)
+    launches_per_step = 8
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 state / f64 weights / u64 fixed-point CDF", "data": "synthetic",
+            "config": {"workload": f"smc-iteration gauss N=2^{int(np.log2(n))} D={d} fp32 resample-every-iteration",
+                       "n": n, "d": d, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (particle state %.2f GB per buffer)" % (n * d * 4 / 1e9)},
+            "roofline": roof(dominant) if dominant in byt else roof("move_reweight"),
+            "dominant_kernel": dominant,
+            "redistribute": roof("redistribute"),
+            "stages_ms": {k: round(v, 5) for k, v in stage_ms.items()},
+            "stage_roofline": {k: roof(k) for k in byt},
+            "survivors_last_iteration": int(survivors),
+            "gpu_launches": launches_per_step * K,
+            "clocks": clocks.summary(t_host0, t_host1),
+            "e2e": e2e,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(d)
+        print(json.dumps(line), flush=True)
+    S.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_redistribute(args):
+    """Resample + redistribute microbenchmark: i.i.d. N(0, s^2) log-weights or
+    one-hot; resampling then redistribute of D=16 FP32 rows."""
+    import torch
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1905_10252_gb300 import build as B
+
+    B.build()
+    from paper_1905_10252_gb300 import inputs, native
+
+    peak, peak_kind = peaks()
+    d = args.d
+    for n in (1 << 16, 1 << 20, 1 << 24):
+        x = torch.as_tensor(inputs.particles(n, d, seed=1), device="cuda")
+        out = torch.empty_like(x)
+        wsb = torch.empty(native.smc_redistribute_ws_bytes(n), dtype=torch.uint8, device="cuda")
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        for case in ("s0.5", "s2", "s8", "onehot"):
+            lw = inputs.one_hot_log_weights(n, 0) if case == "onehot" else inputs.log_weights(n, float(case[1:]), 0)
+            lwd = torch.as_tensor(lw, device="cuda")
+            nc = torch.empty(n, dtype=torch.int32, device="cuda")
+            res_ms, red_ms = [], []
+            for it in range(args.warmup + 20):
+                flush.zero_()  # L2 flush between iterations
+                a, b, c = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                a.record()
+                native.smc_resample_raw(lwd, 0, it + 1, native.RESAMPLE_ALWAYS, ncopies=nc, ws=wsb)
+                b.record()
+                flush.zero_()
+                b2 = torch.cuda.Event(enable_timing=True)
+                b2.record()
+                native.smc_redistribute_raw(nc, x, out, ws=wsb)
+                c.record()
+                torch.cuda.synchronize()
+                if it >= args.warmup:
+                    res_ms.append(a.elapsed_time(b))
+                    red_ms.append(b2.elapsed_time(c))
+            nnz = int((nc > 0).sum().item())
+            red_bytes = 4 * n + 64 * nnz + 64 * n
+            res_bytes = 8 * n + 8 * n + 4 * n
+            rm, dm = statistics.median(res_ms), statistics.median(red_ms)
+            line = {"metric": "redistribute GB/s", "workload": f"resample+redistribute N=2^{int(np.log2(n))} {case}",
+                    "n": n, "d": d, "survivors": nnz, "resample_ms": rm, "redistribute_ms": dm,
+                    "redistribute_gbs": red_bytes / (dm * 1e-3) / 1e9, "resample_gbs": res_bytes / (rm * 1e-3) / 1e9,
+                    "peak_gbs": peak, "peak_kind": peak_kind,
+                    "redistribute_frac": red_bytes / (dm * 1e-3) / 1e9 / peak, "timing": "median of 20, L2 flushed"}
+            if rank == 0:
+                print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.workload == "redistribute":
+        run_redistribute(args)
+    else:
+        run_iteration(args)
+
+
+if __name__ == "__main__":
+    main()

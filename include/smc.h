@@ -1,0 +1,201 @@
+/*
+ * smc.h -- C-ABI of libsmc.so, the GB300 (sm_103a) hot path of one iteration of
+ * the SMC sampler with recycling of Varsi, Kekempanos, Thiyagalingam & Maskell,
+ * "A Single SMC Sampler on MPI that Outperforms a Single MCMC Sampler"
+ * (arXiv:1905.10252).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named *_dev are DEVICE pointers on the current CUDA device; the
+ *    caller allocates and frees them (the library never allocates device
+ *    memory).  Host pointers are named *_host.
+ *  - Particles are row-major N x D arrays of float (SMC_F32) or double
+ *    (SMC_F64); row i is particle x^i (the paper's x_t in R^{N x M}, Sec. 3.1,
+ *    with the paper's state dimension M called D here).  Log-weights are
+ *    double[N]; the cached log-target log pi(x^i) has the particle dtype.
+ *  - Every call only enqueues work on the sampler's stream (or the stream
+ *    argument) and returns; results land in device memory.  A call returns
+ *    SMC_OK when its launches were accepted.  Errors found on the device
+ *    (non-finite weights, an invalid copy-count vector, a bounded wait that
+ *    gave up) are recorded in an error word and returned by the next
+ *    smc_sync() / smc_ws_status().
+ *  - Sizes: 1 <= N < 2^31, 1 <= D <= 32.
+ *  - Not thread-safe per handle; distinct handles are independent.
+ */
+#ifndef SMC_H_
+#define SMC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (identical type); NULL is the legacy default stream. */
+typedef struct CUstream_st* smc_stream_t;
+
+typedef enum {
+  SMC_OK = 0,
+  SMC_EINVAL = 1,      /* bad argument: size, dtype, null pointer, ncopies not summing to N */
+  SMC_ENOMEM = 2,      /* workspace too small / admission refused */
+  SMC_ECUDA = 3,       /* a CUDA runtime call failed (message in smc_last_error) */
+  SMC_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+  SMC_ENONFINITE = 5   /* a log-weight is NaN, or every log-weight is -inf */
+} smc_status;
+
+typedef enum { SMC_F32 = 1, SMC_F64 = 2 } smc_dtype;
+
+/* Targets pi(x) of the static SMC sampler (Sec. 3.1.2), normalising
+ * constants dropped:
+ *  SMC_GAUSS      log pi = -1/2 (x-mu)^T Sigma^-1 (x-mu)
+ *  SMC_LOGISTIC   log pi = sum_m [y_m z_m - softplus(z_m)] - |x|^2/(2 prior_var),
+ *                 z = X x (Bayesian logistic regression, M data rows)
+ *  SMC_STUDENT_T  log pi = -(nu+1)/2 log(1 + (x-mu)^2/nu), D = 1 (Sec. 5.2.3, eq. (14)) */
+typedef enum { SMC_GAUSS = 1, SMC_LOGISTIC = 2, SMC_STUDENT_T = 3 } smc_target_kind;
+
+/* When to resample (Sec. 3.1): SMC_RESAMPLE_ESS resamples iff N_eff < N/2,
+ * decided exactly on the quantised weights (2 S^2 < N sum W^2);
+ * SMC_RESAMPLE_ALWAYS is the worst case of Sec. 5.2 (every iteration). */
+typedef enum { SMC_RESAMPLE_ESS = 0, SMC_RESAMPLE_ALWAYS = 1, SMC_RESAMPLE_NEVER = 2 } smc_resample_mode;
+
+typedef struct {
+  int64_t n;              /* N particles */
+  int32_t d;              /* D state dimension */
+  int32_t dtype;          /* smc_dtype of particles and log pi */
+  uint64_t seed;          /* Philox4x64-10 key word 0 */
+  int32_t target;         /* smc_target_kind */
+  int32_t resample_mode;  /* smc_resample_mode */
+  double step;            /* random-walk proposal std eps: x_t = x_{t-1} + eps z (Sec. 5.2.3) */
+  double init_scale;      /* q0 = N(0, init_scale^2 I) (Algorithm 2, line 1) */
+  /* target parameters, DEVICE pointers, read during smc_init only */
+  const double* mu_dev;     /* GAUSS: D; STUDENT_T: 1 */
+  const double* sigma_dev;  /* GAUSS: D x D symmetric positive definite, row-major */
+  const float* X_dev;       /* LOGISTIC: M x D row-major */
+  const float* y_dev;       /* LOGISTIC: M labels in {0, 1} */
+  int32_t m;                /* LOGISTIC: M rows */
+  int32_t reserved;
+  double prior_var;         /* LOGISTIC: prior N(0, prior_var I) */
+  double nu;                /* STUDENT_T: degrees of freedom */
+} smc_config;
+
+typedef struct smc_sampler smc_sampler;
+
+/* Per-iteration statistics written by smc_reweight / smc_step (device memory,
+ * one record per iteration when a trace buffer is given). */
+typedef struct {
+  double lse;        /* log sum_i w_t^i (eq. (2) normaliser, log space) */
+  double logc;       /* log c_t = LSE_t - LSE_{t-1} (eq. (8)); LSE_{t-1} = 0 after a reset */
+  double ess;        /* N_eff = 1 / sum_i (w~_t^i)^2 (eq. (1)), from the quantised weights */
+  double max_logw;   /* m = max_i log w_t^i */
+  int64_t resampled; /* 1 if N_eff < N* triggered resampling (Algorithm 2, lines 7-9) */
+  int64_t t;         /* iteration index */
+  int64_t survivors; /* particles with ncopies > 0 when resampled, else 0 */
+} smc_iter_stats;
+
+/* Bytes of device workspace a sampler with this configuration needs. */
+int smc_workspace_bytes(const smc_config* cfg, size_t* bytes);
+
+/* Algorithm 2, line 1: draws x_0 ~ q0 = N(0, init_scale^2 I) with Philox
+ * (seed, t = 0, particle i) and sets w_0 = pi(x_0)/q0(x_0).
+ * x_dev/x_alt_dev: two N x D particle buffers (ping-pong: redistribute writes
+ * the other one); logpi_dev/logpi_alt_dev: two N buffers of the particle
+ * dtype; logw_dev: N doubles; workspace_dev: smc_workspace_bytes() bytes,
+ * 256-byte aligned.  All are borrowed until smc_destroy.  On success *out is
+ * a new handle.  Errors: SMC_EINVAL (sizes, pointers, alignment, target),
+ * SMC_ENOMEM (workspace too small), SMC_ECUDA. */
+int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_dev, double* logw_dev,
+             void* logpi_dev, void* logpi_alt_dev, void* workspace_dev, size_t workspace_bytes,
+             smc_stream_t stream);
+
+/* Algorithm 2, line 4 (proposal): starts iteration t <- t+1 and moves every
+ * particle x_t = x_{t-1} + eps z, z ~ N(0, I) from Philox (seed, t, i). */
+int smc_move(smc_sampler* h);
+
+/* Eq. (5) with the forward-proposal L-kernel L = q of Sec. 5.2.3 (the L/q
+ * factor is exactly 1):  log w_t = log w_{t-1} + log pi(x_t) - log pi(x_{t-1});
+ * then eqs. (1), (2), (8): m, LSE_t, N_eff, log c_t and the resampling
+ * decision into the device statistics (smc_read_stats). */
+int smc_reweight(smc_sampler* h);
+
+/* Eq. (7): f_t = sum_i w~_t^i x_t^i into mean_dev[D] (double) and, if
+ * cov_dev is not NULL, the weighted covariance into cov_dev[D*D]. */
+int smc_estimate(smc_sampler* h, double* mean_dev, double* cov_dev);
+
+/* Algorithm 4, line 1 (MVR): systematic resampling of the quantised weights
+ * W_i = E(log w_i - m) >> (62 - F) into ncopies_dev[N] (int32, sum N, eq. (9)),
+ * whatever the decision; did_resample_dev (int32, may be NULL) receives the
+ * decision of the last smc_reweight. */
+int smc_resample(smc_sampler* h, int32_t* ncopies_dev, int32_t* did_resample_dev);
+
+/* Algorithm 4, lines 2-3 with Algorithm 5 (S-R) as the definition of the
+ * result: particle row i and its log pi are written ncopies[i] times, in
+ * index order, into the other buffer, which becomes current; every log-weight
+ * is reset to -log N.  ncopies_dev must be N non-negative ints summing to N
+ * (else SMC_EINVAL at the next smc_sync, and nothing is written). */
+int smc_redistribute(smc_sampler* h, const int32_t* ncopies_dev);
+
+/* K iterations of Algorithm 2 (lines 3-10): move, reweight, normalise,
+ * estimate, N_eff, and resample + redistribute + reset when N_eff < N*,
+ * with no host synchronisation between iterations (the decision stays on the
+ * device; the launches of an iteration are replayed from a CUDA graph).
+ * mean_dev[D] receives f_K, cov_dev[D*D] (may be NULL) the final weighted
+ * covariance, trace_dev (may be NULL) K smc_iter_stats records, and
+ * fhat_dev[D] (may be NULL) the recycled estimate of eq. (6) over all
+ * iterations run so far. */
+int smc_step(smc_sampler* h, int32_t k, double* mean_dev, double* cov_dev, smc_iter_stats* trace_dev,
+             double* fhat_dev);
+
+/* Tracing: one iteration of smc_step launched directly (not from a graph),
+ * with events_host[0] (cudaEvent_t, created by the caller) recorded before it
+ * and events_host[j] after stage j: 1 move + reweight, 2 max / mean finalise,
+ * 3 quantise reduce, 4 quantise finalise, 5 systematic scan, 6 redistribute,
+ * 7 commit.  n_events must be 8, or 0 to record nothing.  The iteration is
+ * identical to one iteration of smc_step (mean_dev may be NULL). */
+int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host, int32_t n_events);
+
+/* Synchronises the sampler's stream; returns the first error recorded on the
+ * device since the last smc_sync (then clears it), or SMC_OK. */
+int smc_sync(smc_sampler* h);
+
+/* Copies the last iteration's statistics to the host (synchronising). */
+int smc_read_stats(smc_sampler* h, smc_iter_stats* out_host);
+
+/* 0 if x_dev / logpi_dev hold the current particles, 1 if the _alt buffers do
+ * (synchronising). */
+int smc_current(smc_sampler* h, int32_t* which_host);
+
+/* Frees the handle (host memory only). */
+int smc_destroy(smc_sampler* h);
+
+/* Message of the last error on this handle (or of the last handle-less call
+ * when h is NULL); never NULL. */
+const char* smc_last_error(const smc_sampler* h);
+
+/* ---------------------------------------------------------------------------
+ * Stateless redistribute (the resample + redistribute microbenchmark).
+ * Algorithm 5 on raw rows: out row k = in row src(k), src(k) = the i with
+ * off_i <= k < off_i + ncopies_i, off = exclusive cumulative sum of ncopies.
+ * row_bytes must be a multiple of 4; in/out must not overlap.  ws_dev:
+ * smc_redistribute_ws_bytes(n) bytes, 256-byte aligned.  An ncopies vector
+ * with a negative entry or a sum other than n writes nothing and records
+ * SMC_EINVAL, returned by smc_ws_status. */
+int smc_redistribute_ws_bytes(int64_t n, size_t* bytes);
+int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
+                         void* out_dev, void* ws_dev, smc_stream_t stream);
+
+/* Stateless resampling (Algorithm 4, line 1) of logw_dev[n] with Philox
+ * (seed, t): writes ncopies_dev[n] and, when stats_dev is not NULL, one
+ * smc_iter_stats record (lse, ess, max_logw, resampled decision under mode).
+ * ws_dev: smc_redistribute_ws_bytes(n) bytes. */
+int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t t, int32_t mode,
+                     int32_t* ncopies_dev, smc_iter_stats* stats_dev, void* ws_dev, smc_stream_t stream);
+
+/* Synchronises stream and returns (then clears) the error recorded in a
+ * stateless workspace. */
+int smc_ws_status(void* ws_dev, smc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMC_H_ */

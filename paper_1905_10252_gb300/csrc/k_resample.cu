@@ -1,0 +1,620 @@
+// k_resample.cu -- resampling and redistribute on sm_103a.
+//
+//  * Quantisation of the weights to 64-bit fixed point, W_i = E(log w_i - m)
+//    >> (62 - F), with exact 128-bit sums S, sum W^2, sum E (reduce pass), the
+//    N_eff decision 2 S^2 < N sum W^2 (eq. (1) against N* = N/2), LSE_t and
+//    log c_t (eqs. (2), (8)) in a single-block finaliser.
+//  * Systematic resampling (MVR, Algorithm 4 line 1) on the integer CDF:
+//    off_i = floor((N C_{i-1} + U)/S) is the exclusive cumulative sum of
+//    ncopies and ncopies_i = off_{i+1} - off_i (eq. (9) holds by telescoping);
+//    a block-local scan of W plus the block prefix gives C_i.
+//  * Redistribute (Algorithm 5 as the definition of the output): output-tile
+//    parallel gather.  A tile of 4096 output rows knows its first source row
+//    (written by the scan pass), marks the start of every source run that
+//    begins inside the tile (max over equal offsets picks the survivor), a
+//    block max-scan turns the marks into src(k), and the rows are copied with
+//    16-byte vector loads/stores.  Replaces the paper's MPI nearly-sort and
+//    rotational shifts (Sec. 4) with O(1) passes over the data.
+#include <cmath>
+
+#include "smc_internal.cuh"
+#include "smc_kernels.h"
+
+namespace smc {
+
+// 2^-j/64 table of the fixed-point exponential, ~2^63 2^(-j/64).
+__constant__ uint64_t c_T[64];
+
+// floor(sqrt(n)) for n < 2^126 by Newton's iteration from above.
+static uint64_t isqrt_newton(u128 n) {
+  if (n == 0) return 0;
+  u128 x = u128(1) << 64;  // >= sqrt(n) for n < 2^128
+  while (true) {
+    const u128 y = (x + n / x) >> 1;
+    if (y >= x) break;
+    x = y;
+  }
+  return uint64_t(x);
+}
+
+// T[j] = prod over the set bits b (b = 1 is the top of 6) of c_b with
+// c_0 = 2^62 and c_b = isqrt(c_{b-1} 2^63) ~= 2^63 2^(-2^-b); every product is
+// floored to 2^63 fixed point.
+static void build_table(uint64_t T[64]) {
+  uint64_t c[7];
+  c[0] = 1ull << 62;
+  for (int b = 1; b <= 6; ++b) c[b] = isqrt_newton(u128(c[b - 1]) << 63);
+  for (int j = 0; j < 64; ++j) {
+    uint64_t acc = 1ull << 63;
+    for (int b = 1; b <= 6; ++b)
+      if (j & (1 << (6 - b))) acc = uint64_t((u128(acc) * c[b]) >> 63);
+    T[j] = acc;
+  }
+}
+
+cudaError_t upload_expfx_table() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  uint64_t T[64];
+  build_table(T);
+  e = cudaMemcpyToSymbol(c_T, T, sizeof T);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
+__device__ __forceinline__ void load_table(uint64_t* T) {
+  if (threadIdx.x < 64) T[threadIdx.x] = c_T[threadIdx.x];
+  __syncthreads();
+}
+
+// padded shared-memory index: 16 items per thread, stride 17 (bank spread)
+__device__ __forceinline__ int pad_idx(int idx) { return (idx >> 4) * 17 + (idx & 15); }
+
+// ---------------------------------------------------------------- state init
+// reset value of Algorithm 4 line 3, -log N, from the exact log so that both
+// implementations agree bit for bit
+__global__ void k_state_init(DevState* st, int64_t n, int64_t t, int F) {
+  if (threadIdx.x != 0) return;
+  const double reset_logw = -det_log(double(n));
+  st->t = t;
+  st->cur = 0;
+  st->flag = 0;
+  st->err = 0;
+  st->F = F;
+  st->L = 1;
+  st->m = 0.0;
+  st->lse = 0.0;
+  st->lse_prev = 0.0;
+  st->logc = 0.0;
+  st->ess = 0.0;
+  st->reset_logw = reset_logw;
+  st->S = st->U = 0;
+  st->sw2_lo = st->sw2_hi = st->se_lo = st->se_hi = 0;
+  st->recip = 0;
+  st->rc_max = -INFINITY;
+  st->rc_den = 0.0;
+  for (int c = 0; c < kMaxD; ++c) st->rc_num[c] = st->mean[c] = 0.0;
+  st->est_s = 0.0;
+  st->trace = nullptr;
+  st->trace_t0 = 0;
+  st->mean_out = st->fhat_out = st->cov_out = nullptr;
+  st->want_cov = 0;
+}
+
+// ---------------------------------------------------------------- max of log w (stateless path)
+// part[b] = {max, number of finite entries}; NaN is an error.
+__global__ void __launch_bounds__(kQThreads) k_max_logw(const double* __restrict__ logw, int64_t n,
+                                                       double* __restrict__ part, DevState* st) {
+  __shared__ double shm[kQThreads / 32], shc[kQThreads / 32];
+  double m = -INFINITY, cnt = 0.0;
+  bool nan = false;
+  const int64_t base = int64_t(blockIdx.x) * kQTile;
+#pragma unroll 4
+  for (int k = 0; k < kQItems; ++k) {
+    const int64_t i = base + k * kQThreads + threadIdx.x;
+    if (i < n) {
+      const double v = logw[i];
+      nan |= isnan(v);
+      if (v > -INFINITY) cnt += 1.0;
+      m = fmax(m, v);
+    }
+  }
+  if (nan) record_error(st, SMC_ENONFINITE);
+  m = warp_max(m);
+  cnt = warp_sum(cnt);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    shm[wid] = m;
+    shc[wid] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = -INFINITY, cc = 0.0;
+    for (int w = 0; w < kQThreads / 32; ++w) {
+      mm = fmax(mm, shm[w]);
+      cc += shc[w];
+    }
+    part[2 * blockIdx.x] = mm;
+    part[2 * blockIdx.x + 1] = cc;
+  }
+}
+
+// ---------------------------------------------------------------- quantise: reduce
+__global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
+  __shared__ uint64_t T[64];
+  __shared__ uint64_t sh[kQThreads / 32][5];
+  load_table(T);
+  const DevState* st = a.st;
+  uint64_t sw = 0;
+  u128 sw2 = 0, se = 0;
+  if (!st->err) {
+    const double m = st->m;
+    const int sh_w = 62 - st->F;
+    const int64_t base = int64_t(blockIdx.x) * kQTile;
+#pragma unroll 4
+    for (int k = 0; k < kQItems; ++k) {
+      const int64_t i = base + k * kQThreads + threadIdx.x;
+      if (i < a.n) {
+        const uint64_t E = expfx(a.logw[i] - m, T);
+        const uint64_t W = E >> sh_w;
+        sw += W;
+        sw2 += u128(W) * W;
+        se += E;
+      }
+    }
+  }
+  sw = warp_sum(sw);
+  sw2 = warp_sum_u128(sw2);
+  se = warp_sum_u128(se);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[wid][0] = sw;
+    sh[wid][1] = uint64_t(sw2);
+    sh[wid][2] = uint64_t(sw2 >> 64);
+    sh[wid][3] = uint64_t(se);
+    sh[wid][4] = uint64_t(se >> 64);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t tw = 0;
+    u128 t2 = 0, te = 0;
+    for (int w = 0; w < kQThreads / 32; ++w) {
+      tw += sh[w][0];
+      t2 += (u128(sh[w][2]) << 64) | sh[w][1];
+      te += (u128(sh[w][4]) << 64) | sh[w][3];
+    }
+    uint64_t* q = a.qpart + 5 * int64_t(blockIdx.x);
+    q[0] = tw;
+    q[1] = uint64_t(t2);
+    q[2] = uint64_t(t2 >> 64);
+    q[3] = uint64_t(te);
+    q[4] = uint64_t(te >> 64);
+  }
+}
+
+__device__ __forceinline__ double u128_to_double(u128 v) {
+  return double(uint64_t(v >> 64)) * 0x1p64 + double(uint64_t(v));
+}
+
+// ---------------------------------------------------------------- quantise: finalise
+// Single block: totals, exclusive prefix of the block sums (the CDF base of
+// each scan block), decision, systematic offset U, division constants, LSE,
+// N_eff, log c_t, and the statistics record.
+__global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int set_lse_prev) {
+  __shared__ uint64_t scratch[33];
+  __shared__ uint64_t shw[32], sh2l[32], sh2h[32], shel[32], sheh[32];
+  DevState* st = a.st;
+  const int nb = a.nblocks;
+  uint64_t tw = 0;
+  u128 t2 = 0, te = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const uint64_t* q = a.qpart + 5 * int64_t(b);
+    tw += q[0];
+    t2 += (u128(q[2]) << 64) | q[1];
+    te += (u128(q[4]) << 64) | q[3];
+  }
+  tw = warp_sum(tw);
+  t2 = warp_sum_u128(t2);
+  te = warp_sum_u128(te);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    shw[wid] = tw;
+    sh2l[wid] = uint64_t(t2);
+    sh2h[wid] = uint64_t(t2 >> 64);
+    shel[wid] = uint64_t(te);
+    sheh[wid] = uint64_t(te >> 64);
+  }
+  // exclusive scan of the block sums of W: contiguous chunk per thread
+  const int chunk = (nb + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * chunk, b1 = min(nb, b0 + chunk);
+  uint64_t local = 0;
+  for (int b = b0; b < b1; ++b) local += a.qpart[5 * int64_t(b)];
+  uint64_t total;
+  uint64_t pre = block_excl_scan_u64(local, scratch, &total);  // contains __syncthreads
+  for (int b = b0; b < b1; ++b) {
+    a.cbase[b] = pre;
+    pre += a.qpart[5 * int64_t(b)];
+  }
+  if (threadIdx.x != 0) return;
+  uint64_t S = 0;
+  u128 sw2 = 0, se = 0;
+  for (int w = 0; w < nw; ++w) {
+    S += shw[w];
+    sw2 += (u128(sh2h[w]) << 64) | sh2l[w];
+    se += (u128(sheh[w]) << 64) | shel[w];
+  }
+  const uint64_t n = uint64_t(a.n);
+  int flag = 0;
+  if (!st->err && S > 0) {
+    if (a.mode == SMC_RESAMPLE_ALWAYS)
+      flag = 1;
+    else if (a.mode == SMC_RESAMPLE_NEVER)
+      flag = 0;
+    else
+      flag = (u128(S) * S * 2) < u128(n) * sw2;
+  }
+  const P4 r = stream_block(a.seed, uint64_t(st->t), kPurposeResample, ~0ull, 0);
+  const uint64_t U = S ? __umul64hi(r.v[0], S) : 0;
+  const int L = S ? 64 - __clzll((long long)S) : 1;
+  const uint64_t R = S ? uint64_t(((u128(1) << (63 + L)) - 1) / S) : 0;
+  const double m = st->m;
+  const double lse = m + log(u128_to_double(se) * 0x1p-62);
+  const double Sd = double(S);
+  const double ess = (S && sw2) ? Sd * Sd / u128_to_double(sw2) : 0.0;
+  st->S = S;
+  st->U = U;
+  st->L = L;
+  st->recip = R;
+  st->sw2_lo = uint64_t(sw2);
+  st->sw2_hi = uint64_t(sw2 >> 64);
+  st->se_lo = uint64_t(se);
+  st->se_hi = uint64_t(se >> 64);
+  st->flag = flag;
+  st->lse = lse;
+  st->ess = ess;
+  st->logc = lse - st->lse_prev;
+  if (set_lse_prev) st->lse_prev = lse;
+  smc_iter_stats rec;
+  rec.lse = lse;
+  rec.logc = st->logc;
+  rec.ess = ess;
+  rec.max_logw = m;
+  rec.resampled = flag;
+  rec.t = st->t;
+  rec.survivors = 0;
+  st->survivors = 0;
+  st->last = rec;
+  if (st->trace) {
+    const int64_t idx = st->t - st->trace_t0 - 1;
+    if (idx >= 0) st->trace[idx] = rec;
+  }
+  if (a.stats_out) *a.stats_out = rec;
+}
+
+// ---------------------------------------------------------------- quantise: scan + ncopies
+__global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
+  const DevState* st = a.st;
+  if (st->err || !(a.force || st->flag)) return;
+  __shared__ uint64_t T[64];
+  __shared__ union {
+    double lw[kQThreads * 17];
+    uint32_t o[2][kQThreads * 17];
+  } buf;
+  __shared__ uint64_t scratch[33];
+  load_table(T);
+  const int64_t n = a.n;
+  const int64_t base = int64_t(blockIdx.x) * kQTile;
+#pragma unroll 4
+  for (int k = 0; k < kQItems; ++k) {
+    const int idx = k * kQThreads + threadIdx.x;
+    const int64_t i = base + idx;
+    buf.lw[pad_idx(idx)] = i < n ? a.logw[i] : -INFINITY;
+  }
+  __syncthreads();
+  const double m = st->m;
+  const int sh_w = 62 - st->F;
+  const uint64_t S = st->S, U = st->U, R = st->recip;
+  const int L = st->L;
+  uint64_t W[kQItems];
+  uint64_t tsum = 0;
+#pragma unroll
+  for (int q = 0; q < kQItems; ++q) {
+    W[q] = expfx(buf.lw[threadIdx.x * 17 + q] - m, T) >> sh_w;
+    tsum += W[q];
+  }
+  uint64_t btot;
+  uint64_t C = a.cbase[blockIdx.x] + block_excl_scan_u64(tsum, scratch, &btot);
+  uint32_t offv[kQItems], ncv[kQItems];
+  unsigned nsurv = 0;
+  uint64_t lo = div_by_S(u128(n) * C + U, S, L, R);
+  const int64_t i0 = base + int64_t(threadIdx.x) * kQItems;
+#pragma unroll
+  for (int q = 0; q < kQItems; ++q) {
+    C += W[q];
+    const uint64_t hi = div_by_S(u128(n) * C + U, S, L, R);
+    offv[q] = uint32_t(lo);
+    ncv[q] = uint32_t(hi - lo);
+    const int64_t i = i0 + q;
+    if (hi > lo && i < n) {
+      ++nsurv;
+      // every redistribute tile whose first output row lies in [lo, hi)
+      for (uint64_t kb = ((lo + kRTile - 1) / kRTile) * kRTile; kb < hi && kb < uint64_t(n); kb += kRTile)
+        a.tile_src[kb / kRTile] = int32_t(i);
+    }
+    lo = hi;
+  }
+  {
+    unsigned v = nsurv;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&const_cast<DevState*>(st)->survivors, (unsigned long long)v);
+  }
+  __syncthreads();  // buf.lw no longer read
+#pragma unroll
+  for (int q = 0; q < kQItems; ++q) {
+    buf.o[0][threadIdx.x * 17 + q] = offv[q];
+    buf.o[1][threadIdx.x * 17 + q] = ncv[q];
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int k = 0; k < kQItems; ++k) {
+    const int idx = k * kQThreads + threadIdx.x;
+    const int64_t i = base + idx;
+    if (i < n) {
+      a.off[i] = buf.o[0][pad_idx(idx)];
+      if (a.ncopies) a.ncopies[i] = int32_t(buf.o[1][pad_idx(idx)]);
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) a.off[n] = uint32_t(n);
+}
+
+// ---------------------------------------------------------------- standalone ncopies scan
+__global__ void __launch_bounds__(kQThreads) k_nc_reduce(NcScanArgs a) {
+  __shared__ uint64_t sh[kQThreads / 32];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  uint64_t s = 0;
+  const int64_t base = int64_t(blockIdx.x) * kQTile;
+#pragma unroll 4
+  for (int k = 0; k < kQItems; ++k) {
+    const int64_t i = base + k * kQThreads + threadIdx.x;
+    if (i < a.n) {
+      const int32_t c = a.ncopies[i];
+      if (c < 0) bad = 1;
+      s += uint64_t(uint32_t(max(c, 0)));
+    }
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < kQThreads / 32; ++w) t += sh[w];
+    a.part[blockIdx.x] = t;
+    if (bad) record_error(a.st, SMC_EINVAL);
+  }
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_nc_finalize(NcScanArgs a) {
+  __shared__ uint64_t scratch[33];
+  const int nb = a.nblocks;
+  const int chunk = (nb + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * chunk, b1 = min(nb, b0 + chunk);
+  uint64_t local = 0;
+  for (int b = b0; b < b1; ++b) local += a.part[b];
+  uint64_t total;
+  uint64_t pre = block_excl_scan_u64(local, scratch, &total);
+  for (int b = b0; b < b1; ++b) {
+    a.cbase[b] = pre;
+    pre += a.part[b];
+  }
+  if (threadIdx.x == 0 && total != uint64_t(a.n)) record_error(a.st, SMC_EINVAL);
+}
+
+__global__ void __launch_bounds__(kQThreads) k_nc_scan(NcScanArgs a) {
+  if (a.st->err) return;
+  __shared__ uint32_t buf[kQThreads * 17];
+  __shared__ uint64_t scratch[33];
+  const int64_t n = a.n;
+  const int64_t base = int64_t(blockIdx.x) * kQTile;
+#pragma unroll 4
+  for (int k = 0; k < kQItems; ++k) {
+    const int idx = k * kQThreads + threadIdx.x;
+    const int64_t i = base + idx;
+    buf[pad_idx(idx)] = i < n ? uint32_t(a.ncopies[i]) : 0u;
+  }
+  __syncthreads();
+  uint32_t c[kQItems];
+  uint64_t tsum = 0;
+#pragma unroll
+  for (int q = 0; q < kQItems; ++q) {
+    c[q] = buf[threadIdx.x * 17 + q];
+    tsum += c[q];
+  }
+  uint64_t btot;
+  uint64_t o = a.cbase[blockIdx.x] + block_excl_scan_u64(tsum, scratch, &btot);
+  const int64_t i0 = base + int64_t(threadIdx.x) * kQItems;
+#pragma unroll
+  for (int q = 0; q < kQItems; ++q) {
+    const int64_t i = i0 + q;
+    if (c[q] > 0 && i < n) {
+      for (uint64_t kb = ((o + kRTile - 1) / kRTile) * kRTile; kb < o + c[q] && kb < uint64_t(n); kb += kRTile)
+        a.tile_src[kb / kRTile] = int32_t(i);
+    }
+    buf[threadIdx.x * 17 + q] = uint32_t(o);  // each thread rewrites only its own items
+    o += c[q];
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int k = 0; k < kQItems; ++k) {
+    const int idx = k * kQThreads + threadIdx.x;
+    const int64_t i = base + idx;
+    if (i < n) a.off[i] = buf[pad_idx(idx)];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) a.off[n] = uint32_t(n);
+}
+
+// ---------------------------------------------------------------- redistribute
+template <typename V, int CPR>
+__global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
+  int cur = 0;
+  if (a.stateful) {
+    if (a.st->err || !(a.force || a.st->flag)) return;
+    cur = a.st->cur;
+  } else if (a.st->err) {
+    return;
+  }
+  __shared__ int32_t mark[kRTile];
+  __shared__ int32_t wsc[kRThreads / 32];
+  const int64_t n = a.n;
+  const int64_t k0 = int64_t(blockIdx.x) * kRTile;
+  const int len = int(n - k0 < kRTile ? n - k0 : int64_t(kRTile));
+  // tile_src is complete whenever the copy counts sum to n (checked upstream);
+  // the clamps keep every row index inside [0, n) regardless
+  const int32_t i_lo = min(max(a.tile_src[blockIdx.x], 0), int32_t(n - 1));
+  const int32_t i_hi =
+      (int(blockIdx.x) + 1 < a.ntiles) ? min(max(a.tile_src[blockIdx.x + 1], i_lo), int32_t(n - 1)) : int32_t(n - 1);
+  for (int k = threadIdx.x; k < kRTile; k += blockDim.x) mark[k] = (k == 0) ? i_lo : -1;
+  __syncthreads();
+  // runs starting inside the tile: the largest i with off_i == k is the survivor
+  for (int64_t i = int64_t(i_lo) + 1 + threadIdx.x; i <= i_hi; i += blockDim.x) {
+    const int64_t o = int64_t(a.off[i]) - k0;
+    if (o > 0 && o < len) atomicMax(&mark[o], int32_t(i));
+  }
+  __syncthreads();
+  // inclusive max-scan of mark[0, kRTile): 16 consecutive entries per thread
+  {
+    constexpr int kItems = kRTile / kRThreads;
+    const int b = threadIdx.x * kItems;
+    int run = -1;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) run = max(run, mark[b + q]);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = warp_incl_max_i32(run);
+    if (lane == 31) wsc[wid] = incl;
+    __syncthreads();
+    int carry = -1;
+    for (int w = 0; w < wid; ++w) carry = max(carry, wsc[w]);
+    int excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = -1;
+    run = max(carry, excl);
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      run = max(run, mark[b + q]);
+      mark[b + q] = run;
+    }
+  }
+  __syncthreads();
+  // copy rows: element e of the tile is chunk (e % cpr) of row (e / cpr)
+  const int cpr = CPR > 0 ? CPR : a.row_bytes / int(sizeof(V));
+  const V* __restrict__ in = static_cast<const V*>(cur ? a.x_in[1] : a.x_in[0]);
+  V* __restrict__ out = static_cast<V*>(cur ? a.x_out[1] : a.x_out[0]) + k0 * cpr;
+  const int total = len * cpr;
+  constexpr int kU = 4;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kRThreads * kU) {
+    V v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * kRThreads;
+      if (e < total) {
+        const int k = e / cpr, c = e - k * cpr;
+        v[u] = in[int64_t(mark[k]) * cpr + c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * kRThreads;
+      if (e < total) out[e] = v[u];
+    }
+  }
+  if (a.lp_bytes == 4) {
+    const uint32_t* __restrict__ li = static_cast<const uint32_t*>(cur ? a.lp_in[1] : a.lp_in[0]);
+    uint32_t* __restrict__ lo = static_cast<uint32_t*>(cur ? a.lp_out[1] : a.lp_out[0]) + k0;
+    for (int k = threadIdx.x; k < len; k += kRThreads) lo[k] = li[mark[k]];
+  } else if (a.lp_bytes == 8) {
+    const uint64_t* __restrict__ li = static_cast<const uint64_t*>(cur ? a.lp_in[1] : a.lp_in[0]);
+    uint64_t* __restrict__ lo = static_cast<uint64_t*>(cur ? a.lp_out[1] : a.lp_out[0]) + k0;
+    for (int k = threadIdx.x; k < len; k += kRThreads) lo[k] = li[mark[k]];
+  }
+  if (a.logw) {
+    const double reset = a.stateful ? a.st->reset_logw : a.reset_logw;
+    double* __restrict__ lw = a.logw + k0;
+    for (int k = threadIdx.x; k < len; k += kRThreads) lw[k] = reset;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+static int qblocks(int64_t n) { return int((n + kQTile - 1) / kQTile); }
+
+cudaError_t launch_state_init(DevState* st, int64_t n, int64_t t, int F, cudaStream_t s) {
+  k_state_init<<<1, 32, 0, s>>>(st, n, t, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_logw(const double* logw, int64_t n, double* part, int nb, DevState* st, cudaStream_t s) {
+  k_max_logw<<<nb, kQThreads, 0, s>>>(logw, n, part, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant_reduce(const QuantArgs& a, cudaStream_t s) {
+  k_quant_reduce<<<qblocks(a.n), kQThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant_finalize(const QuantArgs& a, int set_lse_prev, cudaStream_t s) {
+  k_quant_finalize<<<1, kFinThreads, 0, s>>>(a, set_lse_prev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant_scan(const QuantArgs& a, cudaStream_t s) {
+  k_quant_scan<<<qblocks(a.n), kQThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nc_reduce(const NcScanArgs& a, cudaStream_t s) {
+  k_nc_reduce<<<qblocks(a.n), kQThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nc_finalize(const NcScanArgs& a, cudaStream_t s) {
+  k_nc_finalize<<<1, kFinThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nc_scan(const NcScanArgs& a, cudaStream_t s) {
+  k_nc_scan<<<qblocks(a.n), kQThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_redistribute(const RedistArgs& a, cudaStream_t s) {
+  const int grid = int((a.n + kRTile - 1) / kRTile);
+  const int rb = a.row_bytes;
+  if (rb % 16 == 0) {
+    switch (rb / 16) {
+      case 1: k_redistribute<uint4, 1><<<grid, kRThreads, 0, s>>>(a); break;
+      case 2: k_redistribute<uint4, 2><<<grid, kRThreads, 0, s>>>(a); break;
+      case 4: k_redistribute<uint4, 4><<<grid, kRThreads, 0, s>>>(a); break;
+      case 8: k_redistribute<uint4, 8><<<grid, kRThreads, 0, s>>>(a); break;
+      default: k_redistribute<uint4, 0><<<grid, kRThreads, 0, s>>>(a); break;
+    }
+  } else if (rb % 8 == 0) {
+    if (rb == 8)
+      k_redistribute<uint2, 1><<<grid, kRThreads, 0, s>>>(a);
+    else
+      k_redistribute<uint2, 0><<<grid, kRThreads, 0, s>>>(a);
+  } else {
+    if (rb == 4)
+      k_redistribute<uint32_t, 1><<<grid, kRThreads, 0, s>>>(a);
+    else
+      k_redistribute<uint32_t, 0><<<grid, kRThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+size_t devstate_bytes() { return sizeof(DevState); }
+
+}  // namespace smc

@@ -1,0 +1,596 @@
+// smc_api.cu -- the C-ABI of libsmc.so (declared in include/smc.h): argument
+// checking, the workspace layout, the order of kernel launches for each step
+// of the sampler, CUDA-graph replay of whole iterations, and error reporting.
+// The library allocates no device memory: every buffer is the caller's.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "smc_internal.cuh"
+#include "smc_kernels.h"
+
+using namespace smc;
+
+namespace {
+
+thread_local std::string g_err = "ok";
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxPartBlocks = 4096;  // particle-kernel grid cap (partials buffer)
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int quant_shift(int64_t n) {
+  int c = 0;
+  while ((int64_t(1) << c) < n) ++c;
+  const int F = 63 - c;
+  return F > 62 ? 62 : F;
+}
+
+// Byte offsets of the stateful sampler's workspace.
+struct Layout {
+  size_t st, tg, part, qpart, cbase, off, tile_src, total;
+  int qblocks, ntiles;
+};
+
+Layout layout_for(int64_t n, int d) {
+  Layout L{};
+  L.qblocks = int(div_up(n, kQTile));
+  L.ntiles = int(div_up(n, kRTile));
+  size_t p = 0;
+  L.st = p;
+  p = align_up(p + sizeof(DevState));
+  L.tg = p;
+  p = align_up(p + sizeof(TargetDev));
+  L.part = p;
+  const size_t part_blocks = size_t(std::max(kMaxPartBlocks, L.qblocks));
+  p = align_up(p + part_blocks * (2 + size_t(d < 1 ? 1 : d)) * sizeof(double));
+  L.qpart = p;
+  p = align_up(p + size_t(L.qblocks) * 5 * sizeof(uint64_t));
+  L.cbase = p;
+  p = align_up(p + size_t(L.qblocks) * sizeof(uint64_t));
+  L.off = p;
+  p = align_up(p + size_t(n + 1) * sizeof(uint32_t));
+  L.tile_src = p;
+  p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
+  L.total = p;
+  return L;
+}
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 132;
+  if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 132;
+  if (dev >= 0 && dev < 64) cached[dev] = v;
+  return v;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+struct smc_sampler {
+  smc_config cfg;
+  int64_t n;
+  int d;
+  int dtype;
+  size_t esize;
+  void* x[2];
+  void* lp[2];
+  double* logw;
+  char* ws;
+  Layout L;
+  cudaStream_t stream;
+  DevState* st;
+  TargetDev* tg;
+  double* part;
+  uint64_t* qpart;
+  uint64_t* cbase;
+  uint32_t* off;
+  int32_t* tile_src;
+  int grid_p;
+  // CUDA graph of one iteration (with and without the covariance stage)
+  cudaGraphExec_t g_iter[2];
+  std::string err;
+};
+
+namespace {
+
+int fail(smc_sampler* h, int code, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_err = msg;
+  return code;
+}
+
+int cuda_fail(smc_sampler* h, cudaError_t e, const char* where) {
+  return fail(h, SMC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SMC_TRY(h, expr)                                  \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) return cuda_fail((h), _e, #expr); \
+  } while (0)
+
+ParticleArgs particle_args(const smc_sampler* h) {
+  ParticleArgs a{};
+  a.n = h->n;
+  a.d = h->d;
+  a.dtype = h->dtype;
+  a.kind = h->cfg.target;
+  a.seed = h->cfg.seed;
+  a.step = h->cfg.step;
+  a.init_scale = h->cfg.init_scale;
+  a.x[0] = h->x[0];
+  a.x[1] = h->x[1];
+  a.logpi[0] = h->lp[0];
+  a.logpi[1] = h->lp[1];
+  a.logw = h->logw;
+  a.part = h->part;
+  a.tg = h->tg;
+  a.st = h->st;
+  return a;
+}
+
+QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies) {
+  QuantArgs q{};
+  q.n = h->n;
+  q.logw = h->logw;
+  q.seed = h->cfg.seed;
+  q.mode = h->cfg.resample_mode;
+  q.force = force;
+  q.qpart = h->qpart;
+  q.cbase = h->cbase;
+  q.off = h->off;
+  q.ncopies = ncopies;
+  q.tile_src = h->tile_src;
+  q.nblocks = h->L.qblocks;
+  q.ntiles = h->L.ntiles;
+  q.st = h->st;
+  q.stats_out = nullptr;
+  return q;
+}
+
+RedistArgs redist_args(const smc_sampler* h, int force) {
+  RedistArgs r{};
+  r.n = h->n;
+  r.row_bytes = int32_t(h->esize * h->d);
+  r.lp_bytes = int32_t(h->esize);
+  r.off = h->off;
+  r.tile_src = h->tile_src;
+  r.ntiles = h->L.ntiles;
+  r.force = force;
+  r.x_in[0] = h->x[0];
+  r.x_in[1] = h->x[1];
+  r.x_out[0] = h->x[1];
+  r.x_out[1] = h->x[0];
+  r.lp_in[0] = h->lp[0];
+  r.lp_in[1] = h->lp[1];
+  r.lp_out[0] = h->lp[1];
+  r.lp_out[1] = h->lp[0];
+  r.logw = h->logw;
+  r.reset_logw = 0.0;
+  r.st = h->st;
+  r.stateful = 1;
+  return r;
+}
+
+// Weighted statistics after a reweight: max + mean, quantised sums, decision.
+cudaError_t launch_stats(smc_sampler* h, int write_mean_out, int set_lse_prev) {
+  cudaError_t e = launch_est_finalize(h->part, h->grid_p, h->d, h->st, write_mean_out, h->stream);
+  if (e != cudaSuccess) return e;
+  const QuantArgs q = quant_args(h, 0, nullptr);
+  e = launch_quant_reduce(q, h->stream);
+  if (e != cudaSuccess) return e;
+  return launch_quant_finalize(q, set_lse_prev, h->stream);
+}
+
+// One iteration of Algorithm 2 (lines 3-10), all on h->stream.
+cudaError_t launch_iteration(smc_sampler* h, bool with_cov) {
+  const ParticleArgs a = particle_args(h);
+  cudaError_t e = launch_begin(h->st, h->stream);
+  if (e == cudaSuccess) e = launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, h->stream);
+  if (e == cudaSuccess) e = launch_est_finalize(h->part, h->grid_p, h->d, h->st, 1, h->stream);
+  if (e == cudaSuccess && with_cov) e = launch_zero_cov(h->st, h->d, h->stream);
+  if (e == cudaSuccess && with_cov) e = launch_cov(a, nullptr, h->grid_p, h->stream);
+  const QuantArgs q = quant_args(h, 0, nullptr);
+  if (e == cudaSuccess) e = launch_quant_reduce(q, h->stream);
+  if (e == cudaSuccess) e = launch_quant_finalize(q, 0, h->stream);
+  if (e == cudaSuccess) e = launch_quant_scan(q, h->stream);
+  if (e == cudaSuccess) e = launch_redistribute(redist_args(h, 0), h->stream);
+  if (e == cudaSuccess) e = launch_commit(h->st, h->d, 0, 1, h->stream);
+  return e;
+}
+
+cudaError_t build_graph(smc_sampler* h, bool with_cov, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = launch_iteration(h, with_cov);
+  e = cudaStreamEndCapture(h->stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return le;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+int check_config(const smc_config* c) {
+  if (!c) return fail(nullptr, SMC_EINVAL, "null config");
+  if (c->n < 1 || c->n > 2147483647LL) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
+  if (c->d < 1 || c->d > kMaxD) return fail(nullptr, SMC_EINVAL, "d must be in [1, 32]");
+  if (c->dtype != SMC_F32 && c->dtype != SMC_F64) return fail(nullptr, SMC_EINVAL, "dtype must be SMC_F32 or SMC_F64");
+  if (c->target != SMC_GAUSS && c->target != SMC_STUDENT_T)
+    return fail(nullptr, SMC_EINVAL, "target kind not supported by this build");
+  if (c->target == SMC_STUDENT_T && (c->d != 1 || !(c->nu > 0.0)))
+    return fail(nullptr, SMC_EINVAL, "Student-t target needs d == 1 and nu > 0");
+  if (c->target == SMC_GAUSS && (!c->mu_dev || !c->sigma_dev))
+    return fail(nullptr, SMC_EINVAL, "Gaussian target needs mu_dev and sigma_dev");
+  if (c->target == SMC_STUDENT_T && !c->mu_dev) return fail(nullptr, SMC_EINVAL, "Student-t target needs mu_dev");
+  if (c->resample_mode < 0 || c->resample_mode > 2) return fail(nullptr, SMC_EINVAL, "bad resample_mode");
+  if (!(c->step >= 0.0) || !(c->init_scale > 0.0)) return fail(nullptr, SMC_EINVAL, "bad step / init_scale");
+  return SMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int smc_workspace_bytes(const smc_config* cfg, size_t* bytes) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!bytes) return fail(nullptr, SMC_EINVAL, "null bytes");
+  *bytes = layout_for(cfg->n, cfg->d).total;
+  return SMC_OK;
+}
+
+int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_dev, double* logw_dev,
+             void* logpi_dev, void* logpi_alt_dev, void* workspace_dev, size_t workspace_bytes,
+             smc_stream_t stream) {
+  if (!out) return fail(nullptr, SMC_EINVAL, "null out");
+  *out = nullptr;
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!x_dev || !x_alt_dev || !logw_dev || !logpi_dev || !logpi_alt_dev || !workspace_dev)
+    return fail(nullptr, SMC_EINVAL, "null buffer");
+  if (!aligned(workspace_dev, kAlign)) return fail(nullptr, SMC_EINVAL, "workspace must be 256-byte aligned");
+  const size_t es = cfg->dtype == SMC_F64 ? 8 : 4;
+  if (!aligned(x_dev, 16) || !aligned(x_alt_dev, 16) || !aligned(logw_dev, 8) || !aligned(logpi_dev, es) ||
+      !aligned(logpi_alt_dev, es))
+    return fail(nullptr, SMC_EINVAL, "particle buffers must be 16-byte aligned");
+  const Layout L = layout_for(cfg->n, cfg->d);
+  if (workspace_bytes < L.total) return fail(nullptr, SMC_ENOMEM, "workspace too small");
+  cudaError_t e = upload_expfx_table();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "upload_expfx_table");
+
+  smc_sampler* h = new (std::nothrow) smc_sampler();
+  if (!h) return fail(nullptr, SMC_ENOMEM, "host allocation failed");
+  h->cfg = *cfg;
+  h->n = cfg->n;
+  h->d = cfg->d;
+  h->dtype = cfg->dtype;
+  h->esize = es;
+  h->x[0] = x_dev;
+  h->x[1] = x_alt_dev;
+  h->lp[0] = logpi_dev;
+  h->lp[1] = logpi_alt_dev;
+  h->logw = logw_dev;
+  h->ws = static_cast<char*>(workspace_dev);
+  h->L = L;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->st = reinterpret_cast<DevState*>(h->ws + L.st);
+  h->tg = reinterpret_cast<TargetDev*>(h->ws + L.tg);
+  h->part = reinterpret_cast<double*>(h->ws + L.part);
+  h->qpart = reinterpret_cast<uint64_t*>(h->ws + L.qpart);
+  h->cbase = reinterpret_cast<uint64_t*>(h->ws + L.cbase);
+  h->off = reinterpret_cast<uint32_t*>(h->ws + L.off);
+  h->tile_src = reinterpret_cast<int32_t*>(h->ws + L.tile_src);
+  h->grid_p = int(std::min<int64_t>(div_up(h->n, kPThreads), int64_t(sm_count()) * 4));
+  if (h->grid_p > kMaxPartBlocks) h->grid_p = kMaxPartBlocks;
+  h->g_iter[0] = h->g_iter[1] = nullptr;
+  h->err = "ok";
+
+  // Algorithm 2, line 1, then the statistics of w_0 (LSE_0 becomes LSE_{t-1})
+  e = cudaMemsetAsync(h->tg, 0, sizeof(TargetDev), h->stream);
+  if (e == cudaSuccess) e = launch_state_init(h->st, h->n, 0, quant_shift(h->n), h->stream);
+  if (e == cudaSuccess)
+    e = launch_target_setup(h->tg, cfg->target, cfg->nu, cfg->mu_dev, cfg->sigma_dev, h->d, h->st, h->stream);
+  if (e == cudaSuccess) e = launch_particles(OP_INIT, particle_args(h), h->grid_p, h->stream);
+  if (e == cudaSuccess) e = launch_stats(h, 0, 1);
+  if (e != cudaSuccess) {
+    int r = cuda_fail(nullptr, e, "smc_init launch");
+    delete h;
+    return r;
+  }
+  *out = h;
+  return SMC_OK;
+}
+
+int smc_move(smc_sampler* h) {
+  if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, launch_begin(h->st, h->stream));
+  SMC_TRY(h, launch_particles(OP_MOVE, particle_args(h), h->grid_p, h->stream));
+  return SMC_OK;
+}
+
+int smc_reweight(smc_sampler* h) {
+  if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, launch_particles(OP_REWEIGHT, particle_args(h), h->grid_p, h->stream));
+  SMC_TRY(h, launch_stats(h, 0, 0));
+  return SMC_OK;
+}
+
+int smc_estimate(smc_sampler* h, double* mean_dev, double* cov_dev) {
+  if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  if (mean_dev) SMC_TRY(h, launch_copy_mean(h->st, mean_dev, h->d, h->stream));
+  if (cov_dev) {
+    SMC_TRY(h, cudaMemsetAsync(cov_dev, 0, sizeof(double) * h->d * h->d, h->stream));
+    SMC_TRY(h, launch_cov(particle_args(h), cov_dev, h->grid_p, h->stream));
+  }
+  return SMC_OK;
+}
+
+int smc_resample(smc_sampler* h, int32_t* ncopies_dev, int32_t* did_resample_dev) {
+  if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  if (ncopies_dev) SMC_TRY(h, launch_quant_scan(quant_args(h, 1, ncopies_dev), h->stream));
+  if (did_resample_dev)
+    SMC_TRY(h, cudaMemcpyAsync(did_resample_dev, &h->st->flag, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                               h->stream));
+  return SMC_OK;
+}
+
+int smc_redistribute(smc_sampler* h, const int32_t* ncopies_dev) {
+  if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  if (!ncopies_dev) return fail(h, SMC_EINVAL, "null ncopies");
+  NcScanArgs s{};
+  s.n = h->n;
+  s.ncopies = ncopies_dev;
+  s.part = h->qpart;
+  s.cbase = h->cbase;
+  s.off = h->off;
+  s.tile_src = h->tile_src;
+  s.nblocks = h->L.qblocks;
+  s.ntiles = h->L.ntiles;
+  s.st = h->st;
+  SMC_TRY(h, launch_nc_reduce(s, h->stream));
+  SMC_TRY(h, launch_nc_finalize(s, h->stream));
+  SMC_TRY(h, launch_nc_scan(s, h->stream));
+  SMC_TRY(h, launch_redistribute(redist_args(h, 1), h->stream));
+  SMC_TRY(h, launch_commit(h->st, h->d, 1, 0, h->stream));
+  return SMC_OK;
+}
+
+int smc_step(smc_sampler* h, int32_t k, double* mean_dev, double* cov_dev, smc_iter_stats* trace_dev,
+             double* fhat_dev) {
+  if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  if (k < 0) return fail(h, SMC_EINVAL, "k must be >= 0");
+  if (k == 0) return SMC_OK;
+  SMC_TRY(h, launch_step_setup(h->st, trace_dev, mean_dev, fhat_dev, cov_dev, h->stream));
+  const bool use_graph = h->stream != nullptr;
+  for (int32_t it = 0; it < k; ++it) {
+    const bool with_cov = cov_dev && it == k - 1;
+    if (use_graph) {
+      cudaGraphExec_t& g = h->g_iter[with_cov ? 1 : 0];
+      if (!g) SMC_TRY(h, build_graph(h, with_cov, &g));
+      SMC_TRY(h, cudaGraphLaunch(g, h->stream));
+    } else {
+      SMC_TRY(h, launch_iteration(h, with_cov));
+    }
+  }
+  return SMC_OK;
+}
+
+int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host, int32_t n_events) {
+  if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  if (n_events != 0 && n_events != 8) return fail(h, SMC_EINVAL, "n_events must be 0 or 8");
+  if (n_events && !events_host) return fail(h, SMC_EINVAL, "null events");
+  cudaStream_t s = h->stream;
+  auto rec = [&](int j) -> cudaError_t {
+    return n_events ? cudaEventRecord(static_cast<cudaEvent_t>(events_host[j]), s) : cudaSuccess;
+  };
+  SMC_TRY(h, launch_step_setup(h->st, nullptr, mean_dev, nullptr, nullptr, s));
+  const ParticleArgs a = particle_args(h);
+  const QuantArgs q = quant_args(h, 0, nullptr);
+  SMC_TRY(h, rec(0));
+  SMC_TRY(h, launch_begin(h->st, s));
+  SMC_TRY(h, launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, s));
+  SMC_TRY(h, rec(1));
+  SMC_TRY(h, launch_est_finalize(h->part, h->grid_p, h->d, h->st, 1, s));
+  SMC_TRY(h, rec(2));
+  SMC_TRY(h, launch_quant_reduce(q, s));
+  SMC_TRY(h, rec(3));
+  SMC_TRY(h, launch_quant_finalize(q, 0, s));
+  SMC_TRY(h, rec(4));
+  SMC_TRY(h, launch_quant_scan(q, s));
+  SMC_TRY(h, rec(5));
+  SMC_TRY(h, launch_redistribute(redist_args(h, 0), s));
+  SMC_TRY(h, rec(6));
+  SMC_TRY(h, launch_commit(h->st, h->d, 0, 1, s));
+  SMC_TRY(h, rec(7));
+  return SMC_OK;
+}
+
+int smc_sync(smc_sampler* h) {
+  if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, cudaStreamSynchronize(h->stream));
+  int32_t err = 0;
+  SMC_TRY(h, cudaMemcpy(&err, &h->st->err, sizeof err, cudaMemcpyDeviceToHost));
+  if (err) {
+    SMC_TRY(h, cudaMemset(&h->st->err, 0, sizeof err));
+    static const char* names[] = {"ok", "invalid argument on the device", "out of memory", "cuda",
+                                  "a bounded device wait timed out", "non-finite log-weights"};
+    return fail(h, err, err >= 0 && err <= 5 ? names[err] : "device error");
+  }
+  return SMC_OK;
+}
+
+int smc_read_stats(smc_sampler* h, smc_iter_stats* out_host) {
+  if (!h || !out_host) return fail(h, SMC_EINVAL, "null argument");
+  SMC_TRY(h, cudaStreamSynchronize(h->stream));
+  SMC_TRY(h, cudaMemcpy(out_host, &h->st->last, sizeof(smc_iter_stats), cudaMemcpyDeviceToHost));
+  return SMC_OK;
+}
+
+int smc_current(smc_sampler* h, int32_t* which_host) {
+  if (!h || !which_host) return fail(h, SMC_EINVAL, "null argument");
+  SMC_TRY(h, cudaStreamSynchronize(h->stream));
+  SMC_TRY(h, cudaMemcpy(which_host, &h->st->cur, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return SMC_OK;
+}
+
+int smc_destroy(smc_sampler* h) {
+  if (!h) return SMC_OK;
+  for (auto& g : h->g_iter)
+    if (g) cudaGraphExecDestroy(g);
+  delete h;
+  return SMC_OK;
+}
+
+const char* smc_last_error(const smc_sampler* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+// ------------------------------------------------------------------ stateless
+namespace {
+struct RawLayout {
+  size_t st, part, qpart, cbase, off, tile_src, total;
+  int qblocks, ntiles;
+};
+RawLayout raw_layout(int64_t n) {
+  RawLayout L{};
+  L.qblocks = int(div_up(n, kQTile));
+  L.ntiles = int(div_up(n, kRTile));
+  size_t p = 0;
+  L.st = p;
+  p = align_up(p + sizeof(DevState));
+  L.part = p;
+  p = align_up(p + size_t(L.qblocks) * 2 * sizeof(double));
+  L.qpart = p;
+  p = align_up(p + size_t(L.qblocks) * 5 * sizeof(uint64_t));
+  L.cbase = p;
+  p = align_up(p + size_t(L.qblocks) * sizeof(uint64_t));
+  L.off = p;
+  p = align_up(p + size_t(n + 1) * sizeof(uint32_t));
+  L.tile_src = p;
+  p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
+  L.total = p;
+  return L;
+}
+}  // namespace
+
+int smc_redistribute_ws_bytes(int64_t n, size_t* bytes) {
+  if (n < 1 || n > 2147483647LL || !bytes) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
+  *bytes = raw_layout(n).total;
+  return SMC_OK;
+}
+
+int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
+                         void* out_dev, void* ws_dev, smc_stream_t stream) {
+  if (n < 1 || n > 2147483647LL) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
+  if (row_bytes < 4 || row_bytes % 4) return fail(nullptr, SMC_EINVAL, "row_bytes must be a positive multiple of 4");
+  if (!ncopies_dev || !in_dev || !out_dev || !ws_dev) return fail(nullptr, SMC_EINVAL, "null pointer");
+  if (!aligned(ws_dev, kAlign)) return fail(nullptr, SMC_EINVAL, "workspace must be 256-byte aligned");
+  const size_t va = row_bytes % 16 == 0 ? 16 : (row_bytes % 8 == 0 ? 8 : 4);
+  if (!aligned(in_dev, va) || !aligned(out_dev, va)) return fail(nullptr, SMC_EINVAL, "rows misaligned");
+  const RawLayout L = raw_layout(n);
+  char* ws = static_cast<char*>(ws_dev);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  DevState* st = reinterpret_cast<DevState*>(ws + L.st);
+  NcScanArgs a{};
+  a.n = n;
+  a.ncopies = ncopies_dev;
+  a.part = reinterpret_cast<uint64_t*>(ws + L.qpart);
+  a.cbase = reinterpret_cast<uint64_t*>(ws + L.cbase);
+  a.off = reinterpret_cast<uint32_t*>(ws + L.off);
+  a.tile_src = reinterpret_cast<int32_t*>(ws + L.tile_src);
+  a.nblocks = L.qblocks;
+  a.ntiles = L.ntiles;
+  a.st = st;
+  RedistArgs r{};
+  r.n = n;
+  r.row_bytes = row_bytes;
+  r.lp_bytes = 0;
+  r.off = a.off;
+  r.tile_src = a.tile_src;
+  r.ntiles = L.ntiles;
+  r.force = 1;
+  r.x_in[0] = r.x_in[1] = in_dev;
+  r.x_out[0] = r.x_out[1] = out_dev;
+  r.logw = nullptr;
+  r.st = st;
+  r.stateful = 0;
+  cudaError_t e = cudaMemsetAsync(&st->err, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = launch_nc_reduce(a, s);
+  if (e == cudaSuccess) e = launch_nc_finalize(a, s);
+  if (e == cudaSuccess) e = launch_nc_scan(a, s);
+  if (e == cudaSuccess) e = launch_redistribute(r, s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "smc_redistribute_raw");
+  return SMC_OK;
+}
+
+int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t t, int32_t mode,
+                     int32_t* ncopies_dev, smc_iter_stats* stats_dev, void* ws_dev, smc_stream_t stream) {
+  if (n < 1 || n > 2147483647LL) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
+  if (!logw_dev || !ncopies_dev || !ws_dev) return fail(nullptr, SMC_EINVAL, "null pointer");
+  if (mode < 0 || mode > 2) return fail(nullptr, SMC_EINVAL, "bad mode");
+  if (!aligned(ws_dev, kAlign)) return fail(nullptr, SMC_EINVAL, "workspace must be 256-byte aligned");
+  cudaError_t e = upload_expfx_table();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "upload_expfx_table");
+  const RawLayout L = raw_layout(n);
+  char* ws = static_cast<char*>(ws_dev);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  DevState* st = reinterpret_cast<DevState*>(ws + L.st);
+  double* part = reinterpret_cast<double*>(ws + L.part);
+  QuantArgs q{};
+  q.n = n;
+  q.logw = logw_dev;
+  q.seed = seed;
+  q.mode = mode;
+  q.force = 1;
+  q.qpart = reinterpret_cast<uint64_t*>(ws + L.qpart);
+  q.cbase = reinterpret_cast<uint64_t*>(ws + L.cbase);
+  q.off = reinterpret_cast<uint32_t*>(ws + L.off);
+  q.ncopies = ncopies_dev;
+  q.tile_src = reinterpret_cast<int32_t*>(ws + L.tile_src);
+  q.nblocks = L.qblocks;
+  q.ntiles = L.ntiles;
+  q.st = st;
+  q.stats_out = stats_dev;
+  e = launch_state_init(st, n, int64_t(t), quant_shift(n), s);
+  if (e == cudaSuccess) e = launch_max_logw(logw_dev, n, part, L.qblocks, st, s);
+  if (e == cudaSuccess) e = launch_est_finalize(part, L.qblocks, 0, st, 0, s);
+  if (e == cudaSuccess) e = launch_quant_reduce(q, s);
+  if (e == cudaSuccess) e = launch_quant_finalize(q, 0, s);
+  if (e == cudaSuccess) e = launch_quant_scan(q, s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "smc_resample_raw");
+  return SMC_OK;
+}
+
+int smc_ws_status(void* ws_dev, smc_stream_t stream) {
+  if (!ws_dev) return fail(nullptr, SMC_EINVAL, "null workspace");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "smc_ws_status");
+  DevState* st = reinterpret_cast<DevState*>(ws_dev);
+  int32_t err = 0;
+  e = cudaMemcpy(&err, &st->err, sizeof err, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "smc_ws_status");
+  if (err) {
+    cudaMemset(&st->err, 0, sizeof err);
+    return fail(nullptr, err, "device-side error in stateless call");
+  }
+  return SMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,358 @@
+// smc_internal.cuh -- device-side building blocks of libsmc.so (sm_103a).
+//
+// Shared by the kernel translation units of the library only.  Contents:
+//  * DevState: the sampler's device-resident control block (iteration t,
+//    current ping-pong buffer, resampling decision, error word, statistics).
+//  * Philox4x64-10 (Salmon et al., SC'11) for counter-based normals keyed by
+//    (seed, iteration, particle).
+//  * IEEE-exact log and sincos(2 pi a) for the FP64 Box-Muller transform: only
+//    correctly rounded basic operations, each written with an explicit
+//    rounding intrinsic so nvcc cannot contract or reorder them.
+//  * The integer fixed-point exponential that quantises the weights before
+//    systematic resampling, and the 128-bit helpers around it.
+//  * Warp / block reductions and scans.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/smc.h"
+
+namespace smc {
+
+typedef unsigned __int128 u128;
+
+// ---------------------------------------------------------------- constants
+constexpr int kMaxD = 32;
+constexpr int kQTile = 4096;          // elements per block of the quantise / scan passes
+constexpr int kQThreads = 256;        // 16 consecutive elements per thread
+constexpr int kQItems = kQTile / kQThreads;
+constexpr int kRTile = 4096;          // output rows per block of the redistribute copy
+constexpr int kRThreads = 256;
+constexpr int kPThreads = 256;        // particle kernels (init / move / reweight)
+constexpr int kFinThreads = 1024;     // single-block finalisers
+
+// Random-stream purposes (third Philox counter word = purpose << 32 | block).
+constexpr uint32_t kPurposeInit = 1;
+constexpr uint32_t kPurposeMove = 2;
+constexpr uint32_t kPurposeResample = 3;
+
+// ---------------------------------------------------------------- device state
+struct alignas(256) DevState {
+  int64_t t;            // iteration index (0 after smc_init)
+  int32_t cur;          // 0: x/logpi hold the particles, 1: the _alt buffers
+  int32_t flag;         // resampling decision of iteration t
+  int32_t err;          // first smc_status recorded on the device, 0 if none
+  int32_t F;            // fixed-point scale of the weights
+  int32_t L;            // bit length of S (ncopies division)
+  int32_t pad0;
+  double m;             // max_i log w
+  double lse;           // LSE_t
+  double lse_prev;      // LSE_{t-1} (0 after a reset)
+  double logc;          // log c_t
+  double ess;           // N_eff
+  double reset_logw;    // -log N
+  uint64_t S, U;        // sum W, systematic offset
+  uint64_t sw2_lo, sw2_hi, se_lo, se_hi;
+  uint64_t recip;       // floor(2^(63+L) / S)
+  // recycling (eq. (6)): running log-max of log c_t and the scaled sums
+  double rc_max;
+  double rc_den;
+  double rc_num[kMaxD];
+  double mean[kMaxD];   // f_t of the current iteration
+  double est_s;         // sum_i exp(log w_i - m) behind mean (estimate kernel)
+  // output pointers of the running smc_step (set before a graph replay)
+  smc_iter_stats* trace;
+  int64_t trace_t0;
+  double* mean_out;
+  double* fhat_out;
+  double* cov_out;
+  int32_t want_cov;
+  int32_t pad1;
+  unsigned long long survivors;  // particles with ncopies > 0 in the current resampling
+  smc_iter_stats last;  // statistics of the last finalised iteration
+};
+
+__device__ __forceinline__ void record_error(DevState* st, int code) {
+  atomicCAS(&st->err, 0, code);
+}
+
+// ---------------------------------------------------------------- Philox4x64-10
+struct P4 {
+  uint64_t v[4];
+};
+
+__device__ __forceinline__ P4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                     uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
+    const uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+  P4 o;
+  o.v[0] = c0;
+  o.v[1] = c1;
+  o.v[2] = c2;
+  o.v[3] = c3;
+  return o;
+}
+
+// Block b of the stream of particle i at iteration t: counter (i, t, p<<32|b, 0), key (seed, 0).
+__device__ __forceinline__ P4 stream_block(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i,
+                                           uint32_t b) {
+  return philox(i, t, (uint64_t(purpose) << 32) | b, 0, seed, 0);
+}
+
+// ---------------------------------------------------------------- exact FP64 helpers
+// ln 2 split so that e * kLn2Hi is exact for |e| < 2^11.
+__device__ __forceinline__ double ln2_hi() { return __longlong_as_double(0x3FE62E42FEE00000ll); }
+__device__ __forceinline__ double ln2_lo() { return __longlong_as_double(0x3DEA39EF35793C76ll); }
+
+// log(u), u finite, normal, > 0: u = 2^e m, m in [sqrt(1/2), sqrt(2)),
+// log m = 2 atanh(s), s = (m-1)/(m+1), series to s^22.
+__device__ __forceinline__ double det_log(double u) {
+  const long long b = __double_as_longlong(u);
+  int e = int((b >> 52) & 0x7ff) - 1023;
+  double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+  if (m > __longlong_as_double(0x3FF6A09E667F3BCDll)) {
+    m = __dmul_rn(m, 0.5);
+    e += 1;
+  }
+  const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+  const double s2 = __dmul_rn(s, s);
+  double p = 1.0 / 23.0;
+  p = __fma_rn(p, s2, 1.0 / 21.0);
+  p = __fma_rn(p, s2, 1.0 / 19.0);
+  p = __fma_rn(p, s2, 1.0 / 17.0);
+  p = __fma_rn(p, s2, 1.0 / 15.0);
+  p = __fma_rn(p, s2, 1.0 / 13.0);
+  p = __fma_rn(p, s2, 1.0 / 11.0);
+  p = __fma_rn(p, s2, 1.0 / 9.0);
+  p = __fma_rn(p, s2, 1.0 / 7.0);
+  p = __fma_rn(p, s2, 1.0 / 5.0);
+  p = __fma_rn(p, s2, 1.0 / 3.0);
+  p = __fma_rn(p, s2, 1.0);
+  const double logm = __dmul_rn(__dmul_rn(2.0, s), p);
+  const double de = double(e);
+  return __fma_rn(de, ln2_hi(), __fma_rn(de, ln2_lo(), logm));
+}
+
+// sin and cos of 2 pi v 2^-53 (0 <= v < 2^53): exact quarter-turn reduction on
+// the integer, Taylor series to degree 17 / 18 on [-pi/4, pi/4].
+__device__ __forceinline__ void det_sincos2pi(uint64_t v, double* s_out, double* c_out) {
+  const uint64_t q = (v + (1ull << 50)) >> 51;
+  const long long vr = (long long)v - (long long)(q << 51);
+  const double x = __dmul_rn(double(vr), 0x1p-53);
+  const double t = __dmul_rn(x, __longlong_as_double(0x401921FB54442D18ll));  // 2 pi
+  const double t2 = __dmul_rn(t, t);
+  double ps = -1.0 / 121645100408832000.0;
+  ps = __fma_rn(ps, t2, 1.0 / 355687428096000.0);
+  ps = __fma_rn(ps, t2, -1.0 / 1307674368000.0);
+  ps = __fma_rn(ps, t2, 1.0 / 6227020800.0);
+  ps = __fma_rn(ps, t2, -1.0 / 39916800.0);
+  ps = __fma_rn(ps, t2, 1.0 / 362880.0);
+  ps = __fma_rn(ps, t2, -1.0 / 5040.0);
+  ps = __fma_rn(ps, t2, 1.0 / 120.0);
+  ps = __fma_rn(ps, t2, -1.0 / 6.0);
+  ps = __fma_rn(ps, t2, 1.0);
+  const double sn = __dmul_rn(t, ps);
+  double pc = 1.0 / 6402373705728000.0;
+  pc = __fma_rn(pc, t2, -1.0 / 20922789888000.0);
+  pc = __fma_rn(pc, t2, 1.0 / 87178291200.0);
+  pc = __fma_rn(pc, t2, -1.0 / 479001600.0);
+  pc = __fma_rn(pc, t2, 1.0 / 3628800.0);
+  pc = __fma_rn(pc, t2, -1.0 / 40320.0);
+  pc = __fma_rn(pc, t2, 1.0 / 720.0);
+  pc = __fma_rn(pc, t2, -1.0 / 24.0);
+  pc = __fma_rn(pc, t2, 1.0 / 2.0);
+  const double cs = __fma_rn(-pc, t2, 1.0);
+  switch (q & 3) {
+    case 0: *s_out = sn; *c_out = cs; break;
+    case 1: *s_out = cs; *c_out = -sn; break;
+    case 2: *s_out = -sn; *c_out = -cs; break;
+    default: *s_out = -cs; *c_out = sn; break;
+  }
+}
+
+// D standard normals (FP64 path): pair p uses stream words 2p, 2p+1 (top 53
+// bits each); u1 = 1 - a, r = sqrt(-2 log u1), (z0, z1) = r (cos, sin)(2 pi b).
+template <int DMAX>
+__device__ __forceinline__ void normals_f64(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, int d,
+                                            double (&z)[DMAX]) {
+#pragma unroll
+  for (int blk = 0; blk < (DMAX + 3) / 4; ++blk) {
+    if (4 * blk < d) {
+      const P4 w = stream_block(seed, t, purpose, i, blk);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = 2 * blk + h;  // pair index
+        if (2 * p < d && 2 * p < DMAX) {
+          const uint64_t va = w.v[2 * h] >> 11, vb = w.v[2 * h + 1] >> 11;
+          const double u1 = __dmul_rn(double((1ull << 53) - va), 0x1p-53);
+          const double r = __dsqrt_rn(__dmul_rn(-2.0, det_log(u1)));
+          double sn, cs;
+          det_sincos2pi(vb, &sn, &cs);
+          z[2 * p] = __dmul_rn(r, cs);
+          if (2 * p + 1 < DMAX) z[2 * p + 1] = __dmul_rn(r, sn);
+        }
+      }
+    }
+  }
+}
+
+// D standard normals (FP32 path): pair p uses 64-bit word p, its low and high
+// 32-bit halves giving 24-bit uniforms a, b.
+template <int DMAX>
+__device__ __forceinline__ void normals_f32(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, int d,
+                                            float (&z)[DMAX]) {
+#pragma unroll
+  for (int blk = 0; blk < (DMAX + 7) / 8; ++blk) {
+    if (8 * blk < d) {
+      const P4 w = stream_block(seed, t, purpose, i, blk);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int p = 4 * blk + h;
+        if (2 * p < d && 2 * p < DMAX) {
+          const uint32_t h0 = uint32_t(w.v[h]), h1 = uint32_t(w.v[h] >> 32);
+          const float u1 = float((1u << 24) - (h0 >> 8)) * 0x1p-24f;
+          const float b2 = float(h1 >> 8) * 0x1p-23f;  // 2b, exact
+          const float r = sqrtf(-2.0f * logf(u1));
+          float sn, cs;
+          sincospif(b2, &sn, &cs);
+          z[2 * p] = r * cs;
+          if (2 * p + 1 < DMAX) z[2 * p + 1] = r * sn;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- fixed-point exp
+// E(y) ~= 2^62 exp(y) for y <= 0, an integer in [0, 2^62]:
+//   a = -y; A = floor(a 2^57) from the bits of a; Z = A round(log2(e) 2^62)
+//   (z = a log2 e = Z 2^-119); k = integer part, f = 64 fraction bits;
+//   2^-f = T[top 6 bits of f] * exp(-g ln 2) for the low 58 bits g;
+//   exp(-h) = 1 - h(1 - h/2(1 - h/3 ...)) to degree 8 in 2^63 fixed point
+//   with floor division by each k;  E = (T[j] P 2^-64) >> k.
+// T (64 entries, ~2^63 2^(-j/64)) is built on the host from integer square
+// roots and lives in shared memory while a kernel uses it.
+__device__ __forceinline__ uint64_t expfx(double y, const uint64_t* __restrict__ T) {
+  const double a = -y;
+  if (!(a < 44.0)) return 0;
+  const uint64_t bits = (uint64_t)__double_as_longlong(a);
+  const int e = int((bits >> 52) & 0x7ff);
+  uint64_t A = 0;
+  if (e != 0) {
+    const uint64_t mant = (bits & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = e - 1018;
+    A = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0);
+  }
+  const uint64_t L2E = 0x5C551D94AE0BF85Eull;  // round(log2(e) 2^62)
+  const uint64_t LN2 = 0xB17217F7D1CF79ACull;  // round(ln(2) 2^64)
+  const uint64_t zlo = A * L2E, zhi = __umul64hi(A, L2E);
+  const unsigned k = unsigned(zhi >> 55);
+  const uint64_t f = (zhi << 9) | (zlo >> 55);
+  const unsigned j = unsigned(f >> 58);
+  const uint64_t g = f & ((1ull << 58) - 1);
+  const uint64_t H = __umul64hi(g << 6, LN2);
+  uint64_t P = 1ull << 63;
+#pragma unroll
+  for (unsigned kk = 8; kk >= 1; --kk) {
+    const uint64_t hp = __umul64hi(H, P) >> 6;
+    P = (1ull << 63) - hp / kk;
+  }
+  return __umul64hi(T[j], P) >> k;
+}
+
+// floor(X / S) for X < 2^(L+33), S in [2^(L-1), 2^L), with R = floor(2^(63+L)/S):
+// estimate from the top bits, then correct by exact 128-bit remainders.
+__device__ __forceinline__ uint64_t div_by_S(u128 X, uint64_t S, int L, uint64_t R) {
+  const uint64_t xs = uint64_t(X >> (L - 1));
+  uint64_t q = __umul64hi(xs, R);
+  u128 qs = u128(q) * S;
+  // q never exceeds floor(X/S); bounded correction loop
+#pragma unroll 1
+  for (int it = 0; it < 4 && qs + S <= X; ++it) {
+    ++q;
+    qs += S;
+  }
+  return q;
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {
+  const uint64_t lo = __shfl_xor_sync(0xffffffffu, uint64_t(v), o);
+  const uint64_t hi = __shfl_xor_sync(0xffffffffu, uint64_t(v >> 64), o);
+  return (u128(hi) << 64) | lo;
+}
+
+__device__ __forceinline__ u128 warp_sum_u128(u128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor_u128(v, o);
+  return v;
+}
+
+// Inclusive warp scan (Hillis-Steele) of 64-bit values.
+__device__ __forceinline__ uint64_t warp_incl_scan_u64(uint64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+__device__ __forceinline__ int warp_incl_max_i32(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = max(v, n);
+  }
+  return v;
+}
+
+// Exclusive block scan of one 64-bit value per thread; returns the exclusive
+// prefix and writes the block total.  scratch: blockDim/32 + 1 words.
+__device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t* scratch, uint64_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint64_t incl = warp_incl_scan_u64(v);
+  if (lane == 31) scratch[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint64_t s = lane < nw ? scratch[lane] : 0;
+    const uint64_t si = warp_incl_scan_u64(s);
+    if (lane < nw) scratch[lane] = si - s;
+    if (lane == nw - 1) scratch[32] = si;
+  }
+  __syncthreads();
+  const uint64_t r = scratch[wid] + incl - v;
+  *total = scratch[32];
+  __syncthreads();
+  return r;
+}
+
+}  // namespace smc

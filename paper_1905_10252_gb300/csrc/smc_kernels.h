@@ -1,0 +1,123 @@
+// smc_kernels.h -- host-visible launch interface between the C-ABI layer
+// (smc_api.cu) and the kernel translation units of libsmc.so.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/smc.h"
+
+namespace smc {
+
+struct DevState;
+constexpr int kTgtMaxD = 32;
+
+// Device copy of the target: Gaussian mean, Cholesky factor L (FP64 path),
+// its inverse P and FP32 copies (FP32 path), Student-t nu.
+struct alignas(256) TargetDev {
+  int32_t kind;
+  int32_t d;
+  double nu;
+  double mu[kTgtMaxD];
+  float muf[kTgtMaxD];
+  double L[kTgtMaxD * kTgtMaxD];
+  double P[kTgtMaxD * kTgtMaxD];
+  float Pf[kTgtMaxD * kTgtMaxD];
+};
+
+enum { OP_INIT = 0, OP_MOVE = 1, OP_REWEIGHT = 2, OP_MOVE_REWEIGHT = 3 };
+
+struct ParticleArgs {
+  int64_t n;
+  int32_t d;
+  int32_t dtype;
+  int32_t kind;
+  int32_t pad;
+  uint64_t seed;
+  double step;
+  double init_scale;
+  void* x[2];
+  void* logpi[2];
+  double* logw;
+  double* part;  // per-block partials (2 + d doubles each)
+  const TargetDev* tg;
+  DevState* st;
+};
+
+struct QuantArgs {
+  int64_t n;
+  const double* logw;
+  uint64_t seed;
+  int32_t mode;        // smc_resample_mode
+  int32_t force;       // scan even if the decision is "no resample"
+  uint64_t* qpart;     // per-block {sumW, sw2 lo, sw2 hi, sumE lo, sumE hi}
+  uint64_t* cbase;     // exclusive prefix of the block sums of W
+  uint32_t* off;       // N + 1 exclusive offsets
+  int32_t* ncopies;    // optional output
+  int32_t* tile_src;   // first source row of each redistribute tile
+  int32_t nblocks;     // quantise blocks
+  int32_t ntiles;      // redistribute tiles
+  DevState* st;
+  smc_iter_stats* stats_out;  // optional single record (stateless path)
+};
+
+struct RedistArgs {
+  int64_t n;
+  int32_t row_bytes;
+  int32_t lp_bytes;      // 0: no log pi payload
+  const uint32_t* off;
+  const int32_t* tile_src;
+  int32_t ntiles;
+  int32_t force;         // copy even if the decision is "no resample"
+  const void* x_in[2];   // indexed by the current buffer (stateful) or [0]
+  void* x_out[2];
+  const void* lp_in[2];
+  void* lp_out[2];
+  double* logw;          // reset to reset_logw (may be NULL)
+  double reset_logw;
+  DevState* st;
+  int32_t stateful;      // 1: choose buffers by st->cur, honour st->flag / st->err
+  int32_t pad;
+};
+
+struct NcScanArgs {
+  int64_t n;
+  const int32_t* ncopies;
+  uint64_t* part;       // per-block sums
+  uint64_t* cbase;      // exclusive block prefixes
+  uint32_t* off;
+  int32_t* tile_src;
+  int32_t nblocks;
+  int32_t ntiles;
+  DevState* st;
+};
+
+size_t devstate_bytes();
+
+cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double* mu, const double* sigma, int d,
+                                DevState* st, cudaStream_t s);
+cudaError_t launch_zero_cov(DevState* st, int d, cudaStream_t s);
+cudaError_t launch_est_finalize(const double* part, int nb, int d, DevState* st, int write_mean_out,
+                                cudaStream_t s);
+cudaError_t launch_cov(const ParticleArgs& a, double* cov, int grid, cudaStream_t s);
+cudaError_t launch_begin(DevState* st, cudaStream_t s);
+cudaError_t launch_commit(DevState* st, int d, int force_flip, int recycle, cudaStream_t s);
+cudaError_t launch_copy_mean(const DevState* st, double* out, int d, cudaStream_t s);
+cudaError_t launch_step_setup(DevState* st, smc_iter_stats* trace, double* mean_out, double* fhat_out,
+                              double* cov_out, cudaStream_t s);
+
+// k_resample.cu
+cudaError_t upload_expfx_table();  // once per device, outside stream capture
+cudaError_t launch_max_logw(const double* logw, int64_t n, double* part, int nb, DevState* st, cudaStream_t s);
+cudaError_t launch_quant_reduce(const QuantArgs& a, cudaStream_t s);
+cudaError_t launch_quant_finalize(const QuantArgs& a, int set_lse_prev, cudaStream_t s);
+cudaError_t launch_quant_scan(const QuantArgs& a, cudaStream_t s);
+cudaError_t launch_nc_reduce(const NcScanArgs& a, cudaStream_t s);
+cudaError_t launch_nc_finalize(const NcScanArgs& a, cudaStream_t s);
+cudaError_t launch_nc_scan(const NcScanArgs& a, cudaStream_t s);
+cudaError_t launch_redistribute(const RedistArgs& a, cudaStream_t s);
+cudaError_t launch_state_init(DevState* st, int64_t n, int64_t t, int F, cudaStream_t s);
+
+}  // namespace smc

@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs shared by the tests, the bench and the oracle legs.
+"""Seeded synthetic inputs shared by the tests, the bench and the CPU baseline.
 
 This module holds no arithmetic of the SMC method: it only draws problem
 instances, particle clouds, log-weights and copy-count vectors with numpy's own

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of libsmc.so (include/smc.h), same names as the C-ABI.
+
+Only argument marshalling lives here: torch tensors supply device memory and
+streams, every step of the sampler runs in the library's CUDA kernels.  There
+is no CPU fallback: ``lib()`` raises when libsmc.so has not been built or no
+CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import torch
+
+_LIB_PATH = Path(__file__).resolve().with_name("libsmc.so")
+
+SMC_OK, SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA, SMC_ETIMEOUT, SMC_ENONFINITE = range(6)
+SMC_F32, SMC_F64 = 1, 2
+SMC_GAUSS, SMC_LOGISTIC, SMC_STUDENT_T = 1, 2, 3
+RESAMPLE_ESS, RESAMPLE_ALWAYS, RESAMPLE_NEVER = 0, 1, 2
+
+EXPORTED = [
+    "smc_workspace_bytes", "smc_init", "smc_move", "smc_reweight", "smc_estimate", "smc_resample",
+    "smc_redistribute", "smc_step", "smc_step_profile", "smc_sync", "smc_read_stats", "smc_current", "smc_destroy",
+    "smc_last_error", "smc_redistribute_ws_bytes", "smc_redistribute_raw", "smc_resample_raw", "smc_ws_status",
+]
+
+
+class SmcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"smc error {code}: {msg}")
+        self.code = code
+
+
+class smc_config(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("d", C.c_int32), ("dtype", C.c_int32), ("seed", C.c_uint64),
+        ("target", C.c_int32), ("resample_mode", C.c_int32), ("step", C.c_double), ("init_scale", C.c_double),
+        ("mu_dev", C.c_void_p), ("sigma_dev", C.c_void_p), ("X_dev", C.c_void_p), ("y_dev", C.c_void_p),
+        ("m", C.c_int32), ("reserved", C.c_int32), ("prior_var", C.c_double), ("nu", C.c_double),
+    ]
+
+
+class smc_iter_stats(C.Structure):
+    _fields_ = [("lse", C.c_double), ("logc", C.c_double), ("ess", C.c_double), ("max_logw", C.c_double),
+                ("resampled", C.c_int64), ("t", C.c_int64), ("survivors", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+STATS_FIELDS = [k for k, _ in smc_iter_stats._fields_]
+STATS_WORDS = len(STATS_FIELDS)
+
+_lib = None
+
+
+def lib_path() -> Path:
+    return _LIB_PATH
+
+
+def load_library() -> C.CDLL:
+    """Loads libsmc.so without touching the GPU (used to check the exports)."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_1905_10252_gb300/build.py "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(str(_LIB_PATH))
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def lib() -> C.CDLL:
+    if not torch.cuda.is_available():
+        raise RuntimeError("libsmc needs a CUDA device; there is no CPU fallback")
+    return load_library()
+
+
+def _declare(L: C.CDLL) -> None:
+    vp, i32, i64, u64, dbl, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_size_t
+    L.smc_workspace_bytes.argtypes = [C.POINTER(smc_config), C.POINTER(sz)]
+    L.smc_init.argtypes = [C.POINTER(vp), C.POINTER(smc_config), vp, vp, vp, vp, vp, vp, sz, vp]
+    for name in ("smc_move", "smc_reweight", "smc_sync", "smc_destroy"):
+        getattr(L, name).argtypes = [vp]
+    L.smc_estimate.argtypes = [vp, vp, vp]
+    L.smc_resample.argtypes = [vp, vp, vp]
+    L.smc_redistribute.argtypes = [vp, vp]
+    L.smc_step.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.smc_step_profile.argtypes = [vp, vp, C.POINTER(vp), i32]
+    L.smc_read_stats.argtypes = [vp, C.POINTER(smc_iter_stats)]
+    L.smc_current.argtypes = [vp, C.POINTER(i32)]
+    L.smc_last_error.argtypes = [vp]
+    L.smc_last_error.restype = C.c_char_p
+    L.smc_redistribute_ws_bytes.argtypes = [i64, C.POINTER(sz)]
+    L.smc_redistribute_raw.argtypes = [i64, i32, vp, vp, vp, vp, vp]
+    L.smc_resample_raw.argtypes = [i64, vp, u64, u64, i32, vp, vp, vp, vp]
+    L.smc_ws_status.argtypes = [vp, vp]
+    for name in EXPORTED:
+        if name != "smc_last_error":
+            getattr(L, name).restype = C.c_int
+
+
+def _check(rc: int, handle=None) -> None:
+    if rc != SMC_OK:
+        msg = lib().smc_last_error(handle).decode(errors="replace")
+        raise SmcError(rc, msg)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+def _alloc_ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------- stateless
+def smc_redistribute_ws_bytes(n: int) -> int:
+    out = C.c_size_t()
+    _check(lib().smc_redistribute_ws_bytes(int(n), C.byref(out)))
+    return out.value
+
+
+def smc_redistribute_raw(ncopies: torch.Tensor, x_in: torch.Tensor, x_out: torch.Tensor | None = None,
+                         ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Algorithm 5 on the rows of x_in (any dtype); returns x_out."""
+    n = ncopies.numel()
+    if x_in.shape[0] != n:
+        raise ValueError("x_in must have one row per ncopies entry")
+    if x_out is None:
+        x_out = torch.empty_like(x_in)
+    if ws is None:
+        ws = _alloc_ws(smc_redistribute_ws_bytes(n), x_in.device)
+    row_bytes = x_in[0].numel() * x_in.element_size() if n else 0
+    _check(lib().smc_redistribute_raw(n, row_bytes, _ptr(ncopies), _ptr(x_in), _ptr(x_out), _ptr(ws),
+                                      _stream_ptr(stream)))
+    return x_out
+
+
+def smc_resample_raw(logw: torch.Tensor, seed: int, t: int, mode: int = RESAMPLE_ESS,
+                     ncopies: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None,
+                     stats: torch.Tensor | None = None):
+    """Algorithm 4, line 1 on logw (float64).  Returns (ncopies int32, stats tensor of 6 x 8 bytes)."""
+    n = logw.numel()
+    if logw.dtype != torch.float64:
+        raise ValueError("logw must be float64")
+    if ncopies is None:
+        ncopies = torch.empty(n, dtype=torch.int32, device=logw.device)
+    if ws is None:
+        ws = _alloc_ws(smc_redistribute_ws_bytes(n), logw.device)
+    if stats is None:
+        stats = torch.zeros(STATS_WORDS, dtype=torch.float64, device=logw.device)
+    _check(lib().smc_resample_raw(n, _ptr(logw), int(seed), int(t), int(mode), _ptr(ncopies), _ptr(stats),
+                                  _ptr(ws), _stream_ptr(stream)))
+    return ncopies, stats
+
+
+def decode_stats(stats: torch.Tensor) -> dict:
+    """One smc_iter_stats record (6 x 8 bytes) as a dict."""
+    raw = stats.detach().cpu().contiguous()
+    b = raw.numpy().tobytes()[: C.sizeof(smc_iter_stats)]
+    return smc_iter_stats.from_buffer_copy(b).as_dict()
+
+
+def smc_ws_status(ws: torch.Tensor, stream=None) -> int:
+    return int(lib().smc_ws_status(_ptr(ws), _stream_ptr(stream)))
+
+
+# ----------------------------------------------------------------- sampler
+class Sampler:
+    """Owns the device buffers of one sampler and a libsmc handle.
+
+    target='gauss' needs mu [D] and sigma [D, D]; target='student_t' needs mu
+    (scalar) and nu.  dtype is torch.float32 or torch.float64 (particle state).
+    """
+
+    def __init__(self, n: int, d: int, *, dtype=torch.float32, seed: int = 0, target: str = "gauss",
+                 mu=None, sigma=None, nu: float = 0.0, step: float = 0.5, init_scale: float = 2.0,
+                 resample_mode: int = RESAMPLE_ESS, device="cuda", stream: torch.cuda.Stream | None = None):
+        L = lib()
+        self.n, self.d, self.dtype = int(n), int(d), dtype
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        cur = torch.cuda.current_stream(self.device)
+        kind = {"gauss": SMC_GAUSS, "student_t": SMC_STUDENT_T}[target]
+        self.mu = torch.as_tensor(mu, dtype=torch.float64).reshape(-1).to(self.device)
+        self.sigma = (torch.as_tensor(sigma, dtype=torch.float64).reshape(d, d).contiguous().to(self.device)
+                      if sigma is not None else None)
+        cfg = smc_config()
+        cfg.n, cfg.d = self.n, self.d
+        cfg.dtype = SMC_F64 if dtype == torch.float64 else SMC_F32
+        cfg.seed, cfg.target, cfg.resample_mode = int(seed), kind, int(resample_mode)
+        cfg.step, cfg.init_scale, cfg.nu = float(step), float(init_scale), float(nu)
+        cfg.mu_dev = self.mu.data_ptr()
+        cfg.sigma_dev = self.sigma.data_ptr() if self.sigma is not None else None
+        self.cfg = cfg
+        nbytes = C.c_size_t()
+        _check(L.smc_workspace_bytes(C.byref(cfg), C.byref(nbytes)))
+        dev = self.device
+        self.x = torch.empty(self.n, self.d, dtype=dtype, device=dev)
+        self.x_alt = torch.empty_like(self.x)
+        self.logw = torch.empty(self.n, dtype=torch.float64, device=dev)
+        self.logpi = torch.empty(self.n, dtype=dtype, device=dev)
+        self.logpi_alt = torch.empty_like(self.logpi)
+        self.ws = _alloc_ws(nbytes.value, dev)
+        self.stream.wait_stream(cur)
+        h = C.c_void_p()
+        rc = L.smc_init(C.byref(h), C.byref(cfg), _ptr(self.x), _ptr(self.x_alt), _ptr(self.logw),
+                        _ptr(self.logpi), _ptr(self.logpi_alt), _ptr(self.ws), nbytes.value,
+                        self.stream.cuda_stream or None)
+        _check(rc, None)
+        self.h = h
+        self._done()
+
+    # every call: our stream waits for the caller's, the caller's waits for ours
+    def _enter(self):
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _done(self):
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def _call(self, fn, *args):
+        self._enter()
+        _check(fn(self.h, *args), self.h)
+        self._done()
+
+    def move(self):
+        self._call(lib().smc_move)
+
+    def reweight(self):
+        self._call(lib().smc_reweight)
+
+    def estimate(self, cov: bool = False):
+        mean = torch.empty(self.d, dtype=torch.float64, device=self.device)
+        c = torch.empty(self.d, self.d, dtype=torch.float64, device=self.device) if cov else None
+        self._call(lib().smc_estimate, _ptr(mean), _ptr(c))
+        return mean, c
+
+    def resample(self):
+        nc = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        did = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self._call(lib().smc_resample, _ptr(nc), _ptr(did))
+        return nc, did
+
+    def redistribute(self, ncopies: torch.Tensor):
+        self._call(lib().smc_redistribute, _ptr(ncopies))
+
+    def step(self, k: int, cov: bool = False, trace: bool = False, fhat: bool = False):
+        mean = torch.empty(self.d, dtype=torch.float64, device=self.device)
+        c = torch.empty(self.d, self.d, dtype=torch.float64, device=self.device) if cov else None
+        tr = torch.zeros(max(k, 1), STATS_WORDS, dtype=torch.float64, device=self.device) if trace else None
+        fh = torch.empty(self.d, dtype=torch.float64, device=self.device) if fhat else None
+        self._call(lib().smc_step, int(k), _ptr(mean), _ptr(c), _ptr(tr), _ptr(fh))
+        return dict(mean=mean, cov=c, trace=tr, fhat=fh)
+
+    def step_profile(self, events=None, mean: torch.Tensor | None = None):
+        """One iteration with 8 caller-created CUDA events recorded around its stages."""
+        if events is not None:
+            arr = (C.c_void_p * 8)(*[e.cuda_event for e in events])
+            n = 8
+        else:
+            arr, n = None, 0
+        self._call(lib().smc_step_profile, _ptr(mean), arr, n)
+
+    def sync(self) -> None:
+        _check(lib().smc_sync(self.h), self.h)
+
+    def stats(self) -> dict:
+        s = smc_iter_stats()
+        _check(lib().smc_read_stats(self.h, C.byref(s)), self.h)
+        return s.as_dict()
+
+    def current(self):
+        """(x, logpi) tensors holding the current particles (synchronises)."""
+        w = C.c_int32()
+        _check(lib().smc_current(self.h, C.byref(w)), self.h)
+        return (self.x, self.logpi) if w.value == 0 else (self.x_alt, self.logpi_alt)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().smc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace_dicts(tr: torch.Tensor) -> list[dict]:
+    """Decodes a [K, 7] smc_iter_stats trace (the last three fields are int64)."""
+    raw = tr.detach().cpu().contiguous()
+    ints = raw.view(torch.int64)
+    out = []
+    for k in range(raw.shape[0]):
+        out.append(dict(lse=float(raw[k, 0]), logc=float(raw[k, 1]), ess=float(raw[k, 2]),
+                        max_logw=float(raw[k, 3]), resampled=int(ints[k, 4]), t=int(ints[k, 5]),
+                        survivors=int(ints[k, 6])))
+    return out
