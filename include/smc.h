@@ -194,6 +194,29 @@ int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t 
  * stateless workspace. */
 int smc_ws_status(void* ws_dev, smc_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free stateless redistribute.  The paper has no counterpart: this
+ * is a deployment convenience.  It computes exactly what smc_redistribute_raw
+ * computes, for callers that cannot allocate device memory when they call --
+ * for example a plug-in handed only its input and output buffers, code inside
+ * a framework whose memory pool owns every device allocation, or a real-time
+ * loop that forbids allocation after start-up.  Its scratch is a fixed device
+ * array inside the library (about 4.2 MB on every GPU that loads the library,
+ * held until the process exits), so:
+ *  - n must be at most SMC_NOALLOC_MAX_N, else SMC_EINVAL and nothing runs;
+ *  - all calls on a device share the array: calls whose work overlaps on the
+ *    GPU (streams with no ordering between them) race and give undefined
+ *    results;
+ *  - the first call on each device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ * status_dev (device int32, may be NULL) receives SMC_OK, or SMC_EINVAL when
+ * ncopies has a negative entry or does not sum to n (then out_dev is not
+ * written).  The call allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine. */
+#define SMC_NOALLOC_MAX_N 1048576
+int smc_redistribute_raw_noalloc(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
+                                 void* out_dev, int32_t* status_dev, smc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

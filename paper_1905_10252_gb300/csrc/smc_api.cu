@@ -77,6 +77,8 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 
 }  // namespace
 
+void smc::set_global_error(const char* msg) { g_err = msg; }
+
 struct smc_sampler {
   smc_config cfg;
   int64_t n;

@@ -95,6 +95,9 @@ struct NcScanArgs {
 
 size_t devstate_bytes();
 
+// Message returned by smc_last_error(NULL) (smc_api.cu).
+void set_global_error(const char* msg);
+
 cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double* mu, const double* sigma, int d,
                                 DevState* st, cudaStream_t s);

@@ -23,7 +23,10 @@ EXPORTED = [
     "smc_workspace_bytes", "smc_init", "smc_move", "smc_reweight", "smc_estimate", "smc_resample",
     "smc_redistribute", "smc_step", "smc_step_profile", "smc_sync", "smc_read_stats", "smc_current", "smc_destroy",
     "smc_last_error", "smc_redistribute_ws_bytes", "smc_redistribute_raw", "smc_resample_raw", "smc_ws_status",
+    "smc_redistribute_raw_noalloc",
 ]
+
+NOALLOC_MAX_N = 1 << 20  # SMC_NOALLOC_MAX_N
 
 
 class SmcError(RuntimeError):
@@ -97,6 +100,7 @@ def _declare(L: C.CDLL) -> None:
     L.smc_redistribute_raw.argtypes = [i64, i32, vp, vp, vp, vp, vp]
     L.smc_resample_raw.argtypes = [i64, vp, u64, u64, i32, vp, vp, vp, vp]
     L.smc_ws_status.argtypes = [vp, vp]
+    L.smc_redistribute_raw_noalloc.argtypes = [i64, i32, vp, vp, vp, vp, vp]
     for name in EXPORTED:
         if name != "smc_last_error":
             getattr(L, name).restype = C.c_int
@@ -174,6 +178,21 @@ def decode_stats(stats: torch.Tensor) -> dict:
     raw = stats.detach().cpu().contiguous()
     b = raw.numpy().tobytes()[: C.sizeof(smc_iter_stats)]
     return smc_iter_stats.from_buffer_copy(b).as_dict()
+
+
+def smc_redistribute_raw_noalloc(ncopies: torch.Tensor, x_in: torch.Tensor, x_out: torch.Tensor,
+                                 status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Algorithm 5 on the rows of x_in into the caller's x_out, using the
+    library's fixed internal scratch instead of a workspace (n <= 2^20).  The
+    library allocates nothing; status (device int32[1], optional) receives
+    SMC_OK or SMC_EINVAL for an invalid ncopies vector."""
+    n = ncopies.numel()
+    if x_in.shape[0] != n or x_out.shape != x_in.shape:
+        raise ValueError("x_in and x_out must have one row per ncopies entry")
+    row_bytes = x_in[0].numel() * x_in.element_size() if n else 0
+    _check(lib().smc_redistribute_raw_noalloc(n, row_bytes, _ptr(ncopies), _ptr(x_in), _ptr(x_out),
+                                              _ptr(status), _stream_ptr(stream)))
+    return x_out
 
 
 def smc_ws_status(ws: torch.Tensor, stream=None) -> int:
