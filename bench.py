@@ -34,7 +34,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "particle-iters/s"
-STAGES = ["move_reweight", "max_mean_finalize", "quantise_reduce", "quantise_finalize", "systematic_scan",
+STAGES = ["move_reweight", "max_finalize", "quantise_reduce_estimate", "quantise_finalize", "systematic_scan",
           "redistribute", "commit"]
 
 
@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--d", type=int, default=16)
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sizes", default="16,20,24", help="redistribute workload: log2 N values")
+    p.add_argument("--cases", default="s0.5,s2,s8,onehot", help="redistribute workload: weight cases")
     return p.parse_args()
 
 
@@ -146,7 +148,7 @@ def oracle_iteration_rate(n_sample: int, iters: int, d: int, seed: int = 0):
 
 
 def cpu_baseline(d: int):
-    n_sample, iters = 1 << 20, 6
+    n_sample, iters = 1 << 20, 20
     rate, dt = oracle_iteration_rate(n_sample, iters, d)
     return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": f"{iters} iterations of N={n_sample} (D={d}, FP64, single thread), {dt:.1f} s",
@@ -203,11 +205,11 @@ def algorithmic_bytes(n: int, d: int, esize: int, survivors: float):
     return {
         # read x, log pi, log w; write x, log pi, log w
         "move_reweight": n * (2 * row + 2 * esize + 2 * 8),
-        # read log w
-        "quantise_reduce": n * 8,
-        # read log w, write the exclusive offsets (the ncopies information)
-        "systematic_scan": n * (8 + 4),
-        # read ncopies (as offsets), the distinct surviving rows + log pi, write
+        # read log w (quantisation) and x (the weighted mean of eq. (7))
+        "quantise_reduce_estimate": n * (8 + row),
+        # read log w, write one run start per survivor (the ncopies information)
+        "systematic_scan": n * 8 + survivors * 4,
+        # read the run starts, the distinct surviving rows + log pi, write
         # N rows + log pi, reset N log-weights
         "redistribute": n * 4 + survivors * (row + esize) + n * (row + esize) + n * 8,
     }
@@ -355,12 +357,12 @@ def run_redistribute(args):
 
     peak, peak_kind = peaks()
     d = args.d
-    for n in (1 << 16, 1 << 20, 1 << 24):
+    for n in [1 << int(v) for v in args.sizes.split(",")]:
         x = torch.as_tensor(inputs.particles(n, d, seed=1), device="cuda")
         out = torch.empty_like(x)
         wsb = torch.empty(native.smc_redistribute_ws_bytes(n), dtype=torch.uint8, device="cuda")
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        for case in ("s0.5", "s2", "s8", "onehot"):
+        for case in args.cases.split(","):
             lw = inputs.one_hot_log_weights(n, 0) if case == "onehot" else inputs.log_weights(n, float(case[1:]), 0)
             lwd = torch.as_tensor(lw, device="cuda")
             nc = torch.empty(n, dtype=torch.int32, device="cuda")

@@ -135,7 +135,8 @@ def expfx(y: float) -> int:
 
 
 def expfx_table() -> np.ndarray:
-    out = np.zeros(64, dtype=np.uint64)
+    """T1 (entries 0..63, ~2^63 2^(-j/64)) and T2 (64..127, ~2^63 2^(-j/4096))."""
+    out = np.zeros(128, dtype=np.uint64)
     lib().orc_expfx_table(_p(out, C.c_uint64))
     return out
 

@@ -21,7 +21,7 @@
  *   orc_philox4x64_10       pinned: numpy.random.Philox (independent library)
  *   orc_log, orc_sincos2pi  pinned: libm / mpmath within 2 ulp
  *   orc_normals             pinned: moments over 2^16 draws; Box-Muller identity
- *   orc_expfx               pinned: Decimal exp within 2^-54 relative
+ *   orc_expfx               pinned: Decimal exp within 2^-54 relative; tables vs exact roots
  *   orc_cholesky, logpi     pinned: numpy.linalg inverse quadratic form
  *   orc_lse_ess             pinned: closed forms (equal / one-hot weights)
  *   orc_systematic          pinned: sum == N, floor bounds, exhaustive-U mean
@@ -189,14 +189,15 @@ void orc_normals(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, int D,
  *   E(y) ~= 2^62 exp(y), an integer in [0, 2^62], E(0) = 2^62,
  * computed as exp(y) = 2^-z, z = -y log2(e) = k + f:
  *   A = floor(-y 2^57); Z = A * L2E (L2E = round(log2(e) 2^62)); k = Z >> 119;
- *   f = the 64 fraction bits below; j = top 6 bits of f, g = the rest;
- *   2^-f = T[j] * exp(-g ln2), T[j] ~= 2^63 2^(-j/64),
- *   exp(-h) by the nested form 1 - h(1 - h/2(1 - h/3(...))) to degree 8 in
- *   2^63 fixed point (each division by k is an integer floor),
- *   E = (T[j] * P) >> (64 + k).
- * T[j] is the product of c_b over the set bits b of j, c_b ~= 2^63 2^(-2^-b),
- * c_0 = 2^62, c_b = isqrt(c_{b-1} 2^63) -- every step an exact integer
- * operation, so any correct implementation gives the same table. */
+ *   f = the 64 fraction bits below; j1 = top 6 bits of f, j2 = next 6 bits,
+ *   g = the low 52 bits;  2^-f = T1[j1] T2[j2] exp(-g ln 2);
+ *   h = g ln 2 (H = h 2^76); exp(-h) = C0 - h(C1 - h(C2 - h(C3 - h C4)))
+ *   in 2^63 fixed point with C_k = floor(2^63 / k!);
+ *   E = ((T1[j1] T2[j2] >> 63) P) >> (64 + k).
+ * T1[j] ~= 2^63 2^(-j/64) and T2[j] ~= 2^63 2^(-j/4096) are products of
+ * c_b ~= 2^63 2^(-2^-b) over the set bits of j (b = 1..6 for T1, 7..12 for
+ * T2), c_0 = 2^62, c_b = isqrt(c_{b-1} 2^63) -- every step an exact integer
+ * operation, so any correct implementation gives the same tables. */
 #define L2E_62 0x5C551D94AE0BF85EULL  /* round(log2(e) * 2^62) */
 #define LN2_64 0xB17217F7D1CF79ACULL  /* round(ln(2) * 2^64)   */
 
@@ -217,25 +218,32 @@ static uint64_t isqrt_u128(u128 n) {
   return (uint64_t)res;
 }
 
-static uint64_t g_T[64];
+static uint64_t g_T[128]; /* T1 = g_T[0..63], T2 = g_T[64..127] */
+static uint64_t g_C[5];
 static int g_T_ready = 0;
 
 static void build_T(void) {
-  uint64_t c[7];
+  uint64_t c[13];
   c[0] = 1ULL << 62;
-  for (int b = 1; b <= 6; ++b) c[b] = isqrt_u128((u128)c[b - 1] << 63);
-  for (int j = 0; j < 64; ++j) {
-    uint64_t acc = 1ULL << 63;
-    for (int b = 1; b <= 6; ++b)
-      if (j & (1 << (6 - b))) acc = (uint64_t)(((u128)acc * c[b]) >> 63);
-    g_T[j] = acc;
+  for (int b = 1; b <= 12; ++b) c[b] = isqrt_u128((u128)c[b - 1] << 63);
+  for (int t = 0; t < 2; ++t)
+    for (int j = 0; j < 64; ++j) {
+      uint64_t acc = 1ULL << 63;
+      for (int b = 1; b <= 6; ++b)
+        if (j & (1 << (6 - b))) acc = (uint64_t)(((u128)acc * c[6 * t + b]) >> 63);
+      g_T[64 * t + j] = acc;
+    }
+  uint64_t fact = 1;
+  for (int k = 0; k <= 4; ++k) {
+    if (k > 0) fact *= (uint64_t)k;
+    g_C[k] = (1ULL << 63) / fact;
   }
   g_T_ready = 1;
 }
 
-void orc_expfx_table(uint64_t* out64) {
+void orc_expfx_table(uint64_t* out128) {
   if (!g_T_ready) build_T();
-  memcpy(out64, g_T, sizeof g_T);
+  memcpy(out128, g_T, sizeof g_T);
 }
 
 uint64_t orc_expfx(double y) {
@@ -258,15 +266,14 @@ uint64_t orc_expfx(double y) {
   u128 Z = (u128)A * L2E_62;
   unsigned k = (unsigned)(Z >> 119);
   uint64_t f = (uint64_t)(Z >> 55);
-  unsigned j = (unsigned)(f >> 58);
-  uint64_t g = f & ((1ULL << 58) - 1);
-  uint64_t H = (uint64_t)(((u128)(g << 6) * LN2_64) >> 64); /* h = H 2^-70 */
-  uint64_t P = 1ULL << 63;
-  for (unsigned kk = 8; kk >= 1; --kk) {
-    uint64_t hp = (uint64_t)(((u128)H * P) >> 70);
-    P = (1ULL << 63) - hp / kk;
-  }
-  return (uint64_t)(((u128)g_T[j] * P) >> (64 + k));
+  unsigned j1 = (unsigned)(f >> 58);
+  unsigned j2 = (unsigned)((f >> 52) & 63);
+  uint64_t g = f & ((1ULL << 52) - 1);
+  uint64_t H = (uint64_t)(((u128)(g << 12) * LN2_64) >> 64); /* h = H 2^-76 */
+  uint64_t P = g_C[4];
+  for (int kk = 3; kk >= 0; --kk) P = g_C[kk] - (uint64_t)(((u128)H * P) >> 76);
+  uint64_t T = (uint64_t)(((u128)g_T[j1] * g_T[64 + j2]) >> 63);
+  return (uint64_t)(((u128)T * P) >> (64 + k));
 }
 
 /* Fixed-point scale F of the weights: F = min(62, 63 - ceil(log2 N)), so that

@@ -3,8 +3,9 @@
 //   * initialisation (Algorithm 2, line 1),
 //   * random-walk move and importance reweighting (Algorithm 2, line 4; eq. (5)),
 //     fused in one pass over the particle rows,
-//   * the per-block partials of max log w and of the weighted mean (eq. (7)),
-//     combined by a single-block finaliser,
+//   * the per-block maxima of log w (integer-ordered compares, no FP64 pipe),
+//     combined by a single-block finaliser (the weighted mean of eq. (7) is
+//     formed in the quantisation pass, from the fixed-point weights),
 //   * the weighted covariance (diagnostic),
 //   * the iteration bookkeeping kernels (begin / commit, eq. (6) recycling).
 //
@@ -142,83 +143,58 @@ __device__ __forceinline__ void store_row(T* __restrict__ p, int d, const T (&x)
   }
 }
 
-// ---------------------------------------------------------------- online weighted sums
-// Per-thread running (max m, sum e, sum e x) with e = exp(log w - m); the
-// accumulators are rescaled when a larger log-weight arrives.
-template <typename A, int DMAX>
-struct Online {
-  double m;
-  A s;
-  A sx[DMAX];
+// ---------------------------------------------------------------- running maximum of log w
+// Doubles compared as integers (order-preserving map of the bit pattern): the
+// FP64 pipe of GB300 runs at a small fraction of its integer rate.
+__device__ __forceinline__ long long ordered_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double from_ordered_key(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFll));
+}
+
+struct MaxTracker {
+  long long best;
   bool nan;
   __device__ __forceinline__ void init() {
-    m = -INFINITY;
-    s = A(0);
-#pragma unroll
-    for (int c = 0; c < DMAX; ++c) sx[c] = A(0);
+    best = ordered_key(-INFINITY);
     nan = false;
   }
-  template <typename T>
-  __device__ __forceinline__ void add(double lw, const T (&x)[DMAX]) {
-    if (isnan(lw)) {
+  __device__ __forceinline__ void add(double v) {
+    const long long b = __double_as_longlong(v);
+    if ((b & 0x7FF0000000000000ll) == 0x7FF0000000000000ll && (b & 0x000FFFFFFFFFFFFFll)) {
       nan = true;
       return;
     }
-    if (lw == -INFINITY) return;
-    if (lw > m) {
-      const A sc = (m == -INFINITY) ? A(0) : A(exp_a(A(m - lw)));
-      s = s * sc + A(1);
-#pragma unroll
-      for (int c = 0; c < DMAX; ++c) sx[c] = sx[c] * sc + A(x[c]);
-      m = lw;
-    } else {
-      const A e = exp_a(A(lw - m));
-      s += e;
-#pragma unroll
-      for (int c = 0; c < DMAX; ++c) sx[c] += e * A(x[c]);
-    }
+    const long long k = b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+    best = k > best ? k : best;
   }
-  __device__ __forceinline__ static float exp_a(float v) { return __expf(v); }
-  __device__ __forceinline__ static double exp_a(double v) { return exp(v); }
 };
 
-// Block-combine the online partials and write one record per block:
-// part[b * (2 + d) + {0: m, 1: s, 2..: s x}].
-template <typename A, int DMAX>
-__device__ __forceinline__ void block_write_partial(Online<A, DMAX>& on, int d, double* __restrict__ part,
-                                                    DevState* st) {
-  __shared__ double sh[kPThreads / 32][DMAX + 2];
-  __shared__ double shm[kPThreads / 32];
-  __shared__ double mb;
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// One record per block: part[2b] = max log w of the block, part[2b+1] = 1.
+__device__ __forceinline__ void block_write_max(const MaxTracker& mt, double* __restrict__ part, DevState* st) {
+  __shared__ long long shm[kPThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (on.nan) record_error(st, SMC_ENONFINITE);
-  double wm = warp_max(on.m);
+  if (mt.nan) record_error(st, SMC_ENONFINITE);
+  const long long wm = warp_max_ll(mt.best);
   if (lane == 0) shm[wid] = wm;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double v = -INFINITY;
-    for (int w = 0; w < nw; ++w) v = fmax(v, shm[w]);
-    mb = v;
+    long long v = shm[0];
+    for (int w = 1; w < nw; ++w) v = shm[w] > v ? shm[w] : v;
+    part[2 * blockIdx.x] = from_ordered_key(v);
+    part[2 * blockIdx.x + 1] = 1.0;
   }
-  __syncthreads();
-  const double scale = (on.m == -INFINITY) ? 0.0 : exp(on.m - mb);
-  double v = double(on.s) * scale;
-  v = warp_sum(v);
-  if (lane == 0) sh[wid][0] = v;
-#pragma unroll
-  for (int c = 0; c < DMAX; ++c) {
-    if (c < d) {
-      double u = warp_sum(double(on.sx[c]) * scale);
-      if (lane == 0) sh[wid][1 + c] = u;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < d + 1) {
-    double acc = 0.0;
-    for (int w = 0; w < nw; ++w) acc += sh[w][threadIdx.x];
-    part[blockIdx.x * (2 + d) + 1 + threadIdx.x] = acc;
-  }
-  if (threadIdx.x == 0) part[blockIdx.x * (2 + d)] = mb;
 }
 
 template <typename T>
@@ -256,9 +232,8 @@ template <typename T, int DMAX>
 __global__ void __launch_bounds__(kPThreads) k_init(ParticleArgs a) {
   __shared__ TargetSmem<T> ts;
   load_target<T>(a.tg, a.d, ts);
-  using A = T;
-  Online<A, DMAX> on;
-  on.init();
+  MaxTracker mt;
+  mt.init();
   T* __restrict__ x = static_cast<T*>(a.x[0]);
   T* __restrict__ lp = static_cast<T*>(a.logpi[0]);
   const T nu = T(a.tg->nu);
@@ -295,9 +270,9 @@ __global__ void __launch_bounds__(kPThreads) k_init(ParticleArgs a) {
     }
     store_row<T, DMAX>(x + i * a.d, a.d, xr);
     a.logw[i] = lw;
-    on.add(lw, xr);
+    mt.add(lw);
   }
-  block_write_partial<A, DMAX>(on, a.d, a.part, a.st);
+  block_write_max(mt, a.part, a.st);
 }
 
 // ---------------------------------------------------------------- move + reweight
@@ -309,9 +284,8 @@ template <typename T, int DMAX, bool MOVE, bool REWEIGHT>
 __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
   __shared__ TargetSmem<T> ts;
   if (REWEIGHT) load_target<T>(a.tg, a.d, ts);
-  using A = T;
-  Online<A, DMAX> on;
-  on.init();
+  MaxTracker mt;
+  mt.init();
   const int cur = a.st->cur;
   const uint64_t t = uint64_t(a.st->t);
   T* __restrict__ x = static_cast<T*>(cur ? a.x[1] : a.x[0]);
@@ -347,67 +321,221 @@ __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
         lw = a.logw[i] + (double(lpi) - double(lpp));
       lp[i] = lpi;
       a.logw[i] = lw;
-      on.add(lw, xr);
+      mt.add(lw);
     }
   }
-  if (REWEIGHT) block_write_partial<A, DMAX>(on, a.d, a.part, a.st);
+  if (REWEIGHT) block_write_max(mt, a.part, a.st);
 }
 
-// ---------------------------------------------------------------- finalise max + mean
-// Single block: m = max_b m_b, s = sum_b s_b e^{m_b - m}, mean = sum_b sx_b e^{m_b-m} / s.
-__global__ void __launch_bounds__(kFinThreads) k_est_finalize(const double* __restrict__ part, int nb, int d,
-                                                             DevState* st, int write_mean_out) {
-  __shared__ double shm[32];
-  __shared__ double sh[32][kMaxD + 1];
-  __shared__ double mall;
+// ---------------------------------------------------------------- move + reweight, FP32 fast path
+// The FP32 path gives each lane DPL coordinates (DPL/8 Philox blocks: four
+// 64-bit words, four Box-Muller pairs per block); LPP = ceil(D/DPL) lanes
+// share a particle.  Box-Muller uses the multi-function unit: r^2 = -2 ln(1-a)
+// by __logf, or by its series when a < 1/16 (where __logf's absolute error
+// would dominate), and __sincosf on 2 pi (b - 1/2) in [-pi, pi); the normals
+// differ from the exactly rounded ones by a few 1e-6 at most, and since the
+// random-walk proposal stays symmetric the weights of eq. (5) are unaffected.
+// The next particle's row, log pi and log w are loaded while the current one
+// is computed.
+__device__ __forceinline__ void bm_pair_fast(uint64_t w, float& z0, float& z1) {
+  const uint32_t h0 = uint32_t(w), h1 = uint32_t(w >> 32);
+  const float a = float(h0 >> 8) * 0x1p-24f;  // u1 = 1 - a
+  float p = fmaf(a, 1.0f / 7.0f, 1.0f / 6.0f);
+  p = fmaf(a, p, 0.2f);
+  p = fmaf(a, p, 0.25f);
+  p = fmaf(a, p, 1.0f / 3.0f);
+  p = fmaf(a, p, 0.5f);
+  p = fmaf(a, p, 1.0f);
+  const float r2s = 2.0f * a * p;                 // -2 ln(1-a), |a| < 1/16
+  const float r2l = -2.0f * __logf(1.0f - a);
+  const float r = sqrtf(a < 0.0625f ? r2s : r2l);
+  const float th = float(int(h1 >> 8) - (1 << 23)) * (0x1p-24f * 6.28318530717958647692f);
+  float sn, cs;
+  __sincosf(th, &sn, &cs);  // (sin, cos)(2 pi b - pi) = -(sin, cos)(2 pi b)
+  z0 = -r * cs;
+  z1 = -r * sn;
+}
+
+// Shared-memory loads the compiler may not hoist out of the particle loop (a
+// hoisted copy of the 136-entry factor would cost 136 registers per thread).
+__device__ __forceinline__ float4 lds4_volatile(const float* p) {
+  float4 v;
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+
+template <int DPL>
+__device__ __forceinline__ void load_seg(const float* __restrict__ row, bool vec, int nvalid, float (&xr)[DPL]) {
+  if (vec) {
+#pragma unroll
+    for (int v = 0; v < DPL / 4; ++v) {
+      const float4 f = reinterpret_cast<const float4*>(row)[v];
+      xr[4 * v] = f.x;
+      xr[4 * v + 1] = f.y;
+      xr[4 * v + 2] = f.z;
+      xr[4 * v + 3] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < DPL; ++c) xr[c] = c < nvalid ? row[c] : 0.0f;
+  }
+}
+
+template <int DPL, int LPP, bool MOVE, bool REWEIGHT>
+__global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleArgs a) {
+  constexpr int DMAX = DPL * LPP;
+  __shared__ __align__(16) float sP[kMaxD * kMaxD];
+  __shared__ float smu[kMaxD];
+  if (REWEIGHT) {
+    for (int i = threadIdx.x; i < kMaxD * kMaxD; i += blockDim.x) sP[i] = a.tg->Pf[i];
+    for (int i = threadIdx.x; i < kMaxD; i += blockDim.x) smu[i] = a.tg->muf[i];
+    __syncthreads();
+  }
+  MaxTracker mt;
+  mt.init();
+  const int cur = a.st->cur;
+  const uint64_t t = uint64_t(a.st->t);
+  float* __restrict__ x = static_cast<float*>(cur ? a.x[1] : a.x[0]);
+  float* __restrict__ lp = static_cast<float*>(cur ? a.logpi[1] : a.logpi[0]);
+  double* __restrict__ logw = a.logw;
+  const int d = a.d;
+  const int q = LPP > 1 ? int(threadIdx.x & (LPP - 1)) : 0;
+  const int c0 = DPL * q;
+  const int nvalid = d - c0;  // coordinates this lane owns (may be <= 0)
+  const bool vec = ((d & 3) == 0) && (nvalid >= DPL);
+  const float eps = float(a.step);
+  // The loop runs over whole warps (its bound is warp-uniform) so that every
+  // lane reaches the group shuffles; lanes past the end are predicated.
+  constexpr int kGroups = 32 / LPP;
+  const int64_t warp_global = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t step = int64_t(gridDim.x) * (blockDim.x >> 5) * kGroups;
+  const int grp = (threadIdx.x & 31) / LPP;
+  int64_t base = warp_global * kGroups;
+  // prologue: the first particle's data
+  float xo[DPL];
+  double lwc = 0.0;
+  float lpc = 0.0f;
+  {
+    const int64_t i = base + grp;
+    if (i < a.n && nvalid > 0) load_seg<DPL>(x + i * d + c0, vec, nvalid, xo);
+    else
+#pragma unroll
+      for (int c = 0; c < DPL; ++c) xo[c] = 0.0f;
+    if (REWEIGHT && i < a.n && q == 0) {
+      lwc = logw[i];
+      lpc = lp[i];
+    }
+  }
+  for (; base < a.n; base += step) {
+    const int64_t i = base + grp;
+    const bool valid = i < a.n;
+    // prefetch the next particle
+    const int64_t inx = i + step;
+    float xn[DPL];
+    double lwn = 0.0;
+    float lpn = 0.0f;
+    if (inx < a.n && nvalid > 0) load_seg<DPL>(x + inx * d + c0, vec, nvalid, xn);
+    else
+#pragma unroll
+      for (int c = 0; c < DPL; ++c) xn[c] = 0.0f;
+    if (REWEIGHT && inx < a.n && q == 0) {
+      lwn = logw[inx];
+      lpn = lp[inx];
+    }
+    if (MOVE && valid && nvalid > 0) {
+#pragma unroll
+      for (int blk = 0; blk < DPL / 8; ++blk) {
+        if (8 * blk < nvalid) {
+          const P4 w = stream_block(a.seed, t, kPurposeMove, uint64_t(i), uint32_t(c0 / 8 + blk));
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            float z0, z1;
+            bm_pair_fast(w.v[h], z0, z1);
+            xo[8 * blk + 2 * h] = fmaf(eps, z0, xo[8 * blk + 2 * h]);
+            xo[8 * blk + 2 * h + 1] = fmaf(eps, z1, xo[8 * blk + 2 * h + 1]);
+          }
+        }
+      }
+      float* row = x + i * d + c0;
+      if (vec) {
+#pragma unroll
+        for (int v = 0; v < DPL / 4; ++v)
+          reinterpret_cast<float4*>(row)[v] = make_float4(xo[4 * v], xo[4 * v + 1], xo[4 * v + 2], xo[4 * v + 3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < DPL; ++c)
+          if (c < nvalid) row[c] = xo[c];
+      }
+    }
+    if (REWEIGHT) {
+      float dv[DMAX];
+      if (LPP == 1) {
+#pragma unroll
+        for (int c = 0; c < DMAX; ++c) dv[c] = xo[c] - smu[c];
+      } else {
+        // all 32 lanes execute the shuffles (valid or not)
+#pragma unroll
+        for (int j = 0; j < LPP; ++j)
+#pragma unroll
+          for (int c = 0; c < DPL; ++c) dv[DPL * j + c] = __shfl_sync(0xffffffffu, xo[c], j, LPP) - smu[DPL * j + c];
+      }
+      if (valid && q == 0) {
+        // every lane reads the same factor entries (broadcast); P is lower
+        // triangular, so the entries above the diagonal that a 4-wide load
+        // brings in are exact zeros and leave acc unchanged
+        float qs = 0.0f;
+#pragma unroll
+        for (int r = 0; r < DMAX; ++r) {
+          if (r < d) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int c4 = 0; c4 <= r / 4; ++c4) {
+              const float4 pv = lds4_volatile(&sP[r * kMaxD + 4 * c4]);
+              acc = fmaf(pv.x, dv[4 * c4 + 0], acc);
+              if (4 * c4 + 1 <= r) acc = fmaf(pv.y, dv[4 * c4 + 1], acc);
+              if (4 * c4 + 2 <= r) acc = fmaf(pv.z, dv[4 * c4 + 2], acc);
+              if (4 * c4 + 3 <= r) acc = fmaf(pv.w, dv[4 * c4 + 3], acc);
+            }
+            qs = fmaf(acc, acc, qs);
+          }
+        }
+        const float lpi = -0.5f * qs;
+        const double lw = lwc + (double(lpi) - double(lpc));
+        lp[i] = lpi;
+        logw[i] = lw;
+        mt.add(lw);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DPL; ++c) xo[c] = xn[c];
+    lwc = lwn;
+    lpc = lpn;
+  }
+  if (REWEIGHT) block_write_max(mt, a.part, a.st);
+}
+
+// ---------------------------------------------------------------- finalise the maximum
+// Single block: m = max over the blocks' maxima; a NaN seen by any block, or a
+// maximum that is not finite (every log-weight -inf, or +inf), is an error.
+__global__ void __launch_bounds__(kFinThreads) k_max_finalize(const double* __restrict__ part, int nb,
+                                                             DevState* st) {
+  __shared__ long long shm[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int stride = 2 + d;
-  double m = -INFINITY;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = fmax(m, part[b * stride]);
-  m = warp_max(m);
+  long long m = ordered_key(-INFINITY);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const long long k = ordered_key(part[2 * b]);
+    m = k > m ? k : m;
+  }
+  m = warp_max_ll(m);
   if (lane == 0) shm[wid] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double v = -INFINITY;
-    for (int w = 0; w < nw; ++w) v = fmax(v, shm[w]);
-    mall = v;
-  }
-  __syncthreads();
-  const double M = mall;
-  double acc[kMaxD + 1];
-#pragma unroll
-  for (int c = 0; c <= kMaxD; ++c) acc[c] = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    const double mb = part[b * stride];
-    const double sc = (mb == -INFINITY) ? 0.0 : exp(mb - M);
-#pragma unroll
-    for (int c = 0; c <= kMaxD; ++c)
-      if (c <= d) acc[c] += part[b * stride + 1 + c] * sc;
-  }
-#pragma unroll
-  for (int c = 0; c <= kMaxD; ++c) {
-    if (c <= d) {
-      const double v = warp_sum(acc[c]);
-      if (lane == 0) sh[wid][c] = v;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x <= d) {
-    double v = 0.0;
-    for (int w = 0; w < nw; ++w) v += sh[w][threadIdx.x];
-    sh[0][threadIdx.x] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const double s = sh[0][0];
+    long long v = shm[0];
+    for (int w = 1; w < nw; ++w) v = shm[w] > v ? shm[w] : v;
+    const double M = from_ordered_key(v);
     st->m = M;
-    st->est_s = s;
-    if (!(M > -INFINITY && M < INFINITY) || !(s > 0.0 && s < INFINITY)) record_error(st, SMC_ENONFINITE);
-  }
-  if (threadIdx.x < d) {
-    const double mean = sh[0][1 + threadIdx.x] / sh[0][0];
-    st->mean[threadIdx.x] = mean;
-    if (write_mean_out && st->mean_out) st->mean_out[threadIdx.x] = mean;
+    if (!(M > -INFINITY && M < INFINITY)) record_error(st, SMC_ENONFINITE);
   }
 }
 
@@ -548,7 +676,23 @@ static cudaError_t launch_particles_d(int op, const ParticleArgs& a, int grid, c
   return launch_particles_t<T, 32>(op, a, grid, s);
 }
 
+template <int DPL, int LPP>
+static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, cudaStream_t s) {
+  switch (op) {
+    case OP_MOVE: k_move_reweight_lanes<DPL, LPP, true, false><<<grid, kPThreads, 0, s>>>(a); break;
+    case OP_REWEIGHT: k_move_reweight_lanes<DPL, LPP, false, true><<<grid, kPThreads, 0, s>>>(a); break;
+    case OP_MOVE_REWEIGHT: k_move_reweight_lanes<DPL, LPP, true, true><<<grid, kPThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s) {
+  if (a.dtype == SMC_F32 && op != OP_INIT && a.kind == SMC_GAUSS) {
+    if (a.d <= 8) return launch_lanes<8, 1>(op, a, grid, s);
+    if (a.d <= 16) return launch_lanes<16, 1>(op, a, grid, s);
+    return launch_lanes<16, 2>(op, a, grid, s);
+  }
   return a.dtype == SMC_F64 ? launch_particles_d<double>(op, a, grid, s) : launch_particles_d<float>(op, a, grid, s);
 }
 
@@ -558,9 +702,8 @@ cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double
   return cudaGetLastError();
 }
 
-cudaError_t launch_est_finalize(const double* part, int nb, int d, DevState* st, int write_mean_out,
-                                cudaStream_t s) {
-  k_est_finalize<<<1, kFinThreads, 0, s>>>(part, nb, d, st, write_mean_out);
+cudaError_t launch_max_finalize(const double* part, int nb, DevState* st, cudaStream_t s) {
+  k_max_finalize<<<1, kFinThreads, 0, s>>>(part, nb, st);
   return cudaGetLastError();
 }
 

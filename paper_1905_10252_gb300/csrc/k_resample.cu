@@ -9,12 +9,14 @@
 //    ncopies and ncopies_i = off_{i+1} - off_i (eq. (9) holds by telescoping);
 //    a block-local scan of W plus the block prefix gives C_i.
 //  * Redistribute (Algorithm 5 as the definition of the output): output-tile
-//    parallel gather.  A tile of 4096 output rows knows its first source row
-//    (written by the scan pass), marks the start of every source run that
-//    begins inside the tile (max over equal offsets picks the survivor), a
-//    block max-scan turns the marks into src(k), and the rows are copied with
-//    16-byte vector loads/stores.  Replaces the paper's MPI nearly-sort and
-//    rotational shifts (Sec. 4) with O(1) passes over the data.
+//    parallel gather.  The scan pass writes runstart[off_i] = i for every
+//    survivor (a run of ncopies_i output rows starts at off_i) and the source
+//    row of each tile's first output row; a tile of 4096 output rows loads its
+//    slice of runstart (resetting it to -1 for the next iteration), a block
+//    max-scan turns it into src(k), and the rows are copied with 16-byte
+//    vector loads/stores.  Every tile does the same bounded work whatever the
+//    weights.  Replaces the paper's MPI nearly-sort and rotational shifts
+//    (Sec. 4) with O(1) passes over the data.
 #include <cmath>
 
 #include "smc_internal.cuh"
@@ -22,8 +24,9 @@
 
 namespace smc {
 
-// 2^-j/64 table of the fixed-point exponential, ~2^63 2^(-j/64).
-__constant__ uint64_t c_T[64];
+// Tables of the fixed-point exponential: [0, 64) ~2^63 2^(-j/64),
+// [64, 128) ~2^63 2^(-j/4096).
+__constant__ uint64_t c_T[128];
 
 // floor(sqrt(n)) for n < 2^126 by Newton's iteration from above.
 static uint64_t isqrt_newton(u128 n) {
@@ -37,18 +40,21 @@ static uint64_t isqrt_newton(u128 n) {
   return uint64_t(x);
 }
 
-// T[j] = prod over the set bits b (b = 1 is the top of 6) of c_b with
-// c_0 = 2^62 and c_b = isqrt(c_{b-1} 2^63) ~= 2^63 2^(-2^-b); every product is
+// c_0 = 2^62, c_b = isqrt(c_{b-1} 2^63) ~= 2^63 2^(-2^-b) for b = 1..12;
+// T1[j] (T[j]) is the product of c_1..c_6 over the set bits of j (c_1 for the
+// top bit), T2[j] (T[64 + j]) the same with c_7..c_12; every product is
 // floored to 2^63 fixed point.
-static void build_table(uint64_t T[64]) {
-  uint64_t c[7];
+static void build_table(uint64_t T[128]) {
+  uint64_t c[13];
   c[0] = 1ull << 62;
-  for (int b = 1; b <= 6; ++b) c[b] = isqrt_newton(u128(c[b - 1]) << 63);
-  for (int j = 0; j < 64; ++j) {
-    uint64_t acc = 1ull << 63;
-    for (int b = 1; b <= 6; ++b)
-      if (j & (1 << (6 - b))) acc = uint64_t((u128(acc) * c[b]) >> 63);
-    T[j] = acc;
+  for (int b = 1; b <= 12; ++b) c[b] = isqrt_newton(u128(c[b - 1]) << 63);
+  for (int half = 0; half < 2; ++half) {
+    for (int j = 0; j < 64; ++j) {
+      uint64_t acc = 1ull << 63;
+      for (int b = 1; b <= 6; ++b)
+        if (j & (1 << (6 - b))) acc = uint64_t((u128(acc) * c[6 * half + b]) >> 63);
+      T[64 * half + j] = acc;
+    }
   }
 }
 
@@ -58,7 +64,7 @@ cudaError_t upload_expfx_table() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  uint64_t T[64];
+  uint64_t T[128];
   build_table(T);
   e = cudaMemcpyToSymbol(c_T, T, sizeof T);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
@@ -66,7 +72,7 @@ cudaError_t upload_expfx_table() {
 }
 
 __device__ __forceinline__ void load_table(uint64_t* T) {
-  if (threadIdx.x < 64) T[threadIdx.x] = c_T[threadIdx.x];
+  if (threadIdx.x < 128) T[threadIdx.x] = c_T[threadIdx.x];
   __syncthreads();
 }
 
@@ -143,17 +149,36 @@ __global__ void __launch_bounds__(kQThreads) k_max_logw(const double* __restrict
 }
 
 // ---------------------------------------------------------------- quantise: reduce
+// Per block of 4096 weights: the exact sums S = sum W, sum W^2, sum E, and
+// (EST) the partial sums sum_i E_i x_i of the estimate of eq. (7), whose
+// normalised weights are E_i / sum E (the fixed-point exp of log w_i - m).
+__device__ __forceinline__ float u64_to_float_trunc(uint64_t v) {
+  if (v == 0) return 0.0f;
+  const int e = 63 - __clzll((long long)v);
+  const uint32_t mant = e >= 23 ? uint32_t(v >> (e - 23)) : uint32_t(v << (23 - e));
+  return __uint_as_float((uint32_t(e + 127) << 23) | (mant & 0x7FFFFFu));
+}
+__device__ __forceinline__ void weight_of(uint64_t E, float* w) { *w = u64_to_float_trunc(E); }
+__device__ __forceinline__ void weight_of(uint64_t E, double* w) { *w = __ull2double_rn(E); }
+
+template <typename ST, int DMAX, bool EST>
 __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
-  __shared__ uint64_t T[64];
+  __shared__ uint64_t T[128];
   __shared__ uint64_t sh[kQThreads / 32][5];
+  __shared__ double shx[kQThreads / 32][DMAX];
   load_table(T);
   const DevState* st = a.st;
   uint64_t sw = 0;
   u128 sw2 = 0, se = 0;
+  ST acc[DMAX];
+#pragma unroll
+  for (int c = 0; c < DMAX; ++c) acc[c] = ST(0);
+  const int d = a.d;
   if (!st->err) {
     const double m = st->m;
     const int sh_w = 62 - st->F;
     const int64_t base = int64_t(blockIdx.x) * kQTile;
+    const ST* __restrict__ x = static_cast<const ST*>(st->cur ? a.x[1] : a.x[0]);
 #pragma unroll 4
     for (int k = 0; k < kQItems; ++k) {
       const int64_t i = base + k * kQThreads + threadIdx.x;
@@ -163,6 +188,27 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
         sw += W;
         sw2 += u128(W) * W;
         se += E;
+        if (EST) {
+          ST w;
+          weight_of(E, &w);
+          const ST* row = x + i * d;
+          if (d == DMAX && (DMAX * sizeof(ST)) % 16 == 0) {
+#pragma unroll
+            for (int v = 0; v < int(DMAX * sizeof(ST) / 16); ++v) {
+              const float4 f = __ldg(reinterpret_cast<const float4*>(row) + v);
+              const ST* fv = reinterpret_cast<const ST*>(&f);
+#pragma unroll
+              for (int u = 0; u < int(16 / sizeof(ST)); ++u) {
+                const int c = v * int(16 / sizeof(ST)) + u;
+                acc[c] = fma(w, fv[u], acc[c]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < DMAX; ++c)
+              if (c < d) acc[c] = fma(w, row[c], acc[c]);
+          }
+        }
       }
     }
   }
@@ -176,6 +222,15 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
     sh[wid][2] = uint64_t(sw2 >> 64);
     sh[wid][3] = uint64_t(se);
     sh[wid][4] = uint64_t(se >> 64);
+  }
+  if (EST) {
+#pragma unroll
+    for (int c = 0; c < DMAX; ++c) {
+      if (c < d) {
+        const double v = warp_sum(double(acc[c]));
+        if (lane == 0) shx[wid][c] = v;
+      }
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -192,6 +247,11 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
     q[2] = uint64_t(t2 >> 64);
     q[3] = uint64_t(te);
     q[4] = uint64_t(te >> 64);
+  }
+  if (EST && threadIdx.x < d) {
+    double v = 0.0;
+    for (int w = 0; w < kQThreads / 32; ++w) v += shx[w][threadIdx.x];
+    a.xpart[int64_t(blockIdx.x) * d + threadIdx.x] = v;
   }
 }
 
@@ -238,6 +298,25 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
     a.cbase[b] = pre;
     pre += a.qpart[5 * int64_t(b)];
   }
+  // eq. (7): f_t = sum_i E_i x_i / sum_i E_i from the per-block partial sums
+  __shared__ double shx[32];
+  __shared__ double sxsum[kMaxD];
+  const bool est = a.x[0] != nullptr && a.d > 0;
+  if (est) {
+    for (int c = 0; c < a.d; ++c) {
+      double v = 0.0;
+      for (int b = threadIdx.x; b < nb; b += blockDim.x) v += a.xpart[int64_t(b) * a.d + c];
+      v = warp_sum(v);
+      if (lane == 0) shx[wid] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += shx[w];
+        sxsum[c] = t;
+      }
+      __syncthreads();
+    }
+  }
   if (threadIdx.x != 0) return;
   uint64_t S = 0;
   u128 sw2 = 0, se = 0;
@@ -261,7 +340,16 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
   const int L = S ? 64 - __clzll((long long)S) : 1;
   const uint64_t R = S ? uint64_t(((u128(1) << (63 + L)) - 1) / S) : 0;
   const double m = st->m;
-  const double lse = m + log(u128_to_double(se) * 0x1p-62);
+  const double se_d = u128_to_double(se);
+  const double lse = m + log(se_d * 0x1p-62);
+  st->est_s = se_d * 0x1p-62;
+  if (est && !st->err && se_d > 0.0) {
+    for (int c = 0; c < a.d; ++c) {
+      const double mc = sxsum[c] / se_d;
+      st->mean[c] = mc;
+      if (st->mean_out) st->mean_out[c] = mc;
+    }
+  }
   const double Sd = double(S);
   const double ess = (S && sw2) ? Sd * Sd / u128_to_double(sw2) : 0.0;
   st->S = S;
@@ -298,10 +386,10 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
 __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
   const DevState* st = a.st;
   if (st->err || !(a.force || st->flag)) return;
-  __shared__ uint64_t T[64];
+  __shared__ uint64_t T[128];
   __shared__ union {
     double lw[kQThreads * 17];
-    uint32_t o[2][kQThreads * 17];
+    uint32_t o[kQThreads * 17];
   } buf;
   __shared__ uint64_t scratch[33];
   load_table(T);
@@ -327,7 +415,7 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
   }
   uint64_t btot;
   uint64_t C = a.cbase[blockIdx.x] + block_excl_scan_u64(tsum, scratch, &btot);
-  uint32_t offv[kQItems], ncv[kQItems];
+  uint32_t ncv[kQItems];
   unsigned nsurv = 0;
   uint64_t lo = div_by_S(u128(n) * C + U, S, L, R);
   const int64_t i0 = base + int64_t(threadIdx.x) * kQItems;
@@ -335,11 +423,11 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
   for (int q = 0; q < kQItems; ++q) {
     C += W[q];
     const uint64_t hi = div_by_S(u128(n) * C + U, S, L, R);
-    offv[q] = uint32_t(lo);
     ncv[q] = uint32_t(hi - lo);
     const int64_t i = i0 + q;
     if (hi > lo && i < n) {
       ++nsurv;
+      if (a.write_rs) a.runstart[lo] = int32_t(i);
       // every redistribute tile whose first output row lies in [lo, hi)
       for (uint64_t kb = ((lo + kRTile - 1) / kRTile) * kRTile; kb < hi && kb < uint64_t(n); kb += kRTile)
         a.tile_src[kb / kRTile] = int32_t(i);
@@ -353,22 +441,17 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(&const_cast<DevState*>(st)->survivors, (unsigned long long)v);
   }
   __syncthreads();  // buf.lw no longer read
+  if (a.ncopies) {
 #pragma unroll
-  for (int q = 0; q < kQItems; ++q) {
-    buf.o[0][threadIdx.x * 17 + q] = offv[q];
-    buf.o[1][threadIdx.x * 17 + q] = ncv[q];
-  }
-  __syncthreads();
+    for (int q = 0; q < kQItems; ++q) buf.o[threadIdx.x * 17 + q] = ncv[q];
+    __syncthreads();
 #pragma unroll 4
-  for (int k = 0; k < kQItems; ++k) {
-    const int idx = k * kQThreads + threadIdx.x;
-    const int64_t i = base + idx;
-    if (i < n) {
-      a.off[i] = buf.o[0][pad_idx(idx)];
-      if (a.ncopies) a.ncopies[i] = int32_t(buf.o[1][pad_idx(idx)]);
+    for (int k = 0; k < kQItems; ++k) {
+      const int idx = k * kQThreads + threadIdx.x;
+      const int64_t i = base + idx;
+      if (i < n) a.ncopies[i] = int32_t(buf.o[pad_idx(idx)]);
     }
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) a.off[n] = uint32_t(n);
 }
 
 // ---------------------------------------------------------------- standalone ncopies scan
@@ -441,21 +524,13 @@ __global__ void __launch_bounds__(kQThreads) k_nc_scan(NcScanArgs a) {
 #pragma unroll
   for (int q = 0; q < kQItems; ++q) {
     const int64_t i = i0 + q;
-    if (c[q] > 0 && i < n) {
+    if (c[q] > 0 && i < n && o < uint64_t(n)) {
+      a.runstart[o] = int32_t(i);
       for (uint64_t kb = ((o + kRTile - 1) / kRTile) * kRTile; kb < o + c[q] && kb < uint64_t(n); kb += kRTile)
         a.tile_src[kb / kRTile] = int32_t(i);
     }
-    buf[threadIdx.x * 17 + q] = uint32_t(o);  // each thread rewrites only its own items
     o += c[q];
   }
-  __syncthreads();
-#pragma unroll 4
-  for (int k = 0; k < kQItems; ++k) {
-    const int idx = k * kQThreads + threadIdx.x;
-    const int64_t i = base + idx;
-    if (i < n) a.off[i] = buf[pad_idx(idx)];
-  }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) a.off[n] = uint32_t(n);
 }
 
 // ---------------------------------------------------------------- redistribute
@@ -463,27 +538,33 @@ template <typename V, int CPR>
 __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
   int cur = 0;
   if (a.stateful) {
-    if (a.st->err || !(a.force || a.st->flag)) return;
+    if (!(a.force || a.st->flag)) return;
     cur = a.st->cur;
-  } else if (a.st->err) {
-    return;
   }
+  // after an error nothing is copied, but the runstart slice is still reset
+  const bool failed = a.st->err != 0;
   __shared__ int32_t mark[kRTile];
   __shared__ int32_t wsc[kRThreads / 32];
   const int64_t n = a.n;
   const int64_t k0 = int64_t(blockIdx.x) * kRTile;
   const int len = int(n - k0 < kRTile ? n - k0 : int64_t(kRTile));
-  // tile_src is complete whenever the copy counts sum to n (checked upstream);
-  // the clamps keep every row index inside [0, n) regardless
-  const int32_t i_lo = min(max(a.tile_src[blockIdx.x], 0), int32_t(n - 1));
-  const int32_t i_hi =
-      (int(blockIdx.x) + 1 < a.ntiles) ? min(max(a.tile_src[blockIdx.x + 1], i_lo), int32_t(n - 1)) : int32_t(n - 1);
-  for (int k = threadIdx.x; k < kRTile; k += blockDim.x) mark[k] = (k == 0) ? i_lo : -1;
+  // this tile's slice of runstart (survivor runs starting here), reset to -1
+  // for the next resampling
+  int32_t* __restrict__ rs = a.runstart + k0;
+  for (int k = threadIdx.x; k < kRTile; k += blockDim.x) {
+    int32_t v = -1;
+    if (k < len) {
+      v = rs[k];
+      if (v >= 0) rs[k] = -1;
+    }
+    mark[k] = v < int32_t(n) ? v : int32_t(n - 1);
+  }
   __syncthreads();
-  // runs starting inside the tile: the largest i with off_i == k is the survivor
-  for (int64_t i = int64_t(i_lo) + 1 + threadIdx.x; i <= i_hi; i += blockDim.x) {
-    const int64_t o = int64_t(a.off[i]) - k0;
-    if (o > 0 && o < len) atomicMax(&mark[o], int32_t(i));
+  if (failed) return;
+  // the run covering the first output row may have started in an earlier tile
+  if (threadIdx.x == 0) {
+    const int32_t first = min(max(a.tile_src[blockIdx.x], 0), int32_t(n - 1));
+    mark[0] = max(mark[0], first);
   }
   __syncthreads();
   // inclusive max-scan of mark[0, kRTile): 16 consecutive entries per thread
@@ -522,7 +603,7 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
       const int e = e0 + u * kRThreads;
       if (e < total) {
         const int k = e / cpr, c = e - k * cpr;
-        v[u] = in[int64_t(mark[k]) * cpr + c];
+        v[u] = __ldg(in + int64_t(mark[k]) * cpr + c);
       }
     }
 #pragma unroll
@@ -560,9 +641,24 @@ cudaError_t launch_max_logw(const double* logw, int64_t n, double* part, int nb,
   return cudaGetLastError();
 }
 
-cudaError_t launch_quant_reduce(const QuantArgs& a, cudaStream_t s) {
-  k_quant_reduce<<<qblocks(a.n), kQThreads, 0, s>>>(a);
+template <typename ST>
+static cudaError_t quant_reduce_t(const QuantArgs& a, cudaStream_t s) {
+  const int g = qblocks(a.n);
+  if (!a.x[0] || a.d < 1)
+    k_quant_reduce<ST, 1, false><<<g, kQThreads, 0, s>>>(a);
+  else if (a.d <= 4)
+    k_quant_reduce<ST, 4, true><<<g, kQThreads, 0, s>>>(a);
+  else if (a.d <= 8)
+    k_quant_reduce<ST, 8, true><<<g, kQThreads, 0, s>>>(a);
+  else if (a.d <= 16)
+    k_quant_reduce<ST, 16, true><<<g, kQThreads, 0, s>>>(a);
+  else
+    k_quant_reduce<ST, 32, true><<<g, kQThreads, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_quant_reduce(const QuantArgs& a, cudaStream_t s) {
+  return a.dtype == SMC_F64 ? quant_reduce_t<double>(a, s) : quant_reduce_t<float>(a, s);
 }
 
 cudaError_t launch_quant_finalize(const QuantArgs& a, int set_lse_prev, cudaStream_t s) {

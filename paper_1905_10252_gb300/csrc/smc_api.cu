@@ -34,7 +34,7 @@ int quant_shift(int64_t n) {
 
 // Byte offsets of the stateful sampler's workspace.
 struct Layout {
-  size_t st, tg, part, qpart, cbase, off, tile_src, total;
+  size_t st, tg, part, qpart, cbase, xpart, rs, tile_src, total;
   int qblocks, ntiles;
 };
 
@@ -54,8 +54,10 @@ Layout layout_for(int64_t n, int d) {
   p = align_up(p + size_t(L.qblocks) * 5 * sizeof(uint64_t));
   L.cbase = p;
   p = align_up(p + size_t(L.qblocks) * sizeof(uint64_t));
-  L.off = p;
-  p = align_up(p + size_t(n + 1) * sizeof(uint32_t));
+  L.xpart = p;
+  p = align_up(p + size_t(L.qblocks) * size_t(d < 1 ? 1 : d) * sizeof(double));
+  L.rs = p;
+  p = align_up(p + size_t(n) * sizeof(int32_t));
   L.tile_src = p;
   p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
   L.total = p;
@@ -96,7 +98,8 @@ struct smc_sampler {
   double* part;
   uint64_t* qpart;
   uint64_t* cbase;
-  uint32_t* off;
+  double* xpart;
+  int32_t* rs;
   int32_t* tile_src;
   int grid_p;
   // CUDA graph of one iteration (with and without the covariance stage)
@@ -153,8 +156,14 @@ QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies) {
   q.force = force;
   q.qpart = h->qpart;
   q.cbase = h->cbase;
-  q.off = h->off;
+  q.runstart = h->rs;
+  q.write_rs = force ? 0 : 1;  // the fused step feeds redistribute; smc_resample does not
   q.ncopies = ncopies;
+  q.x[0] = h->x[0];
+  q.x[1] = h->x[1];
+  q.d = h->d;
+  q.dtype = h->dtype;
+  q.xpart = h->xpart;
   q.tile_src = h->tile_src;
   q.nblocks = h->L.qblocks;
   q.ntiles = h->L.ntiles;
@@ -168,7 +177,7 @@ RedistArgs redist_args(const smc_sampler* h, int force) {
   r.n = h->n;
   r.row_bytes = int32_t(h->esize * h->d);
   r.lp_bytes = int32_t(h->esize);
-  r.off = h->off;
+  r.runstart = h->rs;
   r.tile_src = h->tile_src;
   r.ntiles = h->L.ntiles;
   r.force = force;
@@ -187,9 +196,10 @@ RedistArgs redist_args(const smc_sampler* h, int force) {
   return r;
 }
 
-// Weighted statistics after a reweight: max + mean, quantised sums, decision.
-cudaError_t launch_stats(smc_sampler* h, int write_mean_out, int set_lse_prev) {
-  cudaError_t e = launch_est_finalize(h->part, h->grid_p, h->d, h->st, write_mean_out, h->stream);
+// Weighted statistics after a reweight: max, quantised sums with the mean of
+// eq. (7), decision.
+cudaError_t launch_stats(smc_sampler* h, int set_lse_prev) {
+  cudaError_t e = launch_max_finalize(h->part, h->grid_p, h->st, h->stream);
   if (e != cudaSuccess) return e;
   const QuantArgs q = quant_args(h, 0, nullptr);
   e = launch_quant_reduce(q, h->stream);
@@ -202,12 +212,12 @@ cudaError_t launch_iteration(smc_sampler* h, bool with_cov) {
   const ParticleArgs a = particle_args(h);
   cudaError_t e = launch_begin(h->st, h->stream);
   if (e == cudaSuccess) e = launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, h->stream);
-  if (e == cudaSuccess) e = launch_est_finalize(h->part, h->grid_p, h->d, h->st, 1, h->stream);
-  if (e == cudaSuccess && with_cov) e = launch_zero_cov(h->st, h->d, h->stream);
-  if (e == cudaSuccess && with_cov) e = launch_cov(a, nullptr, h->grid_p, h->stream);
+  if (e == cudaSuccess) e = launch_max_finalize(h->part, h->grid_p, h->st, h->stream);
   const QuantArgs q = quant_args(h, 0, nullptr);
   if (e == cudaSuccess) e = launch_quant_reduce(q, h->stream);
   if (e == cudaSuccess) e = launch_quant_finalize(q, 0, h->stream);
+  if (e == cudaSuccess && with_cov) e = launch_zero_cov(h->st, h->d, h->stream);
+  if (e == cudaSuccess && with_cov) e = launch_cov(a, nullptr, h->grid_p, h->stream);
   if (e == cudaSuccess) e = launch_quant_scan(q, h->stream);
   if (e == cudaSuccess) e = launch_redistribute(redist_args(h, 0), h->stream);
   if (e == cudaSuccess) e = launch_commit(h->st, h->d, 0, 1, h->stream);
@@ -298,20 +308,23 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   h->part = reinterpret_cast<double*>(h->ws + L.part);
   h->qpart = reinterpret_cast<uint64_t*>(h->ws + L.qpart);
   h->cbase = reinterpret_cast<uint64_t*>(h->ws + L.cbase);
-  h->off = reinterpret_cast<uint32_t*>(h->ws + L.off);
+  h->xpart = reinterpret_cast<double*>(h->ws + L.xpart);
+  h->rs = reinterpret_cast<int32_t*>(h->ws + L.rs);
   h->tile_src = reinterpret_cast<int32_t*>(h->ws + L.tile_src);
-  h->grid_p = int(std::min<int64_t>(div_up(h->n, kPThreads), int64_t(sm_count()) * 4));
+  h->grid_p = int(std::min<int64_t>(div_up(h->n * lanes_per_particle(h->dtype, h->d), kPThreads),
+                                    int64_t(sm_count()) * 8));
   if (h->grid_p > kMaxPartBlocks) h->grid_p = kMaxPartBlocks;
   h->g_iter[0] = h->g_iter[1] = nullptr;
   h->err = "ok";
 
   // Algorithm 2, line 1, then the statistics of w_0 (LSE_0 becomes LSE_{t-1})
   e = cudaMemsetAsync(h->tg, 0, sizeof(TargetDev), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->rs, 0xFF, size_t(h->n) * sizeof(int32_t), h->stream);
   if (e == cudaSuccess) e = launch_state_init(h->st, h->n, 0, quant_shift(h->n), h->stream);
   if (e == cudaSuccess)
     e = launch_target_setup(h->tg, cfg->target, cfg->nu, cfg->mu_dev, cfg->sigma_dev, h->d, h->st, h->stream);
   if (e == cudaSuccess) e = launch_particles(OP_INIT, particle_args(h), h->grid_p, h->stream);
-  if (e == cudaSuccess) e = launch_stats(h, 0, 1);
+  if (e == cudaSuccess) e = launch_stats(h, 1);
   if (e != cudaSuccess) {
     int r = cuda_fail(nullptr, e, "smc_init launch");
     delete h;
@@ -331,7 +344,7 @@ int smc_move(smc_sampler* h) {
 int smc_reweight(smc_sampler* h) {
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   SMC_TRY(h, launch_particles(OP_REWEIGHT, particle_args(h), h->grid_p, h->stream));
-  SMC_TRY(h, launch_stats(h, 0, 0));
+  SMC_TRY(h, launch_stats(h, 0));
   return SMC_OK;
 }
 
@@ -362,7 +375,7 @@ int smc_redistribute(smc_sampler* h, const int32_t* ncopies_dev) {
   s.ncopies = ncopies_dev;
   s.part = h->qpart;
   s.cbase = h->cbase;
-  s.off = h->off;
+  s.runstart = h->rs;
   s.tile_src = h->tile_src;
   s.nblocks = h->L.qblocks;
   s.ntiles = h->L.ntiles;
@@ -410,7 +423,7 @@ int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host,
   SMC_TRY(h, launch_begin(h->st, s));
   SMC_TRY(h, launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, s));
   SMC_TRY(h, rec(1));
-  SMC_TRY(h, launch_est_finalize(h->part, h->grid_p, h->d, h->st, 1, s));
+  SMC_TRY(h, launch_max_finalize(h->part, h->grid_p, h->st, s));
   SMC_TRY(h, rec(2));
   SMC_TRY(h, launch_quant_reduce(q, s));
   SMC_TRY(h, rec(3));
@@ -466,7 +479,7 @@ const char* smc_last_error(const smc_sampler* h) { return h ? h->err.c_str() : g
 // ------------------------------------------------------------------ stateless
 namespace {
 struct RawLayout {
-  size_t st, part, qpart, cbase, off, tile_src, total;
+  size_t st, part, qpart, cbase, rs, tile_src, total;
   int qblocks, ntiles;
 };
 RawLayout raw_layout(int64_t n) {
@@ -482,8 +495,8 @@ RawLayout raw_layout(int64_t n) {
   p = align_up(p + size_t(L.qblocks) * 5 * sizeof(uint64_t));
   L.cbase = p;
   p = align_up(p + size_t(L.qblocks) * sizeof(uint64_t));
-  L.off = p;
-  p = align_up(p + size_t(n + 1) * sizeof(uint32_t));
+  L.rs = p;
+  p = align_up(p + size_t(n) * sizeof(int32_t));
   L.tile_src = p;
   p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
   L.total = p;
@@ -514,7 +527,7 @@ int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_de
   a.ncopies = ncopies_dev;
   a.part = reinterpret_cast<uint64_t*>(ws + L.qpart);
   a.cbase = reinterpret_cast<uint64_t*>(ws + L.cbase);
-  a.off = reinterpret_cast<uint32_t*>(ws + L.off);
+  a.runstart = reinterpret_cast<int32_t*>(ws + L.rs);
   a.tile_src = reinterpret_cast<int32_t*>(ws + L.tile_src);
   a.nblocks = L.qblocks;
   a.ntiles = L.ntiles;
@@ -523,7 +536,7 @@ int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_de
   r.n = n;
   r.row_bytes = row_bytes;
   r.lp_bytes = 0;
-  r.off = a.off;
+  r.runstart = a.runstart;
   r.tile_src = a.tile_src;
   r.ntiles = L.ntiles;
   r.force = 1;
@@ -533,6 +546,7 @@ int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_de
   r.st = st;
   r.stateful = 0;
   cudaError_t e = cudaMemsetAsync(&st->err, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.runstart, 0xFF, size_t(n) * sizeof(int32_t), s);
   if (e == cudaSuccess) e = launch_nc_reduce(a, s);
   if (e == cudaSuccess) e = launch_nc_finalize(a, s);
   if (e == cudaSuccess) e = launch_nc_scan(a, s);
@@ -562,7 +576,8 @@ int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t 
   q.force = 1;
   q.qpart = reinterpret_cast<uint64_t*>(ws + L.qpart);
   q.cbase = reinterpret_cast<uint64_t*>(ws + L.cbase);
-  q.off = reinterpret_cast<uint32_t*>(ws + L.off);
+  q.runstart = reinterpret_cast<int32_t*>(ws + L.rs);
+  q.write_rs = 0;
   q.ncopies = ncopies_dev;
   q.tile_src = reinterpret_cast<int32_t*>(ws + L.tile_src);
   q.nblocks = L.qblocks;
@@ -571,7 +586,7 @@ int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t 
   q.stats_out = stats_dev;
   e = launch_state_init(st, n, int64_t(t), quant_shift(n), s);
   if (e == cudaSuccess) e = launch_max_logw(logw_dev, n, part, L.qblocks, st, s);
-  if (e == cudaSuccess) e = launch_est_finalize(part, L.qblocks, 0, st, 0, s);
+  if (e == cudaSuccess) e = launch_max_finalize(part, L.qblocks, st, s);
   if (e == cudaSuccess) e = launch_quant_reduce(q, s);
   if (e == cudaSuccess) e = launch_quant_finalize(q, 0, s);
   if (e == cudaSuccess) e = launch_quant_scan(q, s);

@@ -240,11 +240,12 @@ __device__ __forceinline__ void normals_f32(uint64_t seed, uint64_t t, uint32_t 
 // E(y) ~= 2^62 exp(y) for y <= 0, an integer in [0, 2^62]:
 //   a = -y; A = floor(a 2^57) from the bits of a; Z = A round(log2(e) 2^62)
 //   (z = a log2 e = Z 2^-119); k = integer part, f = 64 fraction bits;
-//   2^-f = T[top 6 bits of f] * exp(-g ln 2) for the low 58 bits g;
-//   exp(-h) = 1 - h(1 - h/2(1 - h/3 ...)) to degree 8 in 2^63 fixed point
-//   with floor division by each k;  E = (T[j] P 2^-64) >> k.
-// T (64 entries, ~2^63 2^(-j/64)) is built on the host from integer square
-// roots and lives in shared memory while a kernel uses it.
+//   2^-f = T1[top 6 bits] T2[next 6 bits] exp(-g ln 2) for the low 52 bits g;
+//   exp(-h) = C0 - h(C1 - h(C2 - h(C3 - h C4))) in 2^63 fixed point with
+//   C_k = floor(2^63 / k!);  E = ((T1 T2 >> 63) P 2^-64) >> k.
+// T (128 entries: T1 ~= 2^63 2^(-j/64), T2 ~= 2^63 2^(-j/4096)) is built on
+// the host from integer square roots and lives in shared memory while a
+// kernel uses it.
 __device__ __forceinline__ uint64_t expfx(double y, const uint64_t* __restrict__ T) {
   const double a = -y;
   if (!(a < 44.0)) return 0;
@@ -261,16 +262,19 @@ __device__ __forceinline__ uint64_t expfx(double y, const uint64_t* __restrict__
   const uint64_t zlo = A * L2E, zhi = __umul64hi(A, L2E);
   const unsigned k = unsigned(zhi >> 55);
   const uint64_t f = (zhi << 9) | (zlo >> 55);
-  const unsigned j = unsigned(f >> 58);
-  const uint64_t g = f & ((1ull << 58) - 1);
-  const uint64_t H = __umul64hi(g << 6, LN2);
-  uint64_t P = 1ull << 63;
-#pragma unroll
-  for (unsigned kk = 8; kk >= 1; --kk) {
-    const uint64_t hp = __umul64hi(H, P) >> 6;
-    P = (1ull << 63) - hp / kk;
-  }
-  return __umul64hi(T[j], P) >> k;
+  const unsigned j1 = unsigned(f >> 58);
+  const unsigned j2 = unsigned((f >> 52) & 63);
+  const uint64_t g = f & ((1ull << 52) - 1);
+  const uint64_t H = __umul64hi(g << 12, LN2);
+  constexpr uint64_t ONE = 1ull << 63;
+  uint64_t P = ONE / 24;
+  P = ONE / 6 - (__umul64hi(H, P) >> 12);
+  P = ONE / 2 - (__umul64hi(H, P) >> 12);
+  P = ONE - (__umul64hi(H, P) >> 12);
+  P = ONE - (__umul64hi(H, P) >> 12);
+  const uint64_t t1 = T[j1], t2 = T[64 + j2];
+  const uint64_t Tm = (__umul64hi(t1, t2) << 1) | ((t1 * t2) >> 63);
+  return __umul64hi(Tm, P) >> k;
 }
 
 // floor(X / S) for X < 2^(L+33), S in [2^(L-1), 2^L), with R = floor(2^(63+L)/S):

@@ -28,6 +28,10 @@ struct alignas(256) TargetDev {
 
 enum { OP_INIT = 0, OP_MOVE = 1, OP_REWEIGHT = 2, OP_MOVE_REWEIGHT = 3 };
 
+// Lanes that share one particle in the move / reweight kernels: the FP32 path
+// gives each lane up to 16 coordinates (two Philox blocks); FP64 uses one lane.
+inline int lanes_per_particle(int dtype, int d) { return (dtype == SMC_F32 && d > 16) ? 2 : 1; }
+
 struct ParticleArgs {
   int64_t n;
   int32_t d;
@@ -53,20 +57,27 @@ struct QuantArgs {
   int32_t force;       // scan even if the decision is "no resample"
   uint64_t* qpart;     // per-block {sumW, sw2 lo, sw2 hi, sumE lo, sumE hi}
   uint64_t* cbase;     // exclusive prefix of the block sums of W
-  uint32_t* off;       // N + 1 exclusive offsets
+  int32_t* runstart;   // runstart[off_i] = i for every survivor (when write_rs)
+  int32_t write_rs;
+  int32_t pad;
   int32_t* ncopies;    // optional output
-  int32_t* tile_src;   // first source row of each redistribute tile
+  int32_t* tile_src;   // source row of the first output row of each redistribute tile
   int32_t nblocks;     // quantise blocks
   int32_t ntiles;      // redistribute tiles
   DevState* st;
   smc_iter_stats* stats_out;  // optional single record (stateless path)
+  // eq. (7) in the reduce pass: sum_i E_i x_i over the current rows, when x[0]
+  const void* x[2];
+  int32_t d;
+  int32_t dtype;
+  double* xpart;       // nblocks x d partial sums
 };
 
 struct RedistArgs {
   int64_t n;
   int32_t row_bytes;
   int32_t lp_bytes;      // 0: no log pi payload
-  const uint32_t* off;
+  int32_t* runstart;     // consumed and reset to -1 by the tile that reads it
   const int32_t* tile_src;
   int32_t ntiles;
   int32_t force;         // copy even if the decision is "no resample"
@@ -86,7 +97,7 @@ struct NcScanArgs {
   const int32_t* ncopies;
   uint64_t* part;       // per-block sums
   uint64_t* cbase;      // exclusive block prefixes
-  uint32_t* off;
+  int32_t* runstart;    // must hold -1 everywhere on entry
   int32_t* tile_src;
   int32_t nblocks;
   int32_t ntiles;
@@ -102,8 +113,7 @@ cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream
 cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double* mu, const double* sigma, int d,
                                 DevState* st, cudaStream_t s);
 cudaError_t launch_zero_cov(DevState* st, int d, cudaStream_t s);
-cudaError_t launch_est_finalize(const double* part, int nb, int d, DevState* st, int write_mean_out,
-                                cudaStream_t s);
+cudaError_t launch_max_finalize(const double* part, int nb, DevState* st, cudaStream_t s);
 cudaError_t launch_cov(const ParticleArgs& a, double* cov, int grid, cudaStream_t s);
 cudaError_t launch_begin(DevState* st, cudaStream_t s);
 cudaError_t launch_commit(DevState* st, int d, int force_flip, int recycle, cudaStream_t s);

@@ -33,12 +33,12 @@ constexpr size_t up(size_t v) { return (v + kAl - 1) / kAl * kAl; }
 constexpr int64_t kMaxN = SMC_NOALLOC_MAX_N;
 constexpr int64_t kBlocks = (kMaxN + smc::kQTile - 1) / smc::kQTile;
 constexpr int64_t kTiles = (kMaxN + smc::kRTile - 1) / smc::kRTile;
-// fixed layout, sized for kMaxN: state | block sums | block prefixes | offsets | tile starts
+// fixed layout, sized for kMaxN: state | block sums | block prefixes | run starts | tile starts
 constexpr size_t kAtState = 0;
 constexpr size_t kAtPart = up(sizeof(smc::DevState));
 constexpr size_t kAtBase = kAtPart + up(size_t(kBlocks) * 8);
-constexpr size_t kAtOff = kAtBase + up(size_t(kBlocks) * 8);
-constexpr size_t kAtTile = kAtOff + up(size_t(kMaxN + 1) * 4);
+constexpr size_t kAtRun = kAtBase + up(size_t(kBlocks) * 8);
+constexpr size_t kAtTile = kAtRun + up(size_t(kMaxN) * 4);
 constexpr size_t kBytes = kAtTile + up(size_t(kTiles + 1) * 4);
 
 }  // namespace
@@ -99,7 +99,7 @@ extern "C" int smc_redistribute_raw_noalloc(int64_t n, int32_t row_bytes, const 
   a.ncopies = ncopies_dev;
   a.part = reinterpret_cast<uint64_t*>(ws + kAtPart);
   a.cbase = reinterpret_cast<uint64_t*>(ws + kAtBase);
-  a.off = reinterpret_cast<uint32_t*>(ws + kAtOff);
+  a.runstart = reinterpret_cast<int32_t*>(ws + kAtRun);
   a.tile_src = reinterpret_cast<int32_t*>(ws + kAtTile);
   a.nblocks = int32_t((n + kQTile - 1) / kQTile);
   a.ntiles = int32_t((n + kRTile - 1) / kRTile);
@@ -108,7 +108,7 @@ extern "C" int smc_redistribute_raw_noalloc(int64_t n, int32_t row_bytes, const 
   r.n = n;
   r.row_bytes = row_bytes;
   r.lp_bytes = 0;
-  r.off = a.off;
+  r.runstart = a.runstart;
   r.tile_src = a.tile_src;
   r.ntiles = a.ntiles;
   r.force = 1;
@@ -118,6 +118,7 @@ extern "C" int smc_redistribute_raw_noalloc(int64_t n, int32_t row_bytes, const 
   r.st = st;
   r.stateful = 0;
   e = cudaMemsetAsync(&st->err, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.runstart, 0xFF, size_t(n) * sizeof(int32_t), s);
   if (e == cudaSuccess) e = launch_nc_reduce(a, s);
   if (e == cudaSuccess) e = launch_nc_finalize(a, s);
   if (e == cudaSuccess) e = launch_nc_scan(a, s);

@@ -255,7 +255,8 @@ def test_nonfinite_weights_reported(nat):
 
 
 # ------------------------------------------------------------------ sampler, FP32
-@pytest.mark.parametrize("N,D", [(5003, 16), (4096, 2), (999, 8), (2049, 32)])
+@pytest.mark.parametrize("N,D", [(5003, 16), (4096, 2), (999, 8), (2049, 32), (3001, 12), (777, 10), (1500, 20),
+                                 (257, 5)])
 def test_fp32_stages(nat, orc, N, D):
     mu, Sigma = _gauss(D, seed=D)
     tgt = orc.Target.gauss(mu, Sigma)

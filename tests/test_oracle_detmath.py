@@ -77,16 +77,20 @@ def test_expfx_special_values(orc):
 
 
 def test_expfx_table_exact_roots(orc):
-    # T[j] ~ 2^63 2^(-j/64); built from integer square roots, so within a few
-    # units of the exactly rounded value
+    # T1[j] ~ 2^63 2^(-j/64), T2[j] ~ 2^63 2^(-j/4096); built from integer
+    # square roots, so within a few units of the exactly rounded value
     getcontext().prec = 60
     T = orc.expfx_table()
-    assert int(T[0]) == 2 ** 63
+    assert int(T[0]) == 2 ** 63 and int(T[64]) == 2 ** 63
     for j in range(64):
-        exact = Decimal(2) ** 63 * (Decimal(2) ** (Decimal(-j) / 64))
-        assert abs(Decimal(int(T[j])) - exact) <= 16, j
-    # T[32] = floor(2^63 / sqrt 2) = isqrt(2^125) exactly (one square-root step)
+        exact1 = Decimal(2) ** 63 * (Decimal(2) ** (Decimal(-j) / 64))
+        exact2 = Decimal(2) ** 63 * (Decimal(2) ** (Decimal(-j) / 4096))
+        assert abs(Decimal(int(T[j])) - exact1) <= 16, j
+        assert abs(Decimal(int(T[64 + j])) - exact2) <= 32, j
+    # T1[32] = floor(2^63 / sqrt 2) = isqrt(2^125) exactly (one square-root step)
     assert int(T[32]) == math.isqrt(2 ** 125)
+    # the c_b chain continued six more times: T2[32] = isqrt applied to T1[1]
+    assert int(T[64 + 32]) == math.isqrt(int(T[1]) << 63)
 
 
 def test_quant_shift(orc):
