@@ -52,7 +52,7 @@ _u32p = C.POINTER(C.c_uint32)
 
 
 def _declare(L: C.CDLL) -> None:
-    L.orc_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
+    L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
     L.orc_log.argtypes = [C.c_double]
     L.orc_log.restype = C.c_double
     L.orc_sincos2pi_u53.argtypes = [C.c_uint64, _dp, _dp]
@@ -105,11 +105,11 @@ def _f64(a) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------- RNG
-def philox4x64_10(ctr, key) -> np.ndarray:
-    c = np.ascontiguousarray(ctr, dtype=np.uint64)
-    k = np.ascontiguousarray(key, dtype=np.uint64)
-    out = np.zeros(4, dtype=np.uint64)
-    lib().orc_philox4x64_10(_p(c, C.c_uint64), _p(k, C.c_uint64), _p(out, C.c_uint64))
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(out, C.c_uint32))
     return out
 
 

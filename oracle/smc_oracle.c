@@ -18,7 +18,7 @@
  * operations and gives the same bits on any conforming machine).
  *
  * Parity status per function (pins live in tests/test_oracle_*.py):
- *   orc_philox4x64_10       pinned: numpy.random.Philox (independent library)
+ *   orc_philox4x32_10       pinned: cuRAND host generator PHILOX4_32_10 (independent library)
  *   orc_log, orc_sincos2pi  pinned: libm / mpmath within 2 ulp
  *   orc_normals             pinned: moments over 2^16 draws; Box-Muller identity
  *   orc_expfx               pinned: Decimal exp within 2^-54 relative; tables vs exact roots
@@ -38,26 +38,26 @@
 typedef unsigned __int128 u128;
 
 /* ------------------------------------------------------------------------ */
-/* Counter-based random numbers: Philox4x64-10 (Salmon, Moraes, Dror & Shaw,
+/* Counter-based random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw,
  * "Parallel random numbers: as easy as 1, 2, 3", SC'11).  Ten rounds of two
- * 64x64->128 multiplies; the key is bumped by the Weyl constants between
+ * 32x32->64 multiplies; the key is bumped by the Weyl constants between
  * rounds.  The paper fixes no generator; Philox lets both implementations draw
  * the same numbers from (seed, iteration, particle). */
-#define PHILOX_M0 0xD2E7470EE14C6C93ULL
-#define PHILOX_M1 0xCA5A826395121157ULL
-#define PHILOX_W0 0x9E3779B97F4A7C15ULL
-#define PHILOX_W1 0xBB67AE8584CAA73BULL
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
 
-void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
-  uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
-  uint64_t k0 = key[0], k1 = key[1];
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
   for (int r = 0; r < 10; ++r) {
-    u128 p0 = (u128)PHILOX_M0 * c0;
-    u128 p1 = (u128)PHILOX_M1 * c2;
-    uint64_t n0 = (uint64_t)(p1 >> 64) ^ c1 ^ k0;
-    uint64_t n1 = (uint64_t)p1;
-    uint64_t n2 = (uint64_t)(p0 >> 64) ^ c3 ^ k1;
-    uint64_t n3 = (uint64_t)p0;
+    uint64_t p0 = (uint64_t)PHILOX_M0 * c0;
+    uint64_t p1 = (uint64_t)PHILOX_M1 * c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
     c0 = n0; c1 = n1; c2 = n2; c3 = n3;
     k0 += PHILOX_W0;
     k1 += PHILOX_W1;
@@ -65,16 +65,22 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Purposes: the third counter word carries (purpose << 32) | block. */
+/* Purposes: the third counter word carries (purpose << 24) | block. */
 enum { ORC_INIT = 1, ORC_MOVE = 2, ORC_RESAMPLE = 3 };
 
-/* 64-bit word w of the random stream of particle i at iteration t. */
-static uint64_t stream_word(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, uint64_t w) {
-  uint64_t ctr[4] = {i, t, ((uint64_t)purpose << 32) | (w >> 2), 0};
-  uint64_t key[2] = {seed, 0};
-  uint64_t out[4];
-  orc_philox4x64_10(ctr, key, out);
+/* 32-bit word w of the random stream of particle i at iteration t:
+ * counter (i, t, purpose << 24 | w / 4, 0), key (seed low, seed high). */
+static uint32_t stream_word(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, uint64_t w) {
+  uint32_t ctr[4] = {(uint32_t)i, (uint32_t)t, (purpose << 24) | (uint32_t)(w >> 2), 0};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
   return out[w & 3];
+}
+
+/* 64-bit word: 32-bit words 2w (high half) and 2w+1 (low half). */
+static uint64_t stream_word64(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, uint64_t w) {
+  return ((uint64_t)stream_word(seed, t, purpose, i, 2 * w) << 32) | stream_word(seed, t, purpose, i, 2 * w + 1);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -155,9 +161,9 @@ void orc_sincos2pi_u53(uint64_t v, double* s_out, double* c_out) {
 }
 
 /* D standard normals for particle i (Box-Muller on consecutive uniform
- * pairs).  ubits = 53: uniform k is the top 53 bits of stream word k.
- * ubits = 24: uniform k is the top 24 bits of 32-bit half k (low half of a
- * word first), the resolution the FP32 path draws at.  For a pair (a, b):
+ * pairs).  ubits = 53: uniform k is the top 53 bits of 64-bit word k (32-bit
+ * words 2k, 2k+1).  ubits = 24: uniform k is the top 24 bits of 32-bit word k,
+ * the resolution the FP32 path draws at.  For a pair (a, b):
  * u1 = 1 - a in (0, 1], r = sqrt(-2 log u1), theta = 2 pi b,
  * z = (r cos theta, r sin theta). */
 void orc_normals(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, int D, int ubits,
@@ -165,13 +171,11 @@ void orc_normals(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, int D,
   for (int p = 0; 2 * p < D; ++p) {
     uint64_t va, vb; /* 53-bit integers: a = va * 2^-53 */
     if (ubits == 53) {
-      va = stream_word(seed, t, purpose, i, 2 * p) >> 11;
-      vb = stream_word(seed, t, purpose, i, 2 * p + 1) >> 11;
+      va = stream_word64(seed, t, purpose, i, 2 * p) >> 11;
+      vb = stream_word64(seed, t, purpose, i, 2 * p + 1) >> 11;
     } else {
-      uint64_t w = stream_word(seed, t, purpose, i, p); /* halves 2p, 2p+1 */
-      uint32_t h0 = (uint32_t)w, h1 = (uint32_t)(w >> 32);
-      va = (uint64_t)(h0 >> 8) << 29;
-      vb = (uint64_t)(h1 >> 8) << 29;
+      va = (uint64_t)(stream_word(seed, t, purpose, i, 2 * p) >> 8) << 29;
+      vb = (uint64_t)(stream_word(seed, t, purpose, i, 2 * p + 1) >> 8) << 29;
     }
     double u1 = (double)((1ULL << 53) - va) * 0x1p-53;
     double r = sqrt(-2.0 * orc_log(u1));
@@ -530,10 +534,10 @@ int orc_decide(int64_t N, uint64_t S, uint64_t sw2_lo, uint64_t sw2_hi, int mode
   return lhs < (u128)N * sw2;
 }
 
-/* The systematic offset U in [0, S): U = floor(r S / 2^64), r one 64-bit word
- * of the resampling stream of iteration t. */
+/* The systematic offset U in [0, S): U = floor(r S / 2^64), r the first 64-bit
+ * word of the resampling stream of iteration t (particle index 2^32 - 1). */
 uint64_t orc_resample_u(uint64_t seed, uint64_t t, uint64_t S) {
-  uint64_t r = stream_word(seed, t, ORC_RESAMPLE, ~0ULL, 0);
+  uint64_t r = stream_word64(seed, t, ORC_RESAMPLE, 0xFFFFFFFFu, 0);
   return (uint64_t)(((u128)r * S) >> 64);
 }
 

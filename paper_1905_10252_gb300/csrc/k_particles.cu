@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
       if constexpr (sizeof(T) == 8)
         lw = __dadd_rn(a.logw[i], __dsub_rn(lpi, lpp));
       else
-        lw = a.logw[i] + (double(lpi) - double(lpp));
+        lw = a.logw[i] + double(lpi - lpp);
       lp[i] = lpi;
       a.logw[i] = lw;
       mt.add(lw);
@@ -328,8 +328,8 @@ __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
 }
 
 // ---------------------------------------------------------------- move + reweight, FP32 fast path
-// The FP32 path gives each lane DPL coordinates (DPL/8 Philox blocks: four
-// 64-bit words, four Box-Muller pairs per block); LPP = ceil(D/DPL) lanes
+// The FP32 path gives each lane DPL coordinates (DPL/4 Philox blocks: four
+// 32-bit words, two Box-Muller pairs per block); LPP = ceil(D/DPL) lanes
 // share a particle.  Box-Muller uses the multi-function unit: r^2 = -2 ln(1-a)
 // by __logf, or by its series when a < 1/16 (where __logf's absolute error
 // would dominate), and __sincosf on 2 pi (b - 1/2) in [-pi, pi); the normals
@@ -337,8 +337,7 @@ __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
 // random-walk proposal stays symmetric the weights of eq. (5) are unaffected.
 // The next particle's row, log pi and log w are loaded while the current one
 // is computed.
-__device__ __forceinline__ void bm_pair_fast(uint64_t w, float& z0, float& z1) {
-  const uint32_t h0 = uint32_t(w), h1 = uint32_t(w >> 32);
+__device__ __forceinline__ void bm_pair_fast(uint32_t h0, uint32_t h1, float& z0, float& z1) {
   const float a = float(h0 >> 8) * 0x1p-24f;  // u1 = 1 - a
   float p = fmaf(a, 1.0f / 7.0f, 1.0f / 6.0f);
   p = fmaf(a, p, 0.2f);
@@ -445,15 +444,15 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
     }
     if (MOVE && valid && nvalid > 0) {
 #pragma unroll
-      for (int blk = 0; blk < DPL / 8; ++blk) {
-        if (8 * blk < nvalid) {
-          const P4 w = stream_block(a.seed, t, kPurposeMove, uint64_t(i), uint32_t(c0 / 8 + blk));
+      for (int blk = 0; blk < DPL / 4; ++blk) {
+        if (4 * blk < nvalid) {
+          const P4 w = stream_block(a.seed, t, kPurposeMove, uint64_t(i), uint32_t(c0 / 4 + blk));
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
+          for (int h = 0; h < 2; ++h) {
             float z0, z1;
-            bm_pair_fast(w.v[h], z0, z1);
-            xo[8 * blk + 2 * h] = fmaf(eps, z0, xo[8 * blk + 2 * h]);
-            xo[8 * blk + 2 * h + 1] = fmaf(eps, z1, xo[8 * blk + 2 * h + 1]);
+            bm_pair_fast(w.v[2 * h], w.v[2 * h + 1], z0, z1);
+            xo[4 * blk + 2 * h] = fmaf(eps, z0, xo[4 * blk + 2 * h]);
+            xo[4 * blk + 2 * h + 1] = fmaf(eps, z1, xo[4 * blk + 2 * h + 1]);
           }
         }
       }
@@ -500,8 +499,10 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
             qs = fmaf(acc, acc, qs);
           }
         }
+        // eq. (5): the log-target difference in FP32 (exact when the two
+        // values are within a factor of two), one FP64 addition
         const float lpi = -0.5f * qs;
-        const double lw = lwc + (double(lpi) - double(lpc));
+        const double lw = lwc + double(lpi - lpc);
         lp[i] = lpi;
         logw[i] = lw;
         mt.add(lw);

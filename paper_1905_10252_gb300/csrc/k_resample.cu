@@ -183,8 +183,9 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
     for (int k = 0; k < kQItems; ++k) {
       const int64_t i = base + k * kQThreads + threadIdx.x;
       if (i < a.n) {
-        const uint64_t E = expfx(a.logw[i] - m, T);
+        const uint64_t E = expfx_a(__dsub_rn(m, a.logw[i]), T);
         const uint64_t W = E >> sh_w;
+        a.wbuf[i] = W;
         sw += W;
         sw2 += u128(W) * W;
         se += E;
@@ -224,11 +225,12 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
     sh[wid][4] = uint64_t(se >> 64);
   }
   if (EST) {
+    // warp sums in the state precision (the FP64 pipe is scarce), then FP64
 #pragma unroll
     for (int c = 0; c < DMAX; ++c) {
       if (c < d) {
-        const double v = warp_sum(double(acc[c]));
-        if (lane == 0) shx[wid][c] = v;
+        const ST v = warp_sum(acc[c]);
+        if (lane == 0) shx[wid][c] = double(v);
       }
     }
   }
@@ -299,23 +301,21 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
     pre += a.qpart[5 * int64_t(b)];
   }
   // eq. (7): f_t = sum_i E_i x_i / sum_i E_i from the per-block partial sums
-  __shared__ double shx[32];
   __shared__ double sxsum[kMaxD];
   const bool est = a.x[0] != nullptr && a.d > 0;
   if (est) {
-    for (int c = 0; c < a.d; ++c) {
+    // thread j sums column j % d over rows j / d, j / d + stride / d, ...
+    // (consecutive threads read consecutive words)
+    if (threadIdx.x < a.d) sxsum[threadIdx.x] = 0.0;
+    __syncthreads();
+    const int stride = (int(blockDim.x) / a.d) * a.d;
+    if (int(threadIdx.x) < stride) {
       double v = 0.0;
-      for (int b = threadIdx.x; b < nb; b += blockDim.x) v += a.xpart[int64_t(b) * a.d + c];
-      v = warp_sum(v);
-      if (lane == 0) shx[wid] = v;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < nw; ++w) t += shx[w];
-        sxsum[c] = t;
-      }
-      __syncthreads();
+      const int64_t total_words = int64_t(nb) * a.d;
+      for (int64_t j = threadIdx.x; j < total_words; j += stride) v += a.xpart[j];
+      atomicAdd(&sxsum[threadIdx.x % a.d], v);
     }
+    __syncthreads();
   }
   if (threadIdx.x != 0) return;
   uint64_t S = 0;
@@ -335,8 +335,9 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
     else
       flag = (u128(S) * S * 2) < u128(n) * sw2;
   }
-  const P4 r = stream_block(a.seed, uint64_t(st->t), kPurposeResample, ~0ull, 0);
-  const uint64_t U = S ? __umul64hi(r.v[0], S) : 0;
+  const P4 r = stream_block(a.seed, uint64_t(st->t), kPurposeResample, 0xFFFFFFFFull, 0);
+  const uint64_t r64 = (uint64_t(r.v[0]) << 32) | r.v[1];
+  const uint64_t U = S ? __umul64hi(r64, S) : 0;
   const int L = S ? 64 - __clzll((long long)S) : 1;
   const uint64_t R = S ? uint64_t(((u128(1) << (63 + L)) - 1) / S) : 0;
   const double m = st->m;
@@ -386,43 +387,62 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
 __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
   const DevState* st = a.st;
   if (st->err || !(a.force || st->flag)) return;
-  __shared__ uint64_t T[128];
   __shared__ union {
-    double lw[kQThreads * 17];
+    uint64_t w[kQThreads * 17];
     uint32_t o[kQThreads * 17];
   } buf;
   __shared__ uint64_t scratch[33];
-  load_table(T);
   const int64_t n = a.n;
   const int64_t base = int64_t(blockIdx.x) * kQTile;
+  // the quantised weights of the reduce pass, staged for a blocked layout
 #pragma unroll 4
   for (int k = 0; k < kQItems; ++k) {
     const int idx = k * kQThreads + threadIdx.x;
     const int64_t i = base + idx;
-    buf.lw[pad_idx(idx)] = i < n ? a.logw[i] : -INFINITY;
+    buf.w[pad_idx(idx)] = i < n ? a.wbuf[i] : 0ull;
   }
   __syncthreads();
-  const double m = st->m;
-  const int sh_w = 62 - st->F;
   const uint64_t S = st->S, U = st->U, R = st->recip;
   const int L = st->L;
   uint64_t W[kQItems];
   uint64_t tsum = 0;
 #pragma unroll
   for (int q = 0; q < kQItems; ++q) {
-    W[q] = expfx(buf.lw[threadIdx.x * 17 + q] - m, T) >> sh_w;
+    W[q] = buf.w[threadIdx.x * 17 + q];
     tsum += W[q];
   }
   uint64_t btot;
   uint64_t C = a.cbase[blockIdx.x] + block_excl_scan_u64(tsum, scratch, &btot);
   uint32_t ncv[kQItems];
   unsigned nsurv = 0;
-  uint64_t lo = div_by_S(u128(n) * C + U, S, L, R);
+  // floor((N C + U) / S) as quotient lo and remainder rem, advanced item by
+  // item: the increment is floor((rem + N W_i) / S), found by at most three
+  // subtractions when N W_i <= 3 S and by a division otherwise
+  u128 X = u128(n) * C + U;
+  uint64_t lo = div_by_S(X, S, L, R);
+  uint64_t rem = uint64_t(X - u128(lo) * S);
+  const u128 S3 = u128(S) * 3;
   const int64_t i0 = base + int64_t(threadIdx.x) * kQItems;
 #pragma unroll
   for (int q = 0; q < kQItems; ++q) {
     C += W[q];
-    const uint64_t hi = div_by_S(u128(n) * C + U, S, L, R);
+    const u128 NW = u128(n) * W[q];
+    uint64_t hi;
+    if (NW <= S3) {
+      u128 t = u128(rem) + NW;
+      hi = lo;
+#pragma unroll
+      for (int it = 0; it < 3; ++it)
+        if (t >= S) {
+          t -= S;
+          ++hi;
+        }
+      rem = uint64_t(t);
+    } else {
+      X = u128(n) * C + U;
+      hi = div_by_S(X, S, L, R);
+      rem = uint64_t(X - u128(hi) * S);
+    }
     ncv[q] = uint32_t(hi - lo);
     const int64_t i = i0 + q;
     if (hi > lo && i < n) {
@@ -440,7 +460,7 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(&const_cast<DevState*>(st)->survivors, (unsigned long long)v);
   }
-  __syncthreads();  // buf.lw no longer read
+  __syncthreads();  // buf.w no longer read
   if (a.ncopies) {
 #pragma unroll
     for (int q = 0; q < kQItems; ++q) buf.o[threadIdx.x * 17 + q] = ncv[q];
@@ -551,13 +571,20 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
   // this tile's slice of runstart (survivor runs starting here), reset to -1
   // for the next resampling
   int32_t* __restrict__ rs = a.runstart + k0;
-  for (int k = threadIdx.x; k < kRTile; k += blockDim.x) {
-    int32_t v = -1;
-    if (k < len) {
-      v = rs[k];
-      if (v >= 0) rs[k] = -1;
+  {
+    constexpr int kItems = kRTile / kRThreads;
+    int32_t v[kItems];
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int k = threadIdx.x + u * kRThreads;
+      v[u] = k < len ? rs[k] : -1;
     }
-    mark[k] = v < int32_t(n) ? v : int32_t(n - 1);
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int k = threadIdx.x + u * kRThreads;
+      if (k < len) rs[k] = -1;  // whole sectors: no read-for-ownership
+      mark[k] = v[u] < int32_t(n) ? v[u] : int32_t(n - 1);
+    }
   }
   __syncthreads();
   if (failed) return;
@@ -595,7 +622,7 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
   const V* __restrict__ in = static_cast<const V*>(cur ? a.x_in[1] : a.x_in[0]);
   V* __restrict__ out = static_cast<V*>(cur ? a.x_out[1] : a.x_out[0]) + k0 * cpr;
   const int total = len * cpr;
-  constexpr int kU = 4;
+  constexpr int kU = 8;
   for (int e0 = threadIdx.x; e0 < total; e0 += kRThreads * kU) {
     V v[kU];
 #pragma unroll

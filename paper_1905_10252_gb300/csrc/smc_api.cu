@@ -34,7 +34,7 @@ int quant_shift(int64_t n) {
 
 // Byte offsets of the stateful sampler's workspace.
 struct Layout {
-  size_t st, tg, part, qpart, cbase, xpart, rs, tile_src, total;
+  size_t st, tg, part, qpart, cbase, xpart, rs, wbuf, tile_src, total;
   int qblocks, ntiles;
 };
 
@@ -58,6 +58,8 @@ Layout layout_for(int64_t n, int d) {
   p = align_up(p + size_t(L.qblocks) * size_t(d < 1 ? 1 : d) * sizeof(double));
   L.rs = p;
   p = align_up(p + size_t(n) * sizeof(int32_t));
+  L.wbuf = p;
+  p = align_up(p + size_t(n) * sizeof(uint64_t));
   L.tile_src = p;
   p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
   L.total = p;
@@ -100,6 +102,7 @@ struct smc_sampler {
   uint64_t* cbase;
   double* xpart;
   int32_t* rs;
+  uint64_t* wbuf;
   int32_t* tile_src;
   int grid_p;
   // CUDA graph of one iteration (with and without the covariance stage)
@@ -158,6 +161,7 @@ QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies) {
   q.cbase = h->cbase;
   q.runstart = h->rs;
   q.write_rs = force ? 0 : 1;  // the fused step feeds redistribute; smc_resample does not
+  q.wbuf = h->wbuf;
   q.ncopies = ncopies;
   q.x[0] = h->x[0];
   q.x[1] = h->x[1];
@@ -310,6 +314,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   h->cbase = reinterpret_cast<uint64_t*>(h->ws + L.cbase);
   h->xpart = reinterpret_cast<double*>(h->ws + L.xpart);
   h->rs = reinterpret_cast<int32_t*>(h->ws + L.rs);
+  h->wbuf = reinterpret_cast<uint64_t*>(h->ws + L.wbuf);
   h->tile_src = reinterpret_cast<int32_t*>(h->ws + L.tile_src);
   h->grid_p = int(std::min<int64_t>(div_up(h->n * lanes_per_particle(h->dtype, h->d), kPThreads),
                                     int64_t(sm_count()) * 8));
@@ -479,7 +484,7 @@ const char* smc_last_error(const smc_sampler* h) { return h ? h->err.c_str() : g
 // ------------------------------------------------------------------ stateless
 namespace {
 struct RawLayout {
-  size_t st, part, qpart, cbase, rs, tile_src, total;
+  size_t st, part, qpart, cbase, rs, wbuf, tile_src, total;
   int qblocks, ntiles;
 };
 RawLayout raw_layout(int64_t n) {
@@ -497,6 +502,8 @@ RawLayout raw_layout(int64_t n) {
   p = align_up(p + size_t(L.qblocks) * sizeof(uint64_t));
   L.rs = p;
   p = align_up(p + size_t(n) * sizeof(int32_t));
+  L.wbuf = p;
+  p = align_up(p + size_t(n) * sizeof(uint64_t));
   L.tile_src = p;
   p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
   L.total = p;
@@ -578,6 +585,7 @@ int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t 
   q.cbase = reinterpret_cast<uint64_t*>(ws + L.cbase);
   q.runstart = reinterpret_cast<int32_t*>(ws + L.rs);
   q.write_rs = 0;
+  q.wbuf = reinterpret_cast<uint64_t*>(ws + L.wbuf);
   q.ncopies = ncopies_dev;
   q.tile_src = reinterpret_cast<int32_t*>(ws + L.tile_src);
   q.nblocks = L.qblocks;

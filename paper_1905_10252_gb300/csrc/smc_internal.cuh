@@ -77,20 +77,20 @@ __device__ __forceinline__ void record_error(DevState* st, int code) {
   atomicCAS(&st->err, 0, code);
 }
 
-// ---------------------------------------------------------------- Philox4x64-10
+// ---------------------------------------------------------------- Philox4x32-10
 struct P4 {
-  uint64_t v[4];
+  uint32_t v[4];
 };
 
-__device__ __forceinline__ P4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
-                                     uint64_t k1) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+__device__ __forceinline__ P4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                     uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
-    const uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
-    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    const uint32_t lo0 = M0 * c0, hi0 = __umulhi(M0, c0);
+    const uint32_t lo1 = M1 * c2, hi1 = __umulhi(M1, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
     c0 = n0;
     c1 = lo1;
     c2 = n2;
@@ -106,10 +106,12 @@ __device__ __forceinline__ P4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint
   return o;
 }
 
-// Block b of the stream of particle i at iteration t: counter (i, t, p<<32|b, 0), key (seed, 0).
+// Block b of the stream of particle i at iteration t: counter
+// (i, t, purpose << 24 | b, 0), key (seed low, seed high); 32-bit word w of the
+// stream is output w % 4 of block w / 4.
 __device__ __forceinline__ P4 stream_block(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i,
                                            uint32_t b) {
-  return philox(i, t, (uint64_t(purpose) << 32) | b, 0, seed, 0);
+  return philox(uint32_t(i), uint32_t(t), (purpose << 24) | b, 0u, uint32_t(seed), uint32_t(seed >> 32));
 }
 
 // ---------------------------------------------------------------- exact FP64 helpers
@@ -183,46 +185,42 @@ __device__ __forceinline__ void det_sincos2pi(uint64_t v, double* s_out, double*
   }
 }
 
-// D standard normals (FP64 path): pair p uses stream words 2p, 2p+1 (top 53
-// bits each); u1 = 1 - a, r = sqrt(-2 log u1), (z0, z1) = r (cos, sin)(2 pi b).
+// D standard normals (FP64 path): pair p uses block p, whose four 32-bit words
+// make the 64-bit words (w0 w1) and (w2 w3); their top 53 bits are a and b;
+// u1 = 1 - a, r = sqrt(-2 log u1), (z0, z1) = r (cos, sin)(2 pi b).
 template <int DMAX>
 __device__ __forceinline__ void normals_f64(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, int d,
                                             double (&z)[DMAX]) {
 #pragma unroll
-  for (int blk = 0; blk < (DMAX + 3) / 4; ++blk) {
-    if (4 * blk < d) {
-      const P4 w = stream_block(seed, t, purpose, i, blk);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int p = 2 * blk + h;  // pair index
-        if (2 * p < d && 2 * p < DMAX) {
-          const uint64_t va = w.v[2 * h] >> 11, vb = w.v[2 * h + 1] >> 11;
-          const double u1 = __dmul_rn(double((1ull << 53) - va), 0x1p-53);
-          const double r = __dsqrt_rn(__dmul_rn(-2.0, det_log(u1)));
-          double sn, cs;
-          det_sincos2pi(vb, &sn, &cs);
-          z[2 * p] = __dmul_rn(r, cs);
-          if (2 * p + 1 < DMAX) z[2 * p + 1] = __dmul_rn(r, sn);
-        }
-      }
+  for (int p = 0; 2 * p < DMAX; ++p) {
+    if (2 * p < d) {
+      const P4 w = stream_block(seed, t, purpose, i, uint32_t(p));
+      const uint64_t va = ((uint64_t(w.v[0]) << 32) | w.v[1]) >> 11;
+      const uint64_t vb = ((uint64_t(w.v[2]) << 32) | w.v[3]) >> 11;
+      const double u1 = __dmul_rn(double((1ull << 53) - va), 0x1p-53);
+      const double r = __dsqrt_rn(__dmul_rn(-2.0, det_log(u1)));
+      double sn, cs;
+      det_sincos2pi(vb, &sn, &cs);
+      z[2 * p] = __dmul_rn(r, cs);
+      if (2 * p + 1 < DMAX) z[2 * p + 1] = __dmul_rn(r, sn);
     }
   }
 }
 
-// D standard normals (FP32 path): pair p uses 64-bit word p, its low and high
-// 32-bit halves giving 24-bit uniforms a, b.
+// D standard normals (FP32 path): pair p uses 32-bit words 2p, 2p+1 (block
+// p / 2), the top 24 bits of each giving the uniforms a, b.
 template <int DMAX>
 __device__ __forceinline__ void normals_f32(uint64_t seed, uint64_t t, uint32_t purpose, uint64_t i, int d,
                                             float (&z)[DMAX]) {
 #pragma unroll
-  for (int blk = 0; blk < (DMAX + 7) / 8; ++blk) {
-    if (8 * blk < d) {
-      const P4 w = stream_block(seed, t, purpose, i, blk);
+  for (int blk = 0; blk < (DMAX + 3) / 4; ++blk) {
+    if (4 * blk < d) {
+      const P4 w = stream_block(seed, t, purpose, i, uint32_t(blk));
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int p = 4 * blk + h;
+      for (int h = 0; h < 2; ++h) {
+        const int p = 2 * blk + h;
         if (2 * p < d && 2 * p < DMAX) {
-          const uint32_t h0 = uint32_t(w.v[h]), h1 = uint32_t(w.v[h] >> 32);
+          const uint32_t h0 = w.v[2 * h], h1 = w.v[2 * h + 1];
           const float u1 = float((1u << 24) - (h0 >> 8)) * 0x1p-24f;
           const float b2 = float(h1 >> 8) * 0x1p-23f;  // 2b, exact
           const float r = sqrtf(-2.0f * logf(u1));
@@ -246,10 +244,12 @@ __device__ __forceinline__ void normals_f32(uint64_t seed, uint64_t t, uint32_t 
 // T (128 entries: T1 ~= 2^63 2^(-j/64), T2 ~= 2^63 2^(-j/4096)) is built on
 // the host from integer square roots and lives in shared memory while a
 // kernel uses it.
-__device__ __forceinline__ uint64_t expfx(double y, const uint64_t* __restrict__ T) {
-  const double a = -y;
-  if (!(a < 44.0)) return 0;
+// Takes a = m - log w >= 0 (one IEEE subtraction, equal to -(log w - m)); the
+// range test is done on the bits (a >= 44, +inf and NaN give 0) so that the
+// only FP64 operation per weight is the caller's subtraction.
+__device__ __forceinline__ uint64_t expfx_a(double a, const uint64_t* __restrict__ T) {
   const uint64_t bits = (uint64_t)__double_as_longlong(a);
+  if (bits >= 0x4046000000000000ull) return 0;  // 44.0 and above (a is never negative)
   const int e = int((bits >> 52) & 0x7ff);
   uint64_t A = 0;
   if (e != 0) {
@@ -275,6 +275,10 @@ __device__ __forceinline__ uint64_t expfx(double y, const uint64_t* __restrict__
   const uint64_t t1 = T[j1], t2 = T[64 + j2];
   const uint64_t Tm = (__umul64hi(t1, t2) << 1) | ((t1 * t2) >> 63);
   return __umul64hi(Tm, P) >> k;
+}
+
+__device__ __forceinline__ uint64_t expfx(double y, const uint64_t* __restrict__ T) {
+  return expfx_a(-y, T);
 }
 
 // floor(X / S) for X < 2^(L+33), S in [2^(L-1), 2^L), with R = floor(2^(63+L)/S):

@@ -60,6 +60,7 @@ struct QuantArgs {
   int32_t* runstart;   // runstart[off_i] = i for every survivor (when write_rs)
   int32_t write_rs;
   int32_t pad;
+  uint64_t* wbuf;      // W_i written by the reduce pass, read by the scan (N words)
   int32_t* ncopies;    // optional output
   int32_t* tile_src;   // source row of the first output row of each redistribute tile
   int32_t nblocks;     // quantise blocks
