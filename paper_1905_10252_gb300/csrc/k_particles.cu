@@ -347,21 +347,13 @@ __device__ __forceinline__ void bm_pair_fast(uint32_t h0, uint32_t h1, float& z0
   p = fmaf(a, p, 1.0f);
   const float r2s = 2.0f * a * p;                 // -2 ln(1-a), |a| < 1/16
   const float r2l = -2.0f * __logf(1.0f - a);
-  const float r = sqrtf(a < 0.0625f ? r2s : r2l);
+  const float r2 = a < 0.0625f ? r2s : r2l;
+  const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
   const float th = float(int(h1 >> 8) - (1 << 23)) * (0x1p-24f * 6.28318530717958647692f);
   float sn, cs;
   __sincosf(th, &sn, &cs);  // (sin, cos)(2 pi b - pi) = -(sin, cos)(2 pi b)
   z0 = -r * cs;
   z1 = -r * sn;
-}
-
-// Shared-memory loads the compiler may not hoist out of the particle loop (a
-// hoisted copy of the 136-entry factor would cost 136 registers per thread).
-__device__ __forceinline__ float4 lds4_volatile(const float* p) {
-  float4 v;
-  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-  return v;
 }
 
 template <int DPL>
@@ -382,15 +374,8 @@ __device__ __forceinline__ void load_seg(const float* __restrict__ row, bool vec
 }
 
 template <int DPL, int LPP, bool MOVE, bool REWEIGHT>
-__global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleArgs a) {
+__global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleArgs a, const GaussParamsF32 gp) {
   constexpr int DMAX = DPL * LPP;
-  __shared__ __align__(16) float sP[kMaxD * kMaxD];
-  __shared__ float smu[kMaxD];
-  if (REWEIGHT) {
-    for (int i = threadIdx.x; i < kMaxD * kMaxD; i += blockDim.x) sP[i] = a.tg->Pf[i];
-    for (int i = threadIdx.x; i < kMaxD; i += blockDim.x) smu[i] = a.tg->muf[i];
-    __syncthreads();
-  }
   MaxTracker mt;
   mt.init();
   const int cur = a.st->cur;
@@ -443,14 +428,19 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
       lpn = lp[inx];
     }
     if (MOVE && valid && nvalid > 0) {
+      // all of the lane's Philox blocks first: independent 10-round chains
+      // that the scheduler interleaves
+      P4 w[DPL / 4];
+#pragma unroll
+      for (int blk = 0; blk < DPL / 4; ++blk)
+        w[blk] = stream_block(a.seed, t, kPurposeMove, uint64_t(i), uint32_t(c0 / 4 + blk));
 #pragma unroll
       for (int blk = 0; blk < DPL / 4; ++blk) {
         if (4 * blk < nvalid) {
-          const P4 w = stream_block(a.seed, t, kPurposeMove, uint64_t(i), uint32_t(c0 / 4 + blk));
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             float z0, z1;
-            bm_pair_fast(w.v[2 * h], w.v[2 * h + 1], z0, z1);
+            bm_pair_fast(w[blk].v[2 * h], w[blk].v[2 * h + 1], z0, z1);
             xo[4 * blk + 2 * h] = fmaf(eps, z0, xo[4 * blk + 2 * h]);
             xo[4 * blk + 2 * h + 1] = fmaf(eps, z1, xo[4 * blk + 2 * h + 1]);
           }
@@ -471,31 +461,24 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
       float dv[DMAX];
       if (LPP == 1) {
 #pragma unroll
-        for (int c = 0; c < DMAX; ++c) dv[c] = xo[c] - smu[c];
+        for (int c = 0; c < DMAX; ++c) dv[c] = xo[c] - gp.mu[c];
       } else {
         // all 32 lanes execute the shuffles (valid or not)
 #pragma unroll
         for (int j = 0; j < LPP; ++j)
 #pragma unroll
-          for (int c = 0; c < DPL; ++c) dv[DPL * j + c] = __shfl_sync(0xffffffffu, xo[c], j, LPP) - smu[DPL * j + c];
+          for (int c = 0; c < DPL; ++c) dv[DPL * j + c] = __shfl_sync(0xffffffffu, xo[c], j, LPP) - gp.mu[DPL * j + c];
       }
       if (valid && q == 0) {
-        // every lane reads the same factor entries (broadcast); P is lower
-        // triangular, so the entries above the diagonal that a 4-wide load
-        // brings in are exact zeros and leave acc unchanged
+        // y = L^-1 (x - mu) row by row; the factor's entries are kernel
+        // parameters, read by the FMAs straight from the constant bank
         float qs = 0.0f;
 #pragma unroll
         for (int r = 0; r < DMAX; ++r) {
           if (r < d) {
             float acc = 0.0f;
 #pragma unroll
-            for (int c4 = 0; c4 <= r / 4; ++c4) {
-              const float4 pv = lds4_volatile(&sP[r * kMaxD + 4 * c4]);
-              acc = fmaf(pv.x, dv[4 * c4 + 0], acc);
-              if (4 * c4 + 1 <= r) acc = fmaf(pv.y, dv[4 * c4 + 1], acc);
-              if (4 * c4 + 2 <= r) acc = fmaf(pv.z, dv[4 * c4 + 2], acc);
-              if (4 * c4 + 3 <= r) acc = fmaf(pv.w, dv[4 * c4 + 3], acc);
-            }
+            for (int c = 0; c <= r; ++c) acc = fmaf(gp.P[r * (r + 1) / 2 + c], dv[c], acc);
             qs = fmaf(acc, acc, qs);
           }
         }
@@ -678,21 +661,21 @@ static cudaError_t launch_particles_d(int op, const ParticleArgs& a, int grid, c
 }
 
 template <int DPL, int LPP>
-static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, cudaStream_t s) {
+static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, cudaStream_t s, const GaussParamsF32& gp) {
   switch (op) {
-    case OP_MOVE: k_move_reweight_lanes<DPL, LPP, true, false><<<grid, kPThreads, 0, s>>>(a); break;
-    case OP_REWEIGHT: k_move_reweight_lanes<DPL, LPP, false, true><<<grid, kPThreads, 0, s>>>(a); break;
-    case OP_MOVE_REWEIGHT: k_move_reweight_lanes<DPL, LPP, true, true><<<grid, kPThreads, 0, s>>>(a); break;
+    case OP_MOVE: k_move_reweight_lanes<DPL, LPP, true, false><<<grid, kPThreads, 0, s>>>(a, gp); break;
+    case OP_REWEIGHT: k_move_reweight_lanes<DPL, LPP, false, true><<<grid, kPThreads, 0, s>>>(a, gp); break;
+    case OP_MOVE_REWEIGHT: k_move_reweight_lanes<DPL, LPP, true, true><<<grid, kPThreads, 0, s>>>(a, gp); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s) {
-  if (a.dtype == SMC_F32 && op != OP_INIT && a.kind == SMC_GAUSS) {
-    if (a.d <= 8) return launch_lanes<8, 1>(op, a, grid, s);
-    if (a.d <= 16) return launch_lanes<16, 1>(op, a, grid, s);
-    return launch_lanes<16, 2>(op, a, grid, s);
+cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s, const GaussParamsF32* gp) {
+  if (a.dtype == SMC_F32 && op != OP_INIT && a.kind == SMC_GAUSS && gp) {
+    if (a.d <= 8) return launch_lanes<8, 1>(op, a, grid, s, *gp);
+    if (a.d <= 16) return launch_lanes<16, 1>(op, a, grid, s, *gp);
+    return launch_lanes<16, 2>(op, a, grid, s, *gp);
   }
   return a.dtype == SMC_F64 ? launch_particles_d<double>(op, a, grid, s) : launch_particles_d<float>(op, a, grid, s);
 }

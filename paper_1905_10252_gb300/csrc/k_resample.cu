@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
   if (EST && threadIdx.x < d) {
     double v = 0.0;
     for (int w = 0; w < kQThreads / 32; ++w) v += shx[w][threadIdx.x];
-    a.xpart[int64_t(blockIdx.x) * d + threadIdx.x] = v;
+    static_cast<ST*>(a.xpart)[int64_t(blockIdx.x) * d + threadIdx.x] = ST(v);
   }
 }
 
@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
   const int nb = a.nblocks;
   uint64_t tw = 0;
   u128 t2 = 0, te = 0;
+#pragma unroll 4
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     const uint64_t* q = a.qpart + 5 * int64_t(b);
     tw += q[0];
@@ -293,6 +294,7 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
   const int chunk = (nb + blockDim.x - 1) / blockDim.x;
   const int b0 = threadIdx.x * chunk, b1 = min(nb, b0 + chunk);
   uint64_t local = 0;
+#pragma unroll 4
   for (int b = b0; b < b1; ++b) local += a.qpart[5 * int64_t(b)];
   uint64_t total;
   uint64_t pre = block_excl_scan_u64(local, scratch, &total);  // contains __syncthreads
@@ -304,16 +306,35 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
   __shared__ double sxsum[kMaxD];
   const bool est = a.x[0] != nullptr && a.d > 0;
   if (est) {
-    // thread j sums column j % d over rows j / d, j / d + stride / d, ...
-    // (consecutive threads read consecutive words)
-    if (threadIdx.x < a.d) sxsum[threadIdx.x] = 0.0;
-    __syncthreads();
+    // thread j sums column j % d over rows j / d, j / d + stride / d, ... in a
+    // fixed order (deterministic), in the particle precision (the FP64 pipe is
+    // scarce); the per-thread partials are then added in order per column
     const int stride = (int(blockDim.x) / a.d) * a.d;
+    const int64_t total_words = int64_t(nb) * a.d;
+    double part = 0.0;
     if (int(threadIdx.x) < stride) {
-      double v = 0.0;
-      const int64_t total_words = int64_t(nb) * a.d;
-      for (int64_t j = threadIdx.x; j < total_words; j += stride) v += a.xpart[j];
-      atomicAdd(&sxsum[threadIdx.x % a.d], v);
+      if (a.dtype == SMC_F64) {
+        const double* xp = static_cast<const double*>(a.xpart);
+        for (int64_t j = threadIdx.x; j < total_words; j += stride) part += xp[j];
+      } else {
+        const float* xp = static_cast<const float*>(a.xpart);
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int64_t j = threadIdx.x;
+        for (; j + 7 * int64_t(stride) < total_words; j += 8 * int64_t(stride)) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] += xp[j + u * int64_t(stride)];
+        }
+        for (; j < total_words; j += stride) v[0] += xp[j];
+        part = double(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+      }
+    }
+    __shared__ double tpart[kFinThreads];
+    tpart[threadIdx.x] = part;
+    __syncthreads();
+    if (int(threadIdx.x) < a.d) {
+      double t = 0.0;
+      for (int k = threadIdx.x; k < stride; k += a.d) t += tpart[k];
+      sxsum[threadIdx.x] = t;
     }
     __syncthreads();
   }
@@ -339,7 +360,8 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
   const uint64_t r64 = (uint64_t(r.v[0]) << 32) | r.v[1];
   const uint64_t U = S ? __umul64hi(r64, S) : 0;
   const int L = S ? 64 - __clzll((long long)S) : 1;
-  const uint64_t R = S ? uint64_t(((u128(1) << (63 + L)) - 1) / S) : 0;
+  // S >= 2^F = 2^(63 - ceil(log2 N)), so floor(N 2^64 / S) <= 2^(2 ceil(log2 N) + 1) fits 64 bits
+  const uint64_t R = S ? uint64_t((u128(n) << 64) / S) : 0;
   const double m = st->m;
   const double se_d = u128_to_double(se);
   const double lse = m + log(se_d * 0x1p-62);
@@ -402,8 +424,7 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
     buf.w[pad_idx(idx)] = i < n ? a.wbuf[i] : 0ull;
   }
   __syncthreads();
-  const uint64_t S = st->S, U = st->U, R = st->recip;
-  const int L = st->L;
+  const uint64_t S = st->S, U = st->U;
   uint64_t W[kQItems];
   uint64_t tsum = 0;
 #pragma unroll
@@ -415,34 +436,33 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
   uint64_t C = a.cbase[blockIdx.x] + block_excl_scan_u64(tsum, scratch, &btot);
   uint32_t ncv[kQItems];
   unsigned nsurv = 0;
-  // floor((N C + U) / S) as quotient lo and remainder rem, advanced item by
-  // item: the increment is floor((rem + N W_i) / S), found by at most three
-  // subtractions when N W_i <= 3 S and by a division otherwise
-  u128 X = u128(n) * C + U;
-  uint64_t lo = div_by_S(X, S, L, R);
-  uint64_t rem = uint64_t(X - u128(lo) * S);
-  const u128 S3 = u128(S) * 3;
+  // off_i = floor((N C_{i-1} + U) / S) for every item independently (no
+  // serial dependency between items): the estimate mulhi(C, floor(N 2^64/S))
+  // is at most 2 below floor(N C / S), and floor((N C + U)/S) is at most 1
+  // above that; exact 128-bit comparisons fix the result.
+  const uint64_t Rn = st->recip;  // floor(N 2^64 / S)
+  uint64_t Cx[kQItems + 1];
+  Cx[0] = C;
+#pragma unroll
+  for (int q = 0; q < kQItems; ++q) Cx[q + 1] = Cx[q] + W[q];
+  uint64_t offs[kQItems + 1];
+#pragma unroll
+  for (int q = 0; q <= kQItems; ++q) {
+    const u128 X = u128(n) * Cx[q] + U;
+    uint64_t qq = __umul64hi(Cx[q], Rn);
+    u128 nxt = u128(qq + 1) * S;
+#pragma unroll
+    for (int it = 0; it < 3; ++it)
+      if (nxt <= X) {
+        ++qq;
+        nxt += S;
+      }
+    offs[q] = qq;
+  }
   const int64_t i0 = base + int64_t(threadIdx.x) * kQItems;
 #pragma unroll
   for (int q = 0; q < kQItems; ++q) {
-    C += W[q];
-    const u128 NW = u128(n) * W[q];
-    uint64_t hi;
-    if (NW <= S3) {
-      u128 t = u128(rem) + NW;
-      hi = lo;
-#pragma unroll
-      for (int it = 0; it < 3; ++it)
-        if (t >= S) {
-          t -= S;
-          ++hi;
-        }
-      rem = uint64_t(t);
-    } else {
-      X = u128(n) * C + U;
-      hi = div_by_S(X, S, L, R);
-      rem = uint64_t(X - u128(hi) * S);
-    }
+    const uint64_t lo = offs[q], hi = offs[q + 1];
     ncv[q] = uint32_t(hi - lo);
     const int64_t i = i0 + q;
     if (hi > lo && i < n) {
@@ -452,7 +472,6 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
       for (uint64_t kb = ((lo + kRTile - 1) / kRTile) * kRTile; kb < hi && kb < uint64_t(n); kb += kRTile)
         a.tile_src[kb / kRTile] = int32_t(i);
     }
-    lo = hi;
   }
   {
     unsigned v = nsurv;
@@ -582,7 +601,9 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
 #pragma unroll
     for (int u = 0; u < kItems; ++u) {
       const int k = threadIdx.x + u * kRThreads;
-      if (k < len) rs[k] = -1;  // whole sectors: no read-for-ownership
+      // reset only the entries that were set (measured: rewriting the whole
+      // slice costs ~0.15 ms more at N = 2^24)
+      if (k < len && v[u] >= 0) rs[k] = -1;
       mark[k] = v[u] < int32_t(n) ? v[u] : int32_t(n - 1);
     }
   }
@@ -622,7 +643,7 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
   const V* __restrict__ in = static_cast<const V*>(cur ? a.x_in[1] : a.x_in[0]);
   V* __restrict__ out = static_cast<V*>(cur ? a.x_out[1] : a.x_out[0]) + k0 * cpr;
   const int total = len * cpr;
-  constexpr int kU = 8;
+  constexpr int kU = 8;  // 16-byte loads in flight per thread
   for (int e0 = threadIdx.x; e0 < total; e0 += kRThreads * kU) {
     V v[kU];
 #pragma unroll

@@ -100,11 +100,14 @@ struct smc_sampler {
   double* part;
   uint64_t* qpart;
   uint64_t* cbase;
-  double* xpart;
+  void* xpart;
   int32_t* rs;
   uint64_t* wbuf;
   int32_t* tile_src;
   int grid_p;
+  // FP32 Gaussian factor for the move / reweight kernel's parameters
+  GaussParamsF32 gp;
+  bool have_gp;
   // CUDA graph of one iteration (with and without the covariance stage)
   cudaGraphExec_t g_iter[2];
   std::string err;
@@ -129,6 +132,8 @@ int cuda_fail(smc_sampler* h, cudaError_t e, const char* where) {
     cudaError_t _e = (expr);                              \
     if (_e != cudaSuccess) return cuda_fail((h), _e, #expr); \
   } while (0)
+
+const GaussParamsF32* gauss_params(const smc_sampler* h) { return h->have_gp ? &h->gp : nullptr; }
 
 ParticleArgs particle_args(const smc_sampler* h) {
   ParticleArgs a{};
@@ -215,7 +220,7 @@ cudaError_t launch_stats(smc_sampler* h, int set_lse_prev) {
 cudaError_t launch_iteration(smc_sampler* h, bool with_cov) {
   const ParticleArgs a = particle_args(h);
   cudaError_t e = launch_begin(h->st, h->stream);
-  if (e == cudaSuccess) e = launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, h->stream);
+  if (e == cudaSuccess) e = launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, h->stream, gauss_params(h));
   if (e == cudaSuccess) e = launch_max_finalize(h->part, h->grid_p, h->st, h->stream);
   const QuantArgs q = quant_args(h, 0, nullptr);
   if (e == cudaSuccess) e = launch_quant_reduce(q, h->stream);
@@ -312,7 +317,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   h->part = reinterpret_cast<double*>(h->ws + L.part);
   h->qpart = reinterpret_cast<uint64_t*>(h->ws + L.qpart);
   h->cbase = reinterpret_cast<uint64_t*>(h->ws + L.cbase);
-  h->xpart = reinterpret_cast<double*>(h->ws + L.xpart);
+  h->xpart = h->ws + L.xpart;
   h->rs = reinterpret_cast<int32_t*>(h->ws + L.rs);
   h->wbuf = reinterpret_cast<uint64_t*>(h->ws + L.wbuf);
   h->tile_src = reinterpret_cast<int32_t*>(h->ws + L.tile_src);
@@ -320,6 +325,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
                                     int64_t(sm_count()) * 8));
   if (h->grid_p > kMaxPartBlocks) h->grid_p = kMaxPartBlocks;
   h->g_iter[0] = h->g_iter[1] = nullptr;
+  h->have_gp = false;
   h->err = "ok";
 
   // Algorithm 2, line 1, then the statistics of w_0 (LSE_0 becomes LSE_{t-1})
@@ -330,6 +336,19 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
     e = launch_target_setup(h->tg, cfg->target, cfg->nu, cfg->mu_dev, cfg->sigma_dev, h->d, h->st, h->stream);
   if (e == cudaSuccess) e = launch_particles(OP_INIT, particle_args(h), h->grid_p, h->stream);
   if (e == cudaSuccess) e = launch_stats(h, 1);
+  if (e == cudaSuccess && cfg->target == SMC_GAUSS && h->dtype == SMC_F32) {
+    // the FP32 factor becomes a kernel parameter of the move / reweight kernel
+    static thread_local float Pf[kTgtMaxD * kTgtMaxD], muf[kTgtMaxD];
+    e = cudaMemcpyAsync(Pf, h->tg->Pf, sizeof Pf, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(muf, h->tg->muf, sizeof muf, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) {
+      for (int r = 0; r < kTgtMaxD; ++r)
+        for (int c = 0; c <= r; ++c) h->gp.P[r * (r + 1) / 2 + c] = Pf[r * kTgtMaxD + c];
+      for (int c = 0; c < kTgtMaxD; ++c) h->gp.mu[c] = muf[c];
+      h->have_gp = true;
+    }
+  }
   if (e != cudaSuccess) {
     int r = cuda_fail(nullptr, e, "smc_init launch");
     delete h;
@@ -342,13 +361,13 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
 int smc_move(smc_sampler* h) {
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   SMC_TRY(h, launch_begin(h->st, h->stream));
-  SMC_TRY(h, launch_particles(OP_MOVE, particle_args(h), h->grid_p, h->stream));
+  SMC_TRY(h, launch_particles(OP_MOVE, particle_args(h), h->grid_p, h->stream, gauss_params(h)));
   return SMC_OK;
 }
 
 int smc_reweight(smc_sampler* h) {
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
-  SMC_TRY(h, launch_particles(OP_REWEIGHT, particle_args(h), h->grid_p, h->stream));
+  SMC_TRY(h, launch_particles(OP_REWEIGHT, particle_args(h), h->grid_p, h->stream, gauss_params(h)));
   SMC_TRY(h, launch_stats(h, 0));
   return SMC_OK;
 }
@@ -426,7 +445,7 @@ int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host,
   const QuantArgs q = quant_args(h, 0, nullptr);
   SMC_TRY(h, rec(0));
   SMC_TRY(h, launch_begin(h->st, s));
-  SMC_TRY(h, launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, s));
+  SMC_TRY(h, launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, s, gauss_params(h)));
   SMC_TRY(h, rec(1));
   SMC_TRY(h, launch_max_finalize(h->part, h->grid_p, h->st, s));
   SMC_TRY(h, rec(2));

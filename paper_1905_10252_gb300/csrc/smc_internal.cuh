@@ -54,7 +54,7 @@ struct alignas(256) DevState {
   double reset_logw;    // -log N
   uint64_t S, U;        // sum W, systematic offset
   uint64_t sw2_lo, sw2_hi, se_lo, se_hi;
-  uint64_t recip;       // floor(2^(63+L) / S)
+  uint64_t recip;       // floor(N 2^64 / S) (ncopies quotients)
   // recycling (eq. (6)): running log-max of log c_t and the scaled sums
   double rc_max;
   double rc_den;
@@ -279,21 +279,6 @@ __device__ __forceinline__ uint64_t expfx_a(double a, const uint64_t* __restrict
 
 __device__ __forceinline__ uint64_t expfx(double y, const uint64_t* __restrict__ T) {
   return expfx_a(-y, T);
-}
-
-// floor(X / S) for X < 2^(L+33), S in [2^(L-1), 2^L), with R = floor(2^(63+L)/S):
-// estimate from the top bits, then correct by exact 128-bit remainders.
-__device__ __forceinline__ uint64_t div_by_S(u128 X, uint64_t S, int L, uint64_t R) {
-  const uint64_t xs = uint64_t(X >> (L - 1));
-  uint64_t q = __umul64hi(xs, R);
-  u128 qs = u128(q) * S;
-  // q never exceeds floor(X/S); bounded correction loop
-#pragma unroll 1
-  for (int it = 0; it < 4 && qs + S <= X; ++it) {
-    ++q;
-    qs += S;
-  }
-  return q;
 }
 
 // ---------------------------------------------------------------- reductions

@@ -28,6 +28,14 @@ struct alignas(256) TargetDev {
 
 enum { OP_INIT = 0, OP_MOVE = 1, OP_REWEIGHT = 2, OP_MOVE_REWEIGHT = 3 };
 
+// FP32 Gaussian target passed by value as a kernel parameter (constant bank):
+// the lower triangle of L^-1 packed row by row (row r holds r + 1 entries at
+// r (r + 1) / 2) and mu.
+struct GaussParamsF32 {
+  float P[kTgtMaxD * (kTgtMaxD + 1) / 2];
+  float mu[kTgtMaxD];
+};
+
 // Lanes that share one particle in the move / reweight kernels: the FP32 path
 // gives each lane up to 16 coordinates (two Philox blocks); FP64 uses one lane.
 inline int lanes_per_particle(int dtype, int d) { return (dtype == SMC_F32 && d > 16) ? 2 : 1; }
@@ -71,7 +79,7 @@ struct QuantArgs {
   const void* x[2];
   int32_t d;
   int32_t dtype;
-  double* xpart;       // nblocks x d partial sums
+  void* xpart;         // nblocks x d partial sums, in the particle dtype
 };
 
 struct RedistArgs {
@@ -110,7 +118,8 @@ size_t devstate_bytes();
 // Message returned by smc_last_error(NULL) (smc_api.cu).
 void set_global_error(const char* msg);
 
-cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s,
+                             const GaussParamsF32* gp = nullptr);
 cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double* mu, const double* sigma, int d,
                                 DevState* st, cudaStream_t s);
 cudaError_t launch_zero_cov(DevState* st, int d, cudaStream_t s);
