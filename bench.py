@@ -62,6 +62,38 @@ def dist_setup():
     return ws, rank, local
 
 
+STAGE_SOURCES = {
+    "move_reweight": ["k_particles.cu", "smc_internal.cuh"],
+    "quantise_reduce_estimate": ["k_resample.cu", "smc_internal.cuh"],
+    "systematic_scan": ["k_resample.cu", "smc_internal.cuh"],
+    "redistribute": ["k_resample.cu", "smc_internal.cuh"],
+}
+
+
+def measured_traffic():
+    """DRAM bytes per particle per stage from profiles/traffic.md, kept only
+    while the stage's kernel sources are the ones that were captured."""
+    import hashlib
+
+    out = {}
+    try:
+        lines = open(os.path.join(ROOT, "profiles", "traffic.md")).read().splitlines()
+    except OSError:
+        return out
+    csrc = os.path.join(ROOT, "paper_1905_10252_gb300", "csrc")
+    for line in lines:
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) != 7 or cells[0] not in STAGE_SOURCES:
+            continue
+        h = hashlib.sha256()
+        for f in STAGE_SOURCES[cells[0]]:
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] == cells[2]:
+            out[cells[0]] = float(cells[6])
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -198,6 +230,26 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- GPU arm
+def max_over_ranks(local_ms: float, world_size: int, device="cpu") -> float:
+    """The step time of the whole job: the slowest rank's (replicas of the
+    sampler run independently; this is the only collective, outside the
+    timed region)."""
+    if world_size <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(local_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_per_rank: int, steps: int, world_size: int, total_ms: float) -> float:
+    """Whole-job particle-iterations per second (weak scaling: every rank runs
+    its own N-particle sampler)."""
+    return n_per_rank * steps * world_size / (total_ms * 1e-3)
+
+
 def algorithmic_bytes(n: int, d: int, esize: int, survivors: float):
     """Per-launch algorithmic bytes of each stage (see the measurement section
     of the design notes): reads + writes the definition of the stage needs."""
@@ -260,11 +312,7 @@ def run_iteration(args):
         dist.barrier()
     time.sleep(0.15)
     clocks.stop()
-    total_ms = start.elapsed_time(stop)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(start.elapsed_time(stop), ws, device="cuda")
     per_stage = {name: [] for name in STAGES}
     for row in ev:
         for j, name in enumerate(STAGES):
@@ -275,13 +323,15 @@ def run_iteration(args):
     byt = algorithmic_bytes(n, d, 4, survivors)
     peak, peak_kind = peaks()
     dominant = max(stage_ms, key=stage_ms.get)
+    traffic = measured_traffic()
 
     def roof(name):
         if name not in byt:
             return None
         gbs = byt[name] / (stage_ms[name] * 1e-3) / 1e9
+        tr = int(traffic[name] * n) if name in traffic else None
         return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(gbs / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "frac": round(gbs / peak, 4), "traffic": tr, "peak_kind": peak_kind,
                 "bytes_per_launch": int(byt[name]), "ms_per_launch": round(stage_ms[name], 5)}
 
     # end to end through the public API with host buffers: pinned H2D of the
@@ -315,7 +365,7 @@ def run_iteration(args):
                "h2d_bytes_per_step": int(x_h.nbytes + lp_h.nbytes + lw_h.nbytes),
                "d2h_bytes_per_step": int(mean_h.nbytes), "ms_per_step": e_ms / args.e2e_steps}
     S.sync()
-    value = n * K * ws / (total_ms * 1e-3)
+    value = job_value(n, K, ws, total_ms)
     launches_per_step = 8
     if rank == 0:
         line = {
