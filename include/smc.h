@@ -217,6 +217,64 @@ int smc_ws_status(void* ws_dev, smc_stream_t stream);
 int smc_redistribute_raw_noalloc(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
                                  void* out_dev, int32_t* status_dev, smc_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent samplers stepped together, one launch per stage
+ * for all of them (Algorithm 2, lines 3-10, for every member at once).  The
+ * paper runs one sampler at a time; batching is an addition for workloads of
+ * many small samplers, where one sampler per launch leaves the GPU idle
+ * between tiny kernels.  Every member's results are bit-identical to those
+ * of smc_step on that sampler alone: each member keeps its own blocks, tiles,
+ * partial sums and reduction order; only the launch is shared.
+ *
+ * Members are handles from smc_init with dtype SMC_F32 and target SMC_GAUSS
+ * (the FP32 move / reweight kernel), all on the current device, each listed
+ * once.  A handle must not be stepped by itself, nor be a member of another
+ * batch, while the batch is in use.  smc_batch_create synchronises every
+ * member's stream once; afterwards the batch works on its own stream, and
+ * smc_batch_sync must return before a member's own calls (smc_read_stats,
+ * smc_current, ...) see the batch's results.
+ *
+ * ws_dev: smc_batch_ws_bytes(...) bytes of device memory, 256-byte aligned,
+ * owned by the caller and alive until smc_batch_destroy.  It holds the
+ * members' kernel arguments and the block maps of the launches. */
+typedef struct smc_batch smc_batch;
+
+int smc_batch_ws_bytes(smc_sampler* const* members, int32_t count, size_t* bytes);
+int smc_batch_create(smc_batch** out, smc_sampler* const* members, int32_t count, void* ws_dev,
+                     size_t ws_bytes, smc_stream_t stream);
+
+/* k iterations for every member.  mean_dev / trace_dev / fhat_dev are NULL or
+ * HOST arrays of count DEVICE pointers (entries may be NULL) with the meaning
+ * smc_step gives its arguments of those names, per member.  Iterations are
+ * replayed from a CUDA graph of one batched iteration (8 launches). */
+int smc_batch_step(smc_batch* b, int32_t k, double* const* mean_dev, smc_iter_stats* const* trace_dev,
+                   double* const* fhat_dev);
+
+/* Launch-shape variants.  None changes any result.  move_variant picks how
+ * many blocks share the move / reweight launch (0: 2 per SM, 1: 4, 2: 8,
+ * 3: 16, 4: one thread per particle), which fixes the particles each warp
+ * handles; copy_variant picks the 16-byte loads each thread keeps in flight
+ * in the redistribute copy (0: 4, 1: 8, 2: 16).  Defaults: 2 and 1. */
+#define SMC_BATCH_MOVE_VARIANTS 5
+#define SMC_BATCH_COPY_VARIANTS 3
+int smc_batch_set_variant(smc_batch* b, int32_t move_variant, int32_t copy_variant);
+
+/* Autotuner: times every variant reps times (CUDA events, median) on work
+ * that leaves every member's state untouched -- the move on the members'
+ * spare buffers, the copy as an in-place identity copy -- then keeps the
+ * fastest of each.  Writes {move_variant, copy_variant} to choice_host when
+ * not NULL.  Synchronises the batch's stream. */
+int smc_batch_tune(smc_batch* b, int32_t reps, int32_t* choice_host);
+
+/* Synchronises the batch's stream; returns (then clears) the first device
+ * error recorded by any member, with the member's index in which_host
+ * (-1 when none; may be NULL). */
+int smc_batch_sync(smc_batch* b, int32_t* which_host);
+
+/* Frees the handle (host memory only); members stay valid. */
+int smc_batch_destroy(smc_batch* b);
+const char* smc_batch_last_error(const smc_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

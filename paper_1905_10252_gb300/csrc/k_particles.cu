@@ -181,8 +181,8 @@ __device__ __forceinline__ long long warp_max_ll(long long v) {
   return v;
 }
 
-// One record per block: part[2b] = max log w of the block, part[2b+1] = 1.
-__device__ __forceinline__ void block_write_max(const MaxTracker& mt, double* __restrict__ part, DevState* st) {
+// One record per block: rec[0] = max log w of the block, rec[1] = 1.
+__device__ __forceinline__ void block_write_max(const MaxTracker& mt, double* __restrict__ rec, DevState* st) {
   __shared__ long long shm[kPThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (mt.nan) record_error(st, SMC_ENONFINITE);
@@ -192,8 +192,8 @@ __device__ __forceinline__ void block_write_max(const MaxTracker& mt, double* __
   if (threadIdx.x == 0) {
     long long v = shm[0];
     for (int w = 1; w < nw; ++w) v = shm[w] > v ? shm[w] : v;
-    part[2 * blockIdx.x] = from_ordered_key(v);
-    part[2 * blockIdx.x + 1] = 1.0;
+    rec[0] = from_ordered_key(v);
+    rec[1] = 1.0;
   }
 }
 
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kPThreads) k_init(ParticleArgs a) {
     a.logw[i] = lw;
     mt.add(lw);
   }
-  block_write_max(mt, a.part, a.st);
+  block_write_max(mt, a.part + 2 * blockIdx.x, a.st);
 }
 
 // ---------------------------------------------------------------- move + reweight
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
       mt.add(lw);
     }
   }
-  if (REWEIGHT) block_write_max(mt, a.part, a.st);
+  if (REWEIGHT) block_write_max(mt, a.part + 2 * blockIdx.x, a.st);
 }
 
 // ---------------------------------------------------------------- move + reweight, FP32 fast path
@@ -373,8 +373,22 @@ __device__ __forceinline__ void load_seg(const float* __restrict__ row, bool vec
   }
 }
 
-template <int DPL, int LPP, bool MOVE, bool REWEIGHT>
-__global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleArgs a, const GaussParamsF32 gp) {
+// Where the FP32 factor comes from: the kernel parameters (one sampler per
+// launch; the FMAs read the constant bank) or shared memory (batched launches).
+struct FactorParam {
+  const GaussParamsF32& g;
+  __device__ __forceinline__ float P(int i) const { return g.P[i]; }
+  __device__ __forceinline__ float mu(int c) const { return g.mu[c]; }
+};
+struct FactorSmem {
+  const float* p;
+  const float* m;
+  __device__ __forceinline__ float P(int i) const { return p[i]; }
+  __device__ __forceinline__ float mu(int c) const { return m[c]; }
+};
+
+template <int DPL, int LPP, bool MOVE, bool REWEIGHT, typename FS>
+__device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const FS gp, const int blk, const int nblk) {
   constexpr int DMAX = DPL * LPP;
   MaxTracker mt;
   mt.init();
@@ -392,8 +406,8 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
   // The loop runs over whole warps (its bound is warp-uniform) so that every
   // lane reaches the group shuffles; lanes past the end are predicated.
   constexpr int kGroups = 32 / LPP;
-  const int64_t warp_global = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t step = int64_t(gridDim.x) * (blockDim.x >> 5) * kGroups;
+  const int64_t warp_global = (int64_t(blk) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t step = int64_t(nblk) * (blockDim.x >> 5) * kGroups;
   const int grp = (threadIdx.x & 31) / LPP;
   int64_t base = warp_global * kGroups;
   // prologue: the first particle's data
@@ -432,17 +446,17 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
       // that the scheduler interleaves
       P4 w[DPL / 4];
 #pragma unroll
-      for (int blk = 0; blk < DPL / 4; ++blk)
-        w[blk] = stream_block(a.seed, t, kPurposeMove, uint64_t(i), uint32_t(c0 / 4 + blk));
+      for (int b4 = 0; b4 < DPL / 4; ++b4)
+        w[b4] = stream_block(a.seed, t, kPurposeMove, uint64_t(i), uint32_t(c0 / 4 + b4));
 #pragma unroll
-      for (int blk = 0; blk < DPL / 4; ++blk) {
-        if (4 * blk < nvalid) {
+      for (int b4 = 0; b4 < DPL / 4; ++b4) {
+        if (4 * b4 < nvalid) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             float z0, z1;
-            bm_pair_fast(w[blk].v[2 * h], w[blk].v[2 * h + 1], z0, z1);
-            xo[4 * blk + 2 * h] = fmaf(eps, z0, xo[4 * blk + 2 * h]);
-            xo[4 * blk + 2 * h + 1] = fmaf(eps, z1, xo[4 * blk + 2 * h + 1]);
+            bm_pair_fast(w[b4].v[2 * h], w[b4].v[2 * h + 1], z0, z1);
+            xo[4 * b4 + 2 * h] = fmaf(eps, z0, xo[4 * b4 + 2 * h]);
+            xo[4 * b4 + 2 * h + 1] = fmaf(eps, z1, xo[4 * b4 + 2 * h + 1]);
           }
         }
       }
@@ -461,13 +475,13 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
       float dv[DMAX];
       if (LPP == 1) {
 #pragma unroll
-        for (int c = 0; c < DMAX; ++c) dv[c] = xo[c] - gp.mu[c];
+        for (int c = 0; c < DMAX; ++c) dv[c] = xo[c] - gp.mu(c);
       } else {
         // all 32 lanes execute the shuffles (valid or not)
 #pragma unroll
         for (int j = 0; j < LPP; ++j)
 #pragma unroll
-          for (int c = 0; c < DPL; ++c) dv[DPL * j + c] = __shfl_sync(0xffffffffu, xo[c], j, LPP) - gp.mu[DPL * j + c];
+          for (int c = 0; c < DPL; ++c) dv[DPL * j + c] = __shfl_sync(0xffffffffu, xo[c], j, LPP) - gp.mu(DPL * j + c);
       }
       if (valid && q == 0) {
         // y = L^-1 (x - mu) row by row; the factor's entries are kernel
@@ -478,7 +492,7 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
           if (r < d) {
             float acc = 0.0f;
 #pragma unroll
-            for (int c = 0; c <= r; ++c) acc = fmaf(gp.P[r * (r + 1) / 2 + c], dv[c], acc);
+            for (int c = 0; c <= r; ++c) acc = fmaf(gp.P(r * (r + 1) / 2 + c), dv[c], acc);
             qs = fmaf(acc, acc, qs);
           }
         }
@@ -496,14 +510,40 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
     lwc = lwn;
     lpc = lpn;
   }
-  if (REWEIGHT) block_write_max(mt, a.part, a.st);
+  if (REWEIGHT) block_write_max(mt, a.part + 2 * blk, a.st);
+}
+
+template <int DPL, int LPP, bool MOVE, bool REWEIGHT>
+__global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleArgs a, const GaussParamsF32 gp) {
+  move_reweight_body<DPL, LPP, MOVE, REWEIGHT>(a, FactorParam{gp}, blockIdx.x, gridDim.x);
+}
+
+// Batched: block b runs block map[b].y of map[b].z of sampler map[b].x; the
+// sampler's packed factor is staged in shared memory.
+__global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_batch(const ParticleArgs* __restrict__ pa,
+                                                                     const GaussParamsF32* __restrict__ gps,
+                                                                     const int4* __restrict__ map) {
+  const int4 m = map[blockIdx.x];
+  const ParticleArgs a = pa[m.x];
+  __shared__ float sP[kTgtMaxD * (kTgtMaxD + 1) / 2];
+  __shared__ float smu[kTgtMaxD];
+  const int np = a.d * (a.d + 1) / 2;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) sP[i] = gps[m.x].P[i];
+  for (int i = threadIdx.x; i < kTgtMaxD; i += blockDim.x) smu[i] = gps[m.x].mu[i];
+  __syncthreads();
+  const FactorSmem fs{sP, smu};
+  if (a.d <= 8)
+    move_reweight_body<8, 1, true, true>(a, fs, m.y, m.z);
+  else if (a.d <= 16)
+    move_reweight_body<16, 1, true, true>(a, fs, m.y, m.z);
+  else
+    move_reweight_body<16, 2, true, true>(a, fs, m.y, m.z);
 }
 
 // ---------------------------------------------------------------- finalise the maximum
 // Single block: m = max over the blocks' maxima; a NaN seen by any block, or a
 // maximum that is not finite (every log-weight -inf, or +inf), is an error.
-__global__ void __launch_bounds__(kFinThreads) k_max_finalize(const double* __restrict__ part, int nb,
-                                                             DevState* st) {
+__device__ __forceinline__ void max_finalize_body(const double* __restrict__ part, int nb, DevState* st) {
   __shared__ long long shm[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   long long m = ordered_key(-INFINITY);
@@ -521,6 +561,18 @@ __global__ void __launch_bounds__(kFinThreads) k_max_finalize(const double* __re
     st->m = M;
     if (!(M > -INFINITY && M < INFINITY)) record_error(st, SMC_ENONFINITE);
   }
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_max_finalize(const double* __restrict__ part, int nb,
+                                                             DevState* st) {
+  max_finalize_body(part, nb, st);
+}
+
+// Batched: block s finalises sampler s over its nb[s] move blocks.
+__global__ void __launch_bounds__(kFinThreads) k_max_finalize_batch(const ParticleArgs* __restrict__ pa,
+                                                                   const int* __restrict__ nb) {
+  const ParticleArgs a = pa[blockIdx.x];
+  max_finalize_body(a.part, nb[blockIdx.x], a.st);
 }
 
 // ---------------------------------------------------------------- covariance
@@ -589,8 +641,7 @@ __global__ void k_begin(DevState* st) {
 // Ends iteration t: swap buffers if resampled (or if forced by an explicit
 // redistribute), LSE_{t} becomes the next LSE_{t-1} (0 after a reset), and
 // the recycling sums of eq. (6) take f_t with weight c_t.
-__global__ void k_commit(DevState* st, int d, int force_flip, int recycle) {
-  if (threadIdx.x != 0) return;
+__device__ __forceinline__ void commit_one(DevState* st, int d, int force_flip, int recycle) {
   const bool flip = force_flip || (st->flag && !st->err);
   if (recycle && !st->err) {
     const double lc = st->logc;
@@ -612,6 +663,42 @@ __global__ void k_commit(DevState* st, int d, int force_flip, int recycle) {
   }
   if (flip) st->cur ^= 1;
   st->lse_prev = flip ? 0.0 : st->lse;
+}
+
+__global__ void k_commit(DevState* st, int d, int force_flip, int recycle) {
+  if (threadIdx.x == 0) commit_one(st, d, force_flip, recycle);
+}
+
+// Batched bookkeeping: thread s handles sampler s.
+__global__ void k_begin_batch(const ParticleArgs* __restrict__ pa, int count) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < count) pa[s].st->t += 1;
+}
+
+__global__ void k_commit_batch(const ParticleArgs* __restrict__ pa, int count) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < count) commit_one(pa[s].st, pa[s].d, 0, 1);
+}
+
+// Points every sampler's step outputs; outs holds three arrays of count
+// pointers: traces, means, recycled estimates (NULL entries allowed).
+__global__ void k_step_setup_batch(const ParticleArgs* __restrict__ pa, void* const* __restrict__ outs, int count) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= count) return;
+  DevState* st = pa[s].st;
+  st->trace = static_cast<smc_iter_stats*>(outs[s]);
+  st->trace_t0 = st->t;
+  st->mean_out = static_cast<double*>(outs[count + s]);
+  st->fhat_out = static_cast<double*>(outs[2 * count + s]);
+  st->cov_out = nullptr;
+}
+
+// Gathers and clears every sampler's device error word.
+__global__ void k_take_errors_batch(const ParticleArgs* __restrict__ pa, int32_t* errs, int count) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= count) return;
+  errs[s] = pa[s].st->err;
+  pa[s].st->err = 0;
 }
 
 // Zeroes the covariance output named by the running smc_step.
@@ -701,6 +788,32 @@ cudaError_t launch_cov(const ParticleArgs& a, double* cov, int grid, cudaStream_
 
 cudaError_t launch_zero_cov(DevState* st, int d, cudaStream_t s) {
   k_zero_cov<<<1, 256, 0, s>>>(st, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_move_reweight_batch(const ParticleArgs* pa, const GaussParamsF32* gps, const int4* map, int nblocks,
+                                       cudaStream_t s) {
+  k_move_reweight_batch<<<nblocks, kPThreads, 0, s>>>(pa, gps, map);
+  return cudaGetLastError();
+}
+cudaError_t launch_max_finalize_batch(const ParticleArgs* pa, const int* nb, int count, cudaStream_t s) {
+  k_max_finalize_batch<<<count, kFinThreads, 0, s>>>(pa, nb);
+  return cudaGetLastError();
+}
+cudaError_t launch_begin_batch(const ParticleArgs* pa, int count, cudaStream_t s) {
+  k_begin_batch<<<(count + 127) / 128, 128, 0, s>>>(pa, count);
+  return cudaGetLastError();
+}
+cudaError_t launch_step_setup_batch(const ParticleArgs* pa, void* const* outs, int count, cudaStream_t s) {
+  k_step_setup_batch<<<(count + 127) / 128, 128, 0, s>>>(pa, outs, count);
+  return cudaGetLastError();
+}
+cudaError_t launch_take_errors_batch(const ParticleArgs* pa, int32_t* errs, int count, cudaStream_t s) {
+  k_take_errors_batch<<<(count + 127) / 128, 128, 0, s>>>(pa, errs, count);
+  return cudaGetLastError();
+}
+cudaError_t launch_commit_batch(const ParticleArgs* pa, int count, cudaStream_t s) {
+  k_commit_batch<<<(count + 127) / 128, 128, 0, s>>>(pa, count);
   return cudaGetLastError();
 }
 

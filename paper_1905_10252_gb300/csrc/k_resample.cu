@@ -161,11 +161,18 @@ __device__ __forceinline__ float u64_to_float_trunc(uint64_t v) {
 __device__ __forceinline__ void weight_of(uint64_t E, float* w) { *w = u64_to_float_trunc(E); }
 __device__ __forceinline__ void weight_of(uint64_t E, double* w) { *w = __ull2double_rn(E); }
 
+// Shared memory of one quantise-reduce block (declared by the calling kernel).
+struct QuantReduceSmem {
+  uint64_t T[128];
+  uint64_t sh[kQThreads / 32][5];
+  double shx[kQThreads / 32][32];
+};
+
 template <typename ST, int DMAX, bool EST>
-__global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
-  __shared__ uint64_t T[128];
-  __shared__ uint64_t sh[kQThreads / 32][5];
-  __shared__ double shx[kQThreads / 32][DMAX];
+__device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int blk, QuantReduceSmem& sm) {
+  uint64_t* const T = sm.T;
+  uint64_t (*const sh)[5] = sm.sh;
+  double (*const shx)[32] = sm.shx;
   load_table(T);
   const DevState* st = a.st;
   uint64_t sw = 0;
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
   if (!st->err) {
     const double m = st->m;
     const int sh_w = 62 - st->F;
-    const int64_t base = int64_t(blockIdx.x) * kQTile;
+    const int64_t base = int64_t(blk) * kQTile;
     const ST* __restrict__ x = static_cast<const ST*>(st->cur ? a.x[1] : a.x[0]);
 #pragma unroll 4
     for (int k = 0; k < kQItems; ++k) {
@@ -243,7 +250,7 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
       t2 += (u128(sh[w][2]) << 64) | sh[w][1];
       te += (u128(sh[w][4]) << 64) | sh[w][3];
     }
-    uint64_t* q = a.qpart + 5 * int64_t(blockIdx.x);
+    uint64_t* q = a.qpart + 5 * int64_t(blk);
     q[0] = tw;
     q[1] = uint64_t(t2);
     q[2] = uint64_t(t2 >> 64);
@@ -253,8 +260,14 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
   if (EST && threadIdx.x < d) {
     double v = 0.0;
     for (int w = 0; w < kQThreads / 32; ++w) v += shx[w][threadIdx.x];
-    static_cast<ST*>(a.xpart)[int64_t(blockIdx.x) * d + threadIdx.x] = ST(v);
+    static_cast<ST*>(a.xpart)[int64_t(blk) * d + threadIdx.x] = ST(v);
   }
+}
+
+template <typename ST, int DMAX, bool EST>
+__global__ void __launch_bounds__(kQThreads) k_quant_reduce(QuantArgs a) {
+  __shared__ QuantReduceSmem sm;
+  quant_reduce_body<ST, DMAX, EST>(a, blockIdx.x, sm);
 }
 
 __device__ __forceinline__ double u128_to_double(u128 v) {
@@ -265,7 +278,7 @@ __device__ __forceinline__ double u128_to_double(u128 v) {
 // Single block: totals, exclusive prefix of the block sums (the CDF base of
 // each scan block), decision, systematic offset U, division constants, LSE,
 // N_eff, log c_t, and the statistics record.
-__global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int set_lse_prev) {
+__device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const int set_lse_prev) {
   __shared__ uint64_t scratch[33];
   __shared__ uint64_t shw[32], sh2l[32], sh2h[32], shel[32], sheh[32];
   DevState* st = a.st;
@@ -405,8 +418,12 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
   if (a.stats_out) *a.stats_out = rec;
 }
 
+__global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int set_lse_prev) {
+  quant_finalize_body(a, set_lse_prev);
+}
+
 // ---------------------------------------------------------------- quantise: scan + ncopies
-__global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
+__device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int blk) {
   const DevState* st = a.st;
   if (st->err || !(a.force || st->flag)) return;
   __shared__ union {
@@ -415,7 +432,7 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
   } buf;
   __shared__ uint64_t scratch[33];
   const int64_t n = a.n;
-  const int64_t base = int64_t(blockIdx.x) * kQTile;
+  const int64_t base = int64_t(blk) * kQTile;
   // the quantised weights of the reduce pass, staged for a blocked layout
 #pragma unroll 4
   for (int k = 0; k < kQItems; ++k) {
@@ -433,7 +450,7 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
     tsum += W[q];
   }
   uint64_t btot;
-  uint64_t C = a.cbase[blockIdx.x] + block_excl_scan_u64(tsum, scratch, &btot);
+  uint64_t C = a.cbase[blk] + block_excl_scan_u64(tsum, scratch, &btot);
   uint32_t ncv[kQItems];
   unsigned nsurv = 0;
   // off_i = floor((N C_{i-1} + U) / S) for every item independently (no
@@ -492,6 +509,8 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) {
     }
   }
 }
+
+__global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) { quant_scan_body(a, blockIdx.x); }
 
 // ---------------------------------------------------------------- standalone ncopies scan
 __global__ void __launch_bounds__(kQThreads) k_nc_reduce(NcScanArgs a) {
@@ -573,8 +592,15 @@ __global__ void __launch_bounds__(kQThreads) k_nc_scan(NcScanArgs a) {
 }
 
 // ---------------------------------------------------------------- redistribute
-template <typename V, int CPR>
-__global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
+// Shared memory of one redistribute block, declared by the calling kernel so
+// that kernels dispatching to several row sizes hold one copy.
+struct RedistSmem {
+  int32_t mark[kRTile];
+  int32_t wsc[kRThreads / 32];
+};
+
+template <typename V, int CPR, int KU = 8>
+__device__ __forceinline__ void redistribute_body(const RedistArgs& a, const int blk, RedistSmem& sm) {
   int cur = 0;
   if (a.stateful) {
     if (!(a.force || a.st->flag)) return;
@@ -582,10 +608,10 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
   }
   // after an error nothing is copied, but the runstart slice is still reset
   const bool failed = a.st->err != 0;
-  __shared__ int32_t mark[kRTile];
-  __shared__ int32_t wsc[kRThreads / 32];
+  int32_t* const mark = sm.mark;
+  int32_t* const wsc = sm.wsc;
   const int64_t n = a.n;
-  const int64_t k0 = int64_t(blockIdx.x) * kRTile;
+  const int64_t k0 = int64_t(blk) * kRTile;
   const int len = int(n - k0 < kRTile ? n - k0 : int64_t(kRTile));
   // this tile's slice of runstart (survivor runs starting here), reset to -1
   // for the next resampling
@@ -611,7 +637,7 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
   if (failed) return;
   // the run covering the first output row may have started in an earlier tile
   if (threadIdx.x == 0) {
-    const int32_t first = min(max(a.tile_src[blockIdx.x], 0), int32_t(n - 1));
+    const int32_t first = min(max(a.tile_src[blk], 0), int32_t(n - 1));
     mark[0] = max(mark[0], first);
   }
   __syncthreads();
@@ -643,7 +669,7 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
   const V* __restrict__ in = static_cast<const V*>(cur ? a.x_in[1] : a.x_in[0]);
   V* __restrict__ out = static_cast<V*>(cur ? a.x_out[1] : a.x_out[0]) + k0 * cpr;
   const int total = len * cpr;
-  constexpr int kU = 8;  // 16-byte loads in flight per thread
+  constexpr int kU = KU;  // loads in flight per thread
   for (int e0 = threadIdx.x; e0 < total; e0 += kRThreads * kU) {
     V v[kU];
 #pragma unroll
@@ -674,6 +700,106 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
     double* __restrict__ lw = a.logw + k0;
     for (int k = threadIdx.x; k < len; k += kRThreads) lw[k] = reset;
   }
+}
+
+template <typename V, int CPR>
+__global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
+  __shared__ RedistSmem sm;
+  redistribute_body<V, CPR>(a, blockIdx.x, sm);
+}
+
+// ---------------------------------------------------------------- batched launches
+// One launch per stage for many samplers: block b of the launch runs block
+// map[b].y of sampler map[b].x with that sampler's own arguments, so every
+// sampler's blocks, reductions and results are those of its own launch.
+__device__ __forceinline__ int dclass(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : (d <= 16 ? 2 : 3)); }
+
+__global__ void __launch_bounds__(kQThreads) k_quant_reduce_batch(const QuantArgs* __restrict__ qa,
+                                                                 const int4* __restrict__ map) {
+  __shared__ QuantReduceSmem sm;
+  const int4 m = map[blockIdx.x];
+  const QuantArgs a = qa[m.x];
+  switch (dclass(a.d)) {
+    case 0: quant_reduce_body<float, 4, true>(a, m.y, sm); break;
+    case 1: quant_reduce_body<float, 8, true>(a, m.y, sm); break;
+    case 2: quant_reduce_body<float, 16, true>(a, m.y, sm); break;
+    default: quant_reduce_body<float, 32, true>(a, m.y, sm); break;
+  }
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_quant_finalize_batch(const QuantArgs* __restrict__ qa) {
+  const QuantArgs a = qa[blockIdx.x];
+  quant_finalize_body(a, 0);
+}
+
+__global__ void __launch_bounds__(kQThreads) k_quant_scan_batch(const QuantArgs* __restrict__ qa,
+                                                               const int4* __restrict__ map) {
+  const int4 m = map[blockIdx.x];
+  const QuantArgs a = qa[m.x];
+  quant_scan_body(a, m.y);
+}
+
+template <int KU>
+__global__ void __launch_bounds__(kRThreads) k_redistribute_batch(const RedistArgs* __restrict__ ra,
+                                                                 const int4* __restrict__ map) {
+  __shared__ RedistSmem sm;
+  const int4 m = map[blockIdx.x];
+  const RedistArgs a = ra[m.x];
+  switch (a.row_bytes) {
+    case 8: redistribute_body<uint2, 1, KU>(a, m.y, sm); break;
+    case 16: redistribute_body<uint4, 1, KU>(a, m.y, sm); break;
+    case 32: redistribute_body<uint4, 2, KU>(a, m.y, sm); break;
+    case 64: redistribute_body<uint4, 4, KU>(a, m.y, sm); break;
+    case 128: redistribute_body<uint4, 8, KU>(a, m.y, sm); break;
+    default:
+      if (a.row_bytes % 16 == 0)
+        redistribute_body<uint4, 0, KU>(a, m.y, sm);
+      else if (a.row_bytes % 8 == 0)
+        redistribute_body<uint2, 0, KU>(a, m.y, sm);
+      else
+        redistribute_body<uint32_t, 0, KU>(a, m.y, sm);
+      break;
+  }
+}
+
+// Timing input for the copy stage: every tile's run starts set to the
+// identity (each row its own single copy), which the copy consumes and resets
+// to -1 as usual.
+__global__ void __launch_bounds__(kRThreads) k_identity_runs_batch(const RedistArgs* __restrict__ ra,
+                                                                  const int4* __restrict__ map) {
+  const int4 m = map[blockIdx.x];
+  const RedistArgs a = ra[m.x];
+  const int64_t k0 = int64_t(m.y) * kRTile;
+  const int len = int(a.n - k0 < kRTile ? a.n - k0 : int64_t(kRTile));
+  for (int k = threadIdx.x; k < len; k += kRThreads) a.runstart[k0 + k] = int32_t(k0 + k);
+  if (threadIdx.x == 0) const_cast<int32_t*>(a.tile_src)[m.y] = int32_t(k0);
+}
+
+cudaError_t launch_quant_reduce_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s) {
+  k_quant_reduce_batch<<<nblocks, kQThreads, 0, s>>>(qa, map);
+  return cudaGetLastError();
+}
+cudaError_t launch_quant_finalize_batch(const QuantArgs* qa, int count, cudaStream_t s) {
+  k_quant_finalize_batch<<<count, kFinThreads, 0, s>>>(qa);
+  return cudaGetLastError();
+}
+cudaError_t launch_quant_scan_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s) {
+  k_quant_scan_batch<<<nblocks, kQThreads, 0, s>>>(qa, map);
+  return cudaGetLastError();
+}
+cudaError_t launch_redistribute_batch(const RedistArgs* ra, const int4* map, int nblocks, int copy_variant,
+                                      cudaStream_t s) {
+  switch (copy_variant) {
+    case 0: k_redistribute_batch<4><<<nblocks, kRThreads, 0, s>>>(ra, map); break;
+    case 1: k_redistribute_batch<8><<<nblocks, kRThreads, 0, s>>>(ra, map); break;
+    case 2: k_redistribute_batch<16><<<nblocks, kRThreads, 0, s>>>(ra, map); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+cudaError_t launch_identity_runs_batch(const RedistArgs* ra, const int4* map, int nblocks, cudaStream_t s) {
+  k_identity_runs_batch<<<nblocks, kRThreads, 0, s>>>(ra, map);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- launchers

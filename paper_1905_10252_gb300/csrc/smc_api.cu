@@ -9,8 +9,7 @@
 #include <new>
 #include <string>
 
-#include "smc_internal.cuh"
-#include "smc_kernels.h"
+#include "smc_host.h"
 
 using namespace smc;
 
@@ -31,12 +30,6 @@ int quant_shift(int64_t n) {
   const int F = 63 - c;
   return F > 62 ? 62 : F;
 }
-
-// Byte offsets of the stateful sampler's workspace.
-struct Layout {
-  size_t st, tg, part, qpart, cbase, xpart, rs, wbuf, tile_src, total;
-  int qblocks, ntiles;
-};
 
 Layout layout_for(int64_t n, int d) {
   Layout L{};
@@ -66,7 +59,13 @@ Layout layout_for(int64_t n, int d) {
   return L;
 }
 
-int sm_count() {
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+void smc::set_global_error(const char* msg) { g_err = msg; }
+
+int smc::sm_count() {
   static int cached[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 132;
@@ -77,41 +76,6 @@ int sm_count() {
   return v;
 }
 
-bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
-
-}  // namespace
-
-void smc::set_global_error(const char* msg) { g_err = msg; }
-
-struct smc_sampler {
-  smc_config cfg;
-  int64_t n;
-  int d;
-  int dtype;
-  size_t esize;
-  void* x[2];
-  void* lp[2];
-  double* logw;
-  char* ws;
-  Layout L;
-  cudaStream_t stream;
-  DevState* st;
-  TargetDev* tg;
-  double* part;
-  uint64_t* qpart;
-  uint64_t* cbase;
-  void* xpart;
-  int32_t* rs;
-  uint64_t* wbuf;
-  int32_t* tile_src;
-  int grid_p;
-  // FP32 Gaussian factor for the move / reweight kernel's parameters
-  GaussParamsF32 gp;
-  bool have_gp;
-  // CUDA graph of one iteration (with and without the covariance stage)
-  cudaGraphExec_t g_iter[2];
-  std::string err;
-};
 
 namespace {
 
@@ -134,6 +98,10 @@ int cuda_fail(smc_sampler* h, cudaError_t e, const char* where) {
   } while (0)
 
 const GaussParamsF32* gauss_params(const smc_sampler* h) { return h->have_gp ? &h->gp : nullptr; }
+
+}  // namespace
+
+namespace smc {
 
 ParticleArgs particle_args(const smc_sampler* h) {
   ParticleArgs a{};
@@ -204,6 +172,10 @@ RedistArgs redist_args(const smc_sampler* h, int force) {
   r.stateful = 1;
   return r;
 }
+
+}  // namespace smc
+
+namespace {
 
 // Weighted statistics after a reweight: max, quantised sums with the mean of
 // eq. (7), decision.

@@ -1,0 +1,58 @@
+// smc_host.h -- host-side state of a sampler handle, shared by the C-ABI
+// translation units (smc_api.cu: single samplers; smc_batch.cu: batches).
+#pragma once
+
+#include <string>
+
+#include "smc_internal.cuh"
+#include "smc_kernels.h"
+
+namespace smc {
+
+// Byte offsets of the stateful sampler's workspace.
+struct Layout {
+  size_t st, tg, part, qpart, cbase, xpart, rs, wbuf, tile_src, total;
+  int qblocks, ntiles;
+};
+
+}  // namespace smc
+
+struct smc_sampler {
+  smc_config cfg;
+  int64_t n;
+  int d;
+  int dtype;
+  size_t esize;
+  void* x[2];
+  void* lp[2];
+  double* logw;
+  char* ws;
+  smc::Layout L;
+  cudaStream_t stream;
+  smc::DevState* st;
+  smc::TargetDev* tg;
+  double* part;
+  uint64_t* qpart;
+  uint64_t* cbase;
+  void* xpart;
+  int32_t* rs;
+  uint64_t* wbuf;
+  int32_t* tile_src;
+  int grid_p;
+  // FP32 Gaussian factor for the move / reweight kernel's parameters
+  smc::GaussParamsF32 gp;
+  bool have_gp;
+  // CUDA graph of one iteration (with and without the covariance stage)
+  cudaGraphExec_t g_iter[2];
+  std::string err;
+};
+
+namespace smc {
+
+ParticleArgs particle_args(const smc_sampler* h);
+QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies);
+RedistArgs redist_args(const smc_sampler* h, int force);
+int sm_count();
+
+}  // namespace smc
+

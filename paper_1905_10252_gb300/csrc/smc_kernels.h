@@ -131,6 +131,21 @@ cudaError_t launch_copy_mean(const DevState* st, double* out, int d, cudaStream_
 cudaError_t launch_step_setup(DevState* st, smc_iter_stats* trace, double* mean_out, double* fhat_out,
                               double* cov_out, cudaStream_t s);
 
+// batched launches (one per stage for many samplers; int4 map = {sampler, block, blocks, 0})
+cudaError_t launch_move_reweight_batch(const ParticleArgs* pa, const GaussParamsF32* gps, const int4* map, int nblocks,
+                                       cudaStream_t s);
+cudaError_t launch_max_finalize_batch(const ParticleArgs* pa, const int* nb, int count, cudaStream_t s);
+cudaError_t launch_begin_batch(const ParticleArgs* pa, int count, cudaStream_t s);
+cudaError_t launch_commit_batch(const ParticleArgs* pa, int count, cudaStream_t s);
+cudaError_t launch_quant_reduce_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s);
+cudaError_t launch_quant_finalize_batch(const QuantArgs* qa, int count, cudaStream_t s);
+cudaError_t launch_quant_scan_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s);
+cudaError_t launch_redistribute_batch(const RedistArgs* ra, const int4* map, int nblocks, int copy_variant,
+                                      cudaStream_t s);  // copy_variant: 4, 8, 16 loads in flight per thread
+cudaError_t launch_identity_runs_batch(const RedistArgs* ra, const int4* map, int nblocks, cudaStream_t s);
+cudaError_t launch_step_setup_batch(const ParticleArgs* pa, void* const* outs, int count, cudaStream_t s);
+cudaError_t launch_take_errors_batch(const ParticleArgs* pa, int32_t* errs, int count, cudaStream_t s);
+
 // k_resample.cu
 cudaError_t upload_expfx_table();  // once per device, outside stream capture
 cudaError_t launch_max_logw(const double* logw, int64_t n, double* part, int nb, DevState* st, cudaStream_t s);

@@ -88,3 +88,14 @@ def composition(N: int, seed: int = 0, kind: str = "multinomial") -> np.ndarray:
         p = np.ones(N)
     p = p / p.sum()
     return g.multinomial(N, p).astype(np.int32)
+
+
+def batch_shapes(count: int, seed: int = 0, n_min: int = 1 << 10, n_max: int = 1 << 18,
+                 dims=(2, 8, 32)) -> list[tuple[int, int]]:
+    """(N, D) of `count` independent samplers: N log-uniform integers in
+    [n_min, n_max], D drawn uniformly from `dims` (the batched workload)."""
+    g = rng(seed, 3)
+    ln = g.uniform(np.log(n_min), np.log(n_max), size=count)
+    ns = np.clip(np.floor(np.exp(ln)).astype(np.int64), n_min, n_max)
+    ds = g.choice(np.asarray(dims, dtype=np.int64), size=count)
+    return [(int(n), int(d)) for n, d in zip(ns, ds)]

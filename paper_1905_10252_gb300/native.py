@@ -23,8 +23,11 @@ EXPORTED = [
     "smc_workspace_bytes", "smc_init", "smc_move", "smc_reweight", "smc_estimate", "smc_resample",
     "smc_redistribute", "smc_step", "smc_step_profile", "smc_sync", "smc_read_stats", "smc_current", "smc_destroy",
     "smc_last_error", "smc_redistribute_ws_bytes", "smc_redistribute_raw", "smc_resample_raw", "smc_ws_status",
-    "smc_redistribute_raw_noalloc",
+    "smc_redistribute_raw_noalloc", "smc_batch_ws_bytes", "smc_batch_create", "smc_batch_step",
+    "smc_batch_set_variant", "smc_batch_tune", "smc_batch_sync", "smc_batch_destroy", "smc_batch_last_error",
 ]
+
+BATCH_MOVE_VARIANTS, BATCH_COPY_VARIANTS = 5, 3  # SMC_BATCH_MOVE_VARIANTS, SMC_BATCH_COPY_VARIANTS
 
 NOALLOC_MAX_N = 1 << 20  # SMC_NOALLOC_MAX_N
 
@@ -101,8 +104,17 @@ def _declare(L: C.CDLL) -> None:
     L.smc_resample_raw.argtypes = [i64, vp, u64, u64, i32, vp, vp, vp, vp]
     L.smc_ws_status.argtypes = [vp, vp]
     L.smc_redistribute_raw_noalloc.argtypes = [i64, i32, vp, vp, vp, vp, vp]
+    L.smc_batch_ws_bytes.argtypes = [C.POINTER(vp), i32, C.POINTER(sz)]
+    L.smc_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), i32, vp, sz, vp]
+    L.smc_batch_step.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
+    L.smc_batch_set_variant.argtypes = [vp, i32, i32]
+    L.smc_batch_tune.argtypes = [vp, i32, C.POINTER(i32)]
+    L.smc_batch_sync.argtypes = [vp, C.POINTER(i32)]
+    L.smc_batch_destroy.argtypes = [vp]
+    L.smc_batch_last_error.argtypes = [vp]
+    L.smc_batch_last_error.restype = C.c_char_p
     for name in EXPORTED:
-        if name != "smc_last_error":
+        if name not in ("smc_last_error", "smc_batch_last_error"):
             getattr(L, name).restype = C.c_int
 
 
@@ -312,6 +324,92 @@ class Sampler:
     def close(self):
         if getattr(self, "h", None):
             lib().smc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_batch(rc: int, handle=None) -> None:
+    if rc != SMC_OK:
+        msg = lib().smc_batch_last_error(handle).decode(errors="replace")
+        raise SmcError(rc, msg)
+
+
+def _ptr_array(tensors):
+    if tensors is None:
+        return None
+    return (C.c_void_p * len(tensors))(*[_ptr(t) for t in tensors])
+
+
+class Batch:
+    """Many FP32 Gaussian samplers stepped with one launch per stage.
+
+    Members keep their own buffers; the batch owns its workspace (kernel
+    arguments and block maps) and a stream.  Results per member equal those of
+    ``Sampler.step`` on that member alone.  Call ``sync()`` before using a
+    member's own methods.
+    """
+
+    def __init__(self, members: list[Sampler], stream: torch.cuda.Stream | None = None):
+        L = lib()
+        self.members = list(members)
+        self.device = self.members[0].device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        handles = (C.c_void_p * len(self.members))(*[m.h for m in self.members])
+        nbytes = C.c_size_t()
+        _check_batch(L.smc_batch_ws_bytes(handles, len(self.members), C.byref(nbytes)))
+        self.ws = _alloc_ws(nbytes.value, self.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        h = C.c_void_p()
+        _check_batch(L.smc_batch_create(C.byref(h), handles, len(self.members), _ptr(self.ws), nbytes.value,
+                                        self.stream.cuda_stream or None))
+        self.h = h
+
+    def _enter(self):
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _done(self):
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def step(self, k: int, mean: bool = True, trace: bool = False, fhat: bool = False):
+        dev, n = self.device, len(self.members)
+        means = [torch.empty(m.d, dtype=torch.float64, device=dev) for m in self.members] if mean else None
+        trs = ([torch.zeros(max(k, 1), STATS_WORDS, dtype=torch.float64, device=dev) for _ in range(n)]
+               if trace else None)
+        fhs = [torch.empty(m.d, dtype=torch.float64, device=dev) for m in self.members] if fhat else None
+        self._enter()
+        _check_batch(lib().smc_batch_step(self.h, int(k), _ptr_array(means), _ptr_array(trs), _ptr_array(fhs)),
+                     self.h)
+        self._done()
+        return dict(mean=means, trace=trs, fhat=fhs)
+
+    def step_raw(self, k: int, means=None, traces=None, fhats=None):
+        """k iterations with caller-provided output tensors (lists or None)."""
+        self._enter()
+        _check_batch(lib().smc_batch_step(self.h, int(k), _ptr_array(means), _ptr_array(traces),
+                                          _ptr_array(fhats)), self.h)
+        self._done()
+
+    def set_variant(self, move_variant: int, copy_variant: int) -> None:
+        _check_batch(lib().smc_batch_set_variant(self.h, int(move_variant), int(copy_variant)), self.h)
+
+    def tune(self, reps: int = 5) -> tuple[int, int]:
+        self._enter()
+        out = (C.c_int32 * 2)()
+        _check_batch(lib().smc_batch_tune(self.h, int(reps), out), self.h)
+        return int(out[0]), int(out[1])
+
+    def sync(self) -> None:
+        which = C.c_int32(-1)
+        _check_batch(lib().smc_batch_sync(self.h, C.byref(which)), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().smc_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
