@@ -11,6 +11,12 @@ C-ABI with host buffers, and the CPU oracle's rate on a bounded sample.
 
 --workload redistribute prints one line per case of the resample+redistribute
 microbenchmark (N in {2^16, 2^20, 2^24}, s in {0.5, 2, 8}, one-hot).
+--workload batch: 256 independent FP32 Gaussian-target samplers (N
+log-uniform in [2^10, 2^18], D in {2, 8, 32}, resampling when N_eff < N/2),
+stepped by one batched launch per stage (CUDA graph, autotuned launch shapes),
+against the same samplers stepped one sampler per launch (each its own graph
+on its own stream, all streams concurrent; and one after another);
+a step is one iteration of every sampler (--steps 50 is the workload's K).
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (rank 0 only).
 Multi-GPU (torchrun): independent replicas, one sampler per GPU, no collective
@@ -44,7 +50,8 @@ def parse():
     p.add_argument("--steps", type=int, default=400)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="iteration", choices=["iteration", "redistribute"])
+    p.add_argument("--workload", default="iteration", choices=["iteration", "redistribute", "batch"])
+    p.add_argument("--count", type=int, default=256, help="batch workload: samplers")
     p.add_argument("--n", type=int, default=1 << 24)
     p.add_argument("--d", type=int, default=16)
     p.add_argument("--e2e-steps", type=int, default=10)
@@ -445,12 +452,126 @@ def run_redistribute(args):
                 print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batched samplers against one sampler per launch on the same GPU."""
+    import ctypes as C
+
+    import torch
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1905_10252_gb300 import build as B
+
+    B.build()
+    from paper_1905_10252_gb300 import inputs, native
+
+    shapes = inputs.batch_shapes(args.count, seed=0)
+    mem = []
+    for j, (n, d) in enumerate(shapes):
+        mu, sig = inputs.gaussian_target(d, seed=1000 + j)
+        mem.append(native.Sampler(n, d, dtype=torch.float32, seed=rank * 100000 + j, mu=mu, sigma=sig, step=0.5,
+                                  init_scale=2.0, resample_mode=native.RESAMPLE_ESS))
+    total_n = sum(n for n, _ in shapes)
+    K, W = args.steps, args.warmup
+    L = native.lib()
+    master = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def solo(concurrent: bool, k: int) -> float:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(master)
+        prev = master
+        for m in mem:
+            m.stream.wait_stream(master if concurrent else prev)
+            native._check(L.smc_step(m.h, int(k), None, None, None, None), m.h)
+            prev = m.stream
+        for m in mem:
+            master.wait_stream(m.stream)
+        e1.record(master)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    solo(True, W)
+    solo_conc_ms = solo(True, K)
+    solo_ser_ms = solo(False, K)
+
+    bt = native.Batch(mem)
+    t0 = time.time()
+    choice = bt.tune(reps=5)
+    tune_s = time.time() - t0
+    bt.step_raw(W)
+    n_prof = 20
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(n_prof)]
+    for row in ev:
+        for e in row:
+            e.record(bt.stream)  # creates the event
+    for row in ev:
+        bt.step_profile(row)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host0 = time.time()
+    start.record(bt.stream)
+    bt.step_raw(K)
+    stop.record(bt.stream)
+    torch.cuda.synchronize()
+    t_host1 = time.time()
+    time.sleep(0.15)
+    clocks.stop()
+    bt.sync()
+    batch_ms = max_over_ranks(start.elapsed_time(stop), ws, device="cuda")
+    stage_ms = {name: float(np.mean([row[j].elapsed_time(row[j + 1]) for row in ev]))
+                for j, name in enumerate(STAGES)}
+    # algorithmic bytes of the stages that do not depend on the resampling decision
+    mv_bytes = sum(n * (2 * 4 * d + 2 * 4 + 2 * 8) for n, d in shapes)
+    q_bytes = sum(n * (8 + 4 * d) for n, d in shapes)
+    peak, peak_kind = peaks()
+
+    def roof(name, byt):
+        gbs = byt / (stage_ms[name] * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                "traffic": None, "peak_kind": peak_kind, "bytes_per_launch": int(byt),
+                "ms_per_launch": round(stage_ms[name], 5)}
+
+    value = job_value(total_n, K, ws, batch_ms)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": batch_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 state / f64 weights / u64 fixed-point CDF", "data": "synthetic",
+            "config": {"workload": f"batched {args.count} gauss samplers N log-uniform [2^10,2^18] D in {{2,8,32}} "
+                                   "fp32 resample when N_eff < N/2",
+                       "samplers": args.count, "total_particles": total_n, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (state %.2f GB)" % (sum(n * d * 4 * 2 for n, d in shapes) / 1e9)},
+            "one_sampler_per_launch": {
+                "concurrent_streams": {"value": job_value(total_n, K, ws, solo_conc_ms), "ms_per_step": solo_conc_ms / K},
+                "one_after_another": {"value": job_value(total_n, K, ws, solo_ser_ms), "ms_per_step": solo_ser_ms / K}},
+            "speedup_vs_concurrent_solo": solo_conc_ms / batch_ms,
+            "tuned_variant": {"move": choice[0], "copy": choice[1], "tune_s": round(tune_s, 3)},
+            "roofline": roof("move_reweight", mv_bytes),
+            "dominant_kernel": max(stage_ms, key=stage_ms.get),
+            "stage_roofline": {"move_reweight": roof("move_reweight", mv_bytes),
+                               "quantise_reduce_estimate": roof("quantise_reduce_estimate", q_bytes)},
+            "stages_ms": {k: round(v, 5) for k, v in stage_ms.items()},
+            "gpu_launches": 8 * K,
+            "clocks": clocks.summary(t_host0, t_host1),
+        }
+        print(json.dumps(line), flush=True)
+    bt.close()
+    for m in mem:
+        m.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "redistribute":
         run_redistribute(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_iteration(args)
 

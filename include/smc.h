@@ -250,6 +250,13 @@ int smc_batch_create(smc_batch** out, smc_sampler* const* members, int32_t count
 int smc_batch_step(smc_batch* b, int32_t k, double* const* mean_dev, smc_iter_stats* const* trace_dev,
                    double* const* fhat_dev);
 
+/* Tracing: one batched iteration launched directly (not from a graph), with
+ * the caller's 8 CUDA events (cudaEvent_t, may be NULL when n_events == 0)
+ * recorded on the batch's stream around the stages, in the order of
+ * smc_step_profile.  Results are identical to one iteration of
+ * smc_batch_step with no outputs. */
+int smc_batch_step_profile(smc_batch* b, void* const* events_host, int32_t n_events);
+
 /* Launch-shape variants.  None changes any result.  move_variant picks how
  * many blocks share the move / reweight launch (0: 2 per SM, 1: 4, 2: 8,
  * 3: 16, 4: one thread per particle), which fixes the particles each warp

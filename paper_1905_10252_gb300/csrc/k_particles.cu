@@ -374,17 +374,53 @@ __device__ __forceinline__ void load_seg(const float* __restrict__ row, bool vec
 }
 
 // Where the FP32 factor comes from: the kernel parameters (one sampler per
-// launch; the FMAs read the constant bank) or shared memory (batched launches).
+// launch; the FMAs read the constant bank) or shared memory (batched
+// launches).  row(r, dv) = sum_{c <= r} P[r][c] dv[c], accumulated with one
+// FMA per term in the order c = 0, 1, ..., r in both cases, so both give the
+// same bits.
 struct FactorParam {
   const GaussParamsF32& g;
-  __device__ __forceinline__ float P(int i) const { return g.P[i]; }
   __device__ __forceinline__ float mu(int c) const { return g.mu[c]; }
+  template <int DMAX>
+  __device__ __forceinline__ float row(int r, const float (&dv)[DMAX]) const {
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < DMAX; ++c)
+      if (c <= r) acc = fmaf(g.P[r * (r + 1) / 2 + c], dv[c], acc);
+    return acc;
+  }
 };
+
+// Shared-memory layout of the factor: row r starts at float offset
+// padded_row_start(r) (a multiple of 4) and is zero-padded to a multiple of 4
+// entries, so that it is read with 16-byte loads.
+__host__ __device__ constexpr int padded_row_start(int r) {
+  int o = 0;
+  for (int k = 0; k < r; ++k) o += (k + 4) / 4 * 4;
+  return o;
+}
+constexpr int kPaddedFactor = padded_row_start(kTgtMaxD);
+
 struct FactorSmem {
-  const float* p;
+  const float4* p;
   const float* m;
-  __device__ __forceinline__ float P(int i) const { return p[i]; }
   __device__ __forceinline__ float mu(int c) const { return m[c]; }
+  template <int DMAX>
+  __device__ __forceinline__ float row(int r, const float (&dv)[DMAX]) const {
+    float acc = 0.0f;
+    const float4* rp = p + padded_row_start(r) / 4;
+#pragma unroll
+    for (int j = 0; j < (DMAX + 3) / 4; ++j) {
+      if (4 * j <= r) {
+        const float4 v = rp[j];
+        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (4 * j + u <= r && 4 * j + u < DMAX) acc = fmaf(e[u], dv[4 * j + u], acc);
+      }
+    }
+    return acc;
+  }
 };
 
 template <int DPL, int LPP, bool MOVE, bool REWEIGHT, typename FS>
@@ -490,9 +526,7 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
 #pragma unroll
         for (int r = 0; r < DMAX; ++r) {
           if (r < d) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int c = 0; c <= r; ++c) acc = fmaf(gp.P(r * (r + 1) / 2 + c), dv[c], acc);
+            const float acc = gp.row(r, dv);
             qs = fmaf(acc, acc, qs);
           }
         }
@@ -525,13 +559,20 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_batch(const Part
                                                                      const int4* __restrict__ map) {
   const int4 m = map[blockIdx.x];
   const ParticleArgs a = pa[m.x];
-  __shared__ float sP[kTgtMaxD * (kTgtMaxD + 1) / 2];
+  __shared__ float4 sP4[kPaddedFactor / 4];
   __shared__ float smu[kTgtMaxD];
-  const int np = a.d * (a.d + 1) / 2;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) sP[i] = gps[m.x].P[i];
+  float* sP = reinterpret_cast<float*>(sP4);
+  // row r of the packed triangle -> its padded, 16-byte aligned slot
+  const float* P = gps[m.x].P;
+  for (int i = threadIdx.x; i < kPaddedFactor; i += blockDim.x) {
+    int r = 0;
+    while (r + 1 < kTgtMaxD && padded_row_start(r + 1) <= i) ++r;
+    const int c = i - padded_row_start(r);
+    sP[i] = (c <= r && r < a.d) ? P[r * (r + 1) / 2 + c] : 0.0f;
+  }
   for (int i = threadIdx.x; i < kTgtMaxD; i += blockDim.x) smu[i] = gps[m.x].mu[i];
   __syncthreads();
-  const FactorSmem fs{sP, smu};
+  const FactorSmem fs{sP4, smu};
   if (a.d <= 8)
     move_reweight_body<8, 1, true, true>(a, fs, m.y, m.z);
   else if (a.d <= 16)
@@ -569,7 +610,7 @@ __global__ void __launch_bounds__(kFinThreads) k_max_finalize(const double* __re
 }
 
 // Batched: block s finalises sampler s over its nb[s] move blocks.
-__global__ void __launch_bounds__(kFinThreads) k_max_finalize_batch(const ParticleArgs* __restrict__ pa,
+__global__ void __launch_bounds__(kFinBatchThreads) k_max_finalize_batch(const ParticleArgs* __restrict__ pa,
                                                                    const int* __restrict__ nb) {
   const ParticleArgs a = pa[blockIdx.x];
   max_finalize_body(a.part, nb[blockIdx.x], a.st);
@@ -797,7 +838,7 @@ cudaError_t launch_move_reweight_batch(const ParticleArgs* pa, const GaussParams
   return cudaGetLastError();
 }
 cudaError_t launch_max_finalize_batch(const ParticleArgs* pa, const int* nb, int count, cudaStream_t s) {
-  k_max_finalize_batch<<<count, kFinThreads, 0, s>>>(pa, nb);
+  k_max_finalize_batch<<<count, kFinBatchThreads, 0, s>>>(pa, nb);
   return cudaGetLastError();
 }
 cudaError_t launch_begin_batch(const ParticleArgs* pa, int count, cudaStream_t s) {

@@ -319,30 +319,34 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
   __shared__ double sxsum[kMaxD];
   const bool est = a.x[0] != nullptr && a.d > 0;
   if (est) {
-    // thread j sums column j % d over rows j / d, j / d + stride / d, ... in a
-    // fixed order (deterministic), in the particle precision (the FP64 pipe is
-    // scarce); the per-thread partials are then added in order per column
-    const int stride = (int(blockDim.x) / a.d) * a.d;
+    // logical thread j (of kFinThreads, whatever the block size) sums column
+    // j % d over rows j / d, j / d + stride / d, ... in a fixed order
+    // (deterministic, and the same in one-sampler and batched launches), in
+    // the particle precision (the FP64 pipe is scarce); the per-thread
+    // partials are then added in order per column
+    const int stride = (kFinThreads / a.d) * a.d;
     const int64_t total_words = int64_t(nb) * a.d;
-    double part = 0.0;
-    if (int(threadIdx.x) < stride) {
-      if (a.dtype == SMC_F64) {
-        const double* xp = static_cast<const double*>(a.xpart);
-        for (int64_t j = threadIdx.x; j < total_words; j += stride) part += xp[j];
-      } else {
-        const float* xp = static_cast<const float*>(a.xpart);
-        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        int64_t j = threadIdx.x;
-        for (; j + 7 * int64_t(stride) < total_words; j += 8 * int64_t(stride)) {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] += xp[j + u * int64_t(stride)];
-        }
-        for (; j < total_words; j += stride) v[0] += xp[j];
-        part = double(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
-      }
-    }
     __shared__ double tpart[kFinThreads];
-    tpart[threadIdx.x] = part;
+    for (int lt = threadIdx.x; lt < kFinThreads; lt += blockDim.x) {
+      double part = 0.0;
+      if (lt < stride) {
+        if (a.dtype == SMC_F64) {
+          const double* xp = static_cast<const double*>(a.xpart);
+          for (int64_t j = lt; j < total_words; j += stride) part += xp[j];
+        } else {
+          const float* xp = static_cast<const float*>(a.xpart);
+          float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          int64_t j = lt;
+          for (; j + 7 * int64_t(stride) < total_words; j += 8 * int64_t(stride)) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] += xp[j + u * int64_t(stride)];
+          }
+          for (; j < total_words; j += stride) v[0] += xp[j];
+          part = double(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+        }
+      }
+      tpart[lt] = part;
+    }
     __syncthreads();
     if (int(threadIdx.x) < a.d) {
       double t = 0.0;
@@ -727,7 +731,7 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce_batch(const QuantArg
   }
 }
 
-__global__ void __launch_bounds__(kFinThreads) k_quant_finalize_batch(const QuantArgs* __restrict__ qa) {
+__global__ void __launch_bounds__(kFinBatchThreads) k_quant_finalize_batch(const QuantArgs* __restrict__ qa) {
   const QuantArgs a = qa[blockIdx.x];
   quant_finalize_body(a, 0);
 }
@@ -780,7 +784,7 @@ cudaError_t launch_quant_reduce_batch(const QuantArgs* qa, const int4* map, int 
   return cudaGetLastError();
 }
 cudaError_t launch_quant_finalize_batch(const QuantArgs* qa, int count, cudaStream_t s) {
-  k_quant_finalize_batch<<<count, kFinThreads, 0, s>>>(qa);
+  k_quant_finalize_batch<<<count, kFinBatchThreads, 0, s>>>(qa);
   return cudaGetLastError();
 }
 cudaError_t launch_quant_scan_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s) {

@@ -337,6 +337,43 @@ int smc_batch_step(smc_batch* b, int32_t k, double* const* mean_dev, smc_iter_st
   return SMC_OK;
 }
 
+int smc_batch_step_profile(smc_batch* b, void* const* events_host, int32_t n_events) {
+  if (!b) return bfail(nullptr, SMC_EINVAL, "null handle");
+  if (n_events != 0 && n_events != 8) return bfail(b, SMC_EINVAL, "n_events must be 0 or 8");
+  if (n_events && !events_host) return bfail(b, SMC_EINVAL, "null events");
+  const int c = b->count, mv = b->move_v;
+  cudaStream_t s = b->stream;
+  auto rec = [&](int j) -> cudaError_t {
+    return n_events ? cudaEventRecord(static_cast<cudaEvent_t>(events_host[j]), s) : cudaSuccess;
+  };
+  std::fill(b->outs_host.begin(), b->outs_host.end(), nullptr);
+  const ParticleArgs* pa = b->at<ParticleArgs>(b->L.pa);
+  const QuantArgs* qa = b->at<QuantArgs>(b->L.qa);
+  const int4* qmap = b->at<int4>(b->L.qmap);
+  const int nq = int(b->plan.qmap.size());
+  BATCH_TRY(b, cudaMemcpyAsync(b->ws + b->L.outs, b->outs_host.data(), 3 * size_t(c) * sizeof(void*),
+                               cudaMemcpyHostToDevice, s));
+  BATCH_TRY(b, launch_step_setup_batch(pa, b->at<void*>(b->L.outs), c, s));
+  BATCH_TRY(b, rec(0));
+  BATCH_TRY(b, launch_begin_batch(pa, c, s));
+  BATCH_TRY(b, launch_move_reweight_batch(pa, b->at<GaussParamsF32>(b->L.gp), b->at<int4>(b->L.mmap[mv]),
+                                          int(b->plan.mmap[mv].size()), s));
+  BATCH_TRY(b, rec(1));
+  BATCH_TRY(b, launch_max_finalize_batch(pa, b->at<int32_t>(b->L.nb) + size_t(mv) * c, c, s));
+  BATCH_TRY(b, rec(2));
+  BATCH_TRY(b, launch_quant_reduce_batch(qa, qmap, nq, s));
+  BATCH_TRY(b, rec(3));
+  BATCH_TRY(b, launch_quant_finalize_batch(qa, c, s));
+  BATCH_TRY(b, rec(4));
+  BATCH_TRY(b, launch_quant_scan_batch(qa, qmap, nq, s));
+  BATCH_TRY(b, rec(5));
+  BATCH_TRY(b, launch_redistribute_batch(b->at<RedistArgs>(b->L.ra), qmap, nq, b->copy_v, s));
+  BATCH_TRY(b, rec(6));
+  BATCH_TRY(b, launch_commit_batch(pa, c, s));
+  BATCH_TRY(b, rec(7));
+  return SMC_OK;
+}
+
 int smc_batch_set_variant(smc_batch* b, int32_t move_variant, int32_t copy_variant) {
   if (!b) return bfail(nullptr, SMC_EINVAL, "null handle");
   if (move_variant < 0 || move_variant >= SMC_BATCH_MOVE_VARIANTS || copy_variant < 0 ||

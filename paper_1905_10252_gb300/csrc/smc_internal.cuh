@@ -31,6 +31,7 @@ constexpr int kRTile = 4096;          // output rows per block of the redistribu
 constexpr int kRThreads = 256;
 constexpr int kPThreads = 256;        // particle kernels (init / move / reweight)
 constexpr int kFinThreads = 1024;     // single-block finalisers
+constexpr int kFinBatchThreads = 256; // one finaliser block per sampler of a batch
 
 // Random-stream purposes (third Philox counter word = purpose << 32 | block).
 constexpr uint32_t kPurposeInit = 1;

@@ -24,7 +24,7 @@ EXPORTED = [
     "smc_redistribute", "smc_step", "smc_step_profile", "smc_sync", "smc_read_stats", "smc_current", "smc_destroy",
     "smc_last_error", "smc_redistribute_ws_bytes", "smc_redistribute_raw", "smc_resample_raw", "smc_ws_status",
     "smc_redistribute_raw_noalloc", "smc_batch_ws_bytes", "smc_batch_create", "smc_batch_step",
-    "smc_batch_set_variant", "smc_batch_tune", "smc_batch_sync", "smc_batch_destroy", "smc_batch_last_error",
+    "smc_batch_step_profile", "smc_batch_set_variant", "smc_batch_tune", "smc_batch_sync", "smc_batch_destroy", "smc_batch_last_error",
 ]
 
 BATCH_MOVE_VARIANTS, BATCH_COPY_VARIANTS = 5, 3  # SMC_BATCH_MOVE_VARIANTS, SMC_BATCH_COPY_VARIANTS
@@ -107,6 +107,7 @@ def _declare(L: C.CDLL) -> None:
     L.smc_batch_ws_bytes.argtypes = [C.POINTER(vp), i32, C.POINTER(sz)]
     L.smc_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), i32, vp, sz, vp]
     L.smc_batch_step.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
+    L.smc_batch_step_profile.argtypes = [vp, C.POINTER(vp), i32]
     L.smc_batch_set_variant.argtypes = [vp, i32, i32]
     L.smc_batch_tune.argtypes = [vp, i32, C.POINTER(i32)]
     L.smc_batch_sync.argtypes = [vp, C.POINTER(i32)]
@@ -392,6 +393,16 @@ class Batch:
         self._enter()
         _check_batch(lib().smc_batch_step(self.h, int(k), _ptr_array(means), _ptr_array(traces),
                                           _ptr_array(fhats)), self.h)
+        self._done()
+
+    def step_profile(self, events=None):
+        """One batched iteration with 8 caller-created CUDA events around its stages."""
+        if events is not None:
+            arr, n = (C.c_void_p * 8)(*[e.cuda_event for e in events]), 8
+        else:
+            arr, n = None, 0
+        self._enter()
+        _check_batch(lib().smc_batch_step_profile(self.h, arr, n), self.h)
         self._done()
 
     def set_variant(self, move_variant: int, copy_variant: int) -> None:
