@@ -328,15 +328,14 @@ __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
 }
 
 // ---------------------------------------------------------------- move + reweight, FP32 fast path
-// The FP32 path gives each lane DPL coordinates (DPL/4 Philox blocks: four
-// 32-bit words, two Box-Muller pairs per block); LPP = ceil(D/DPL) lanes
-// share a particle.  Box-Muller uses the multi-function unit: r^2 = -2 ln(1-a)
+// The FP32 path gives each lane one particle of up to DPL coordinates (DPL/4
+// Philox blocks: four 32-bit words, two Box-Muller pairs per block).  Box-Muller uses the multi-function unit: r^2 = -2 ln(1-a)
 // by __logf, or by its series when a < 1/16 (where __logf's absolute error
 // would dominate), and __sincosf on 2 pi (b - 1/2) in [-pi, pi); the normals
 // differ from the exactly rounded ones by a few 1e-6 at most, and since the
 // random-walk proposal stays symmetric the weights of eq. (5) are unaffected.
-// The next particle's row, log pi and log w are loaded while the current one
-// is computed.
+// Up to 16 coordinates, the next particle's row, log pi and log w are loaded
+// while the current one is computed.
 __device__ __forceinline__ void bm_pair_fast(uint32_t h0, uint32_t h1, float& z0, float& z1) {
   const float a = float(h0 >> 8) * 0x1p-24f;  // u1 = 1 - a
   float p = fmaf(a, 1.0f / 7.0f, 1.0f / 6.0f);
@@ -423,9 +422,20 @@ struct FactorSmem {
   }
 };
 
-template <int DPL, int LPP, bool MOVE, bool REWEIGHT, typename FS>
+// Stages rows < d into the padded row layout of FactorSmem.
+__device__ __forceinline__ void stage_rows(const float* __restrict__ P, const float* __restrict__ mu, int d,
+                                           float* pr, float* m) {
+  for (int r = threadIdx.x; r < d; r += blockDim.x)
+    for (int c = 0; c <= r; ++c) pr[padded_row_start(r) + c] = P[r * (r + 1) / 2 + c];
+  for (int c = threadIdx.x; c < kTgtMaxD; c += blockDim.x) m[c] = mu[c];
+}
+
+template <int DPL, bool MOVE, bool REWEIGHT, typename FS>
 __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const FS gp, const int blk, const int nblk) {
-  constexpr int DMAX = DPL * LPP;
+  constexpr int DMAX = DPL;
+  // the next particle's data is loaded during the current one's arithmetic
+  // when the registers allow it (up to 16 coordinates per lane)
+  constexpr bool PF = DPL <= 16;
   MaxTracker mt;
   mt.init();
   const int cur = a.st->cur;
@@ -434,17 +444,16 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
   float* __restrict__ lp = static_cast<float*>(cur ? a.logpi[1] : a.logpi[0]);
   double* __restrict__ logw = a.logw;
   const int d = a.d;
-  const int q = LPP > 1 ? int(threadIdx.x & (LPP - 1)) : 0;
-  const int c0 = DPL * q;
-  const int nvalid = d - c0;  // coordinates this lane owns (may be <= 0)
+  constexpr int q = 0, c0 = 0;  // one lane per particle: it owns coordinates [0, d)
+  const int nvalid = d;
   const bool vec = ((d & 3) == 0) && (nvalid >= DPL);
   const float eps = float(a.step);
-  // The loop runs over whole warps (its bound is warp-uniform) so that every
-  // lane reaches the group shuffles; lanes past the end are predicated.
-  constexpr int kGroups = 32 / LPP;
+  // The loop runs over whole warps (its bound is warp-uniform); lanes past
+  // the end are predicated.
+  constexpr int kGroups = 32;
   const int64_t warp_global = (int64_t(blk) * blockDim.x + threadIdx.x) >> 5;
   const int64_t step = int64_t(nblk) * (blockDim.x >> 5) * kGroups;
-  const int grp = (threadIdx.x & 31) / LPP;
+  const int grp = threadIdx.x & 31;
   int64_t base = warp_global * kGroups;
   // prologue: the first particle's data
   float xo[DPL];
@@ -464,18 +473,28 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
   for (; base < a.n; base += step) {
     const int64_t i = base + grp;
     const bool valid = i < a.n;
+    if (!PF && base != warp_global * kGroups) {  // (the prologue loaded the first)
+      if (valid && nvalid > 0) load_seg<DPL>(x + i * d + c0, vec, nvalid, xo);
+      if (REWEIGHT && valid && q == 0) {
+        lwc = logw[i];
+        lpc = lp[i];
+      }
+    }
     // prefetch the next particle
     const int64_t inx = i + step;
-    float xn[DPL];
+    constexpr int kPF = PF ? DPL : 1;
+    float xn[kPF];
     double lwn = 0.0;
     float lpn = 0.0f;
-    if (inx < a.n && nvalid > 0) load_seg<DPL>(x + inx * d + c0, vec, nvalid, xn);
-    else
+    if constexpr (PF) {
+      if (inx < a.n && nvalid > 0) load_seg<kPF>(x + inx * d + c0, vec, nvalid, xn);
+      else
 #pragma unroll
-      for (int c = 0; c < DPL; ++c) xn[c] = 0.0f;
-    if (REWEIGHT && inx < a.n && q == 0) {
-      lwn = logw[inx];
-      lpn = lp[inx];
+        for (int c = 0; c < kPF; ++c) xn[c] = 0.0f;
+      if (REWEIGHT && inx < a.n && q == 0) {
+        lwn = logw[inx];
+        lpn = lp[inx];
+      }
     }
     if (MOVE && valid && nvalid > 0) {
       // all of the lane's Philox blocks first: independent 10-round chains
@@ -483,12 +502,14 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       P4 w[DPL / 4];
 #pragma unroll
       for (int b4 = 0; b4 < DPL / 4; ++b4)
-        w[b4] = stream_block(a.seed, t, kPurposeMove, uint64_t(i), uint32_t(c0 / 4 + b4));
+        if (DPL != 8 || 4 * b4 < nvalid)  // wider classes: unconditional (interleaves better)
+          w[b4] = stream_block(a.seed, t, kPurposeMove, uint64_t(i), uint32_t(c0 / 4 + b4));
 #pragma unroll
       for (int b4 = 0; b4 < DPL / 4; ++b4) {
         if (4 * b4 < nvalid) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
+            if (DPL == 8 && 4 * b4 + 2 * h >= nvalid) continue;  // this pair's normals are not used
             float z0, z1;
             bm_pair_fast(w[b4].v[2 * h], w[b4].v[2 * h + 1], z0, z1);
             xo[4 * b4 + 2 * h] = fmaf(eps, z0, xo[4 * b4 + 2 * h]);
@@ -507,78 +528,62 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
           if (c < nvalid) row[c] = xo[c];
       }
     }
-    if (REWEIGHT) {
+    if (REWEIGHT && valid) {
+      // y = L^-1 (x - mu) row by row
       float dv[DMAX];
-      if (LPP == 1) {
 #pragma unroll
-        for (int c = 0; c < DMAX; ++c) dv[c] = xo[c] - gp.mu(c);
-      } else {
-        // all 32 lanes execute the shuffles (valid or not)
+      for (int c = 0; c < DMAX; ++c) dv[c] = xo[c] - gp.mu(c);
+      float qs = 0.0f;
 #pragma unroll
-        for (int j = 0; j < LPP; ++j)
-#pragma unroll
-          for (int c = 0; c < DPL; ++c) dv[DPL * j + c] = __shfl_sync(0xffffffffu, xo[c], j, LPP) - gp.mu(DPL * j + c);
-      }
-      if (valid && q == 0) {
-        // y = L^-1 (x - mu) row by row; the factor's entries are kernel
-        // parameters, read by the FMAs straight from the constant bank
-        float qs = 0.0f;
-#pragma unroll
-        for (int r = 0; r < DMAX; ++r) {
-          if (r < d) {
-            const float acc = gp.row(r, dv);
-            qs = fmaf(acc, acc, qs);
-          }
+      for (int r = 0; r < DMAX; ++r) {
+        if (r < d) {
+          const float acc = gp.row(r, dv);
+          qs = fmaf(acc, acc, qs);
         }
-        // eq. (5): the log-target difference in FP32 (exact when the two
-        // values are within a factor of two), one FP64 addition
-        const float lpi = -0.5f * qs;
-        const double lw = lwc + double(lpi - lpc);
-        lp[i] = lpi;
-        logw[i] = lw;
-        mt.add(lw);
       }
+      // eq. (5): the log-target difference in FP32 (exact when the two
+      // values are within a factor of two), one FP64 addition
+      const float lpi = -0.5f * qs;
+      const double lw = lwc + double(lpi - lpc);
+      lp[i] = lpi;
+      logw[i] = lw;
+      mt.add(lw);
     }
+    if constexpr (PF) {
 #pragma unroll
-    for (int c = 0; c < DPL; ++c) xo[c] = xn[c];
-    lwc = lwn;
-    lpc = lpn;
+      for (int c = 0; c < kPF; ++c) xo[c] = xn[c];
+      lwc = lwn;
+      lpc = lpn;
+    }
   }
   if (REWEIGHT) block_write_max(mt, a.part + 2 * blk, a.st);
 }
 
-template <int DPL, int LPP, bool MOVE, bool REWEIGHT>
+// One sampler per launch: the factor's entries are kernel parameters, read by
+// the FMAs straight from the constant bank.
+template <int DPL, bool MOVE, bool REWEIGHT>
 __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleArgs a, const GaussParamsF32 gp) {
-  move_reweight_body<DPL, LPP, MOVE, REWEIGHT>(a, FactorParam{gp}, blockIdx.x, gridDim.x);
+  move_reweight_body<DPL, MOVE, REWEIGHT>(a, FactorParam{gp}, blockIdx.x, gridDim.x);
 }
 
 // Batched: block b runs block map[b].y of map[b].z of sampler map[b].x; the
-// sampler's packed factor is staged in shared memory.
+// sampler's factor is staged in shared memory (padded rows, 16-byte loads).
 __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_batch(const ParticleArgs* __restrict__ pa,
                                                                      const GaussParamsF32* __restrict__ gps,
                                                                      const int4* __restrict__ map) {
   const int4 m = map[blockIdx.x];
   const ParticleArgs a = pa[m.x];
-  __shared__ float4 sP4[kPaddedFactor / 4];
+  __shared__ float4 sfac[kPaddedFactor / 4];
   __shared__ float smu[kTgtMaxD];
-  float* sP = reinterpret_cast<float*>(sP4);
-  // row r of the packed triangle -> its padded, 16-byte aligned slot
-  const float* P = gps[m.x].P;
-  for (int i = threadIdx.x; i < kPaddedFactor; i += blockDim.x) {
-    int r = 0;
-    while (r + 1 < kTgtMaxD && padded_row_start(r + 1) <= i) ++r;
-    const int c = i - padded_row_start(r);
-    sP[i] = (c <= r && r < a.d) ? P[r * (r + 1) / 2 + c] : 0.0f;
-  }
-  for (int i = threadIdx.x; i < kTgtMaxD; i += blockDim.x) smu[i] = gps[m.x].mu[i];
+  stage_rows(gps[m.x].P, gps[m.x].mu, a.d, reinterpret_cast<float*>(sfac), smu);
   __syncthreads();
-  const FactorSmem fs{sP4, smu};
+  const FactorSmem fs{sfac, smu};
   if (a.d <= 8)
-    move_reweight_body<8, 1, true, true>(a, fs, m.y, m.z);
+    move_reweight_body<8, true, true>(a, fs, m.y, m.z);
   else if (a.d <= 16)
-    move_reweight_body<16, 1, true, true>(a, fs, m.y, m.z);
+    move_reweight_body<16, true, true>(a, fs, m.y, m.z);
   else
-    move_reweight_body<16, 2, true, true>(a, fs, m.y, m.z);
+    move_reweight_body<32, true, true>(a, fs, m.y, m.z);
 }
 
 // ---------------------------------------------------------------- finalise the maximum
@@ -788,12 +793,12 @@ static cudaError_t launch_particles_d(int op, const ParticleArgs& a, int grid, c
   return launch_particles_t<T, 32>(op, a, grid, s);
 }
 
-template <int DPL, int LPP>
+template <int DPL>
 static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, cudaStream_t s, const GaussParamsF32& gp) {
   switch (op) {
-    case OP_MOVE: k_move_reweight_lanes<DPL, LPP, true, false><<<grid, kPThreads, 0, s>>>(a, gp); break;
-    case OP_REWEIGHT: k_move_reweight_lanes<DPL, LPP, false, true><<<grid, kPThreads, 0, s>>>(a, gp); break;
-    case OP_MOVE_REWEIGHT: k_move_reweight_lanes<DPL, LPP, true, true><<<grid, kPThreads, 0, s>>>(a, gp); break;
+    case OP_MOVE: k_move_reweight_lanes<DPL, true, false><<<grid, kPThreads, 0, s>>>(a, gp); break;
+    case OP_REWEIGHT: k_move_reweight_lanes<DPL, false, true><<<grid, kPThreads, 0, s>>>(a, gp); break;
+    case OP_MOVE_REWEIGHT: k_move_reweight_lanes<DPL, true, true><<<grid, kPThreads, 0, s>>>(a, gp); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -801,9 +806,9 @@ static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, cudaStr
 
 cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s, const GaussParamsF32* gp) {
   if (a.dtype == SMC_F32 && op != OP_INIT && a.kind == SMC_GAUSS && gp) {
-    if (a.d <= 8) return launch_lanes<8, 1>(op, a, grid, s, *gp);
-    if (a.d <= 16) return launch_lanes<16, 1>(op, a, grid, s, *gp);
-    return launch_lanes<16, 2>(op, a, grid, s, *gp);
+    if (a.d <= 8) return launch_lanes<8>(op, a, grid, s, *gp);
+    if (a.d <= 16) return launch_lanes<16>(op, a, grid, s, *gp);
+    return launch_lanes<32>(op, a, grid, s, *gp);
   }
   return a.dtype == SMC_F64 ? launch_particles_d<double>(op, a, grid, s) : launch_particles_d<float>(op, a, grid, s);
 }

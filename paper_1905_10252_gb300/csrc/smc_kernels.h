@@ -36,9 +36,9 @@ struct GaussParamsF32 {
   float mu[kTgtMaxD];
 };
 
-// Lanes that share one particle in the move / reweight kernels: the FP32 path
-// gives each lane up to 16 coordinates (two Philox blocks); FP64 uses one lane.
-inline int lanes_per_particle(int dtype, int d) { return (dtype == SMC_F32 && d > 16) ? 2 : 1; }
+// Lanes that share one particle in the move / reweight kernels: one in every
+// path (the FP32 path holds up to 32 coordinates in one lane's registers).
+inline int lanes_per_particle(int, int) { return 1; }
 
 struct ParticleArgs {
   int64_t n;
