@@ -58,6 +58,12 @@ typedef enum { SMC_GAUSS = 1, SMC_LOGISTIC = 2, SMC_STUDENT_T = 3 } smc_target_k
  * SMC_RESAMPLE_ALWAYS is the worst case of Sec. 5.2 (every iteration). */
 typedef enum { SMC_RESAMPLE_ESS = 0, SMC_RESAMPLE_ALWAYS = 1, SMC_RESAMPLE_NEVER = 2 } smc_resample_mode;
 
+/* smc_config.flags.  SMC_FLAG_LOGISTIC_CUDA_CORES: an FP32 logistic sampler
+ * evaluates its likelihood on the CUDA cores in FP32 (z = X b by FMAs) instead
+ * of the default tensor-core contraction (BF16 hi/lo split, FP32 accumulation);
+ * FP64 samplers always use the CUDA cores in FP64. */
+#define SMC_FLAG_LOGISTIC_CUDA_CORES 1
+
 typedef struct {
   int64_t n;              /* N particles */
   int32_t d;              /* D state dimension */
@@ -73,7 +79,7 @@ typedef struct {
   const float* X_dev;       /* LOGISTIC: M x D row-major */
   const float* y_dev;       /* LOGISTIC: M labels in {0, 1} */
   int32_t m;                /* LOGISTIC: M rows */
-  int32_t reserved;
+  int32_t flags;            /* SMC_FLAG_* (0: defaults) */
   double prior_var;         /* LOGISTIC: prior N(0, prior_var I) */
   double nu;                /* STUDENT_T: degrees of freedom */
 } smc_config;

@@ -27,8 +27,10 @@
  *   orc_systematic          pinned: sum == N, floor bounds, exhaustive-U mean
  *   orc_redistribute        pinned: brute-force stable repeat, all compositions
  *   orc_run (Gaussian)      pinned: closed-form posterior moments within MC error
- *   logistic logpi          pinned: naive numpy double loop at small sizes
- *   orc_run (logistic)      parity unpinned beyond the logpi pin (no closed form)
+ *   logistic logpi          pinned: b = 0 closed form (-M log 2), scipy Bernoulli log-likelihood
+ *                           + normal prior, closed-form gradient by central differences,
+ *                           label-flip symmetry
+ *   orc_run (logistic)      parity unpinned beyond the logpi pins (no closed-form posterior)
  */
 #include <math.h>
 #include <stdint.h>

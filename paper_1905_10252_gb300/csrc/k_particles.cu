@@ -64,6 +64,58 @@ __global__ void k_target_setup(TargetDev* tg, int kind, double nu, const double*
   for (int i = 0; i < kMaxD * kMaxD; ++i) tg->Pf[i] = float(tg->P[i]);
 }
 
+// Logistic data: FP32 copies, BF16 hi / lo images and v = X^T y.  Image of
+// data tile j (rows 256 j ..): kLgTileBytes bytes, hi then lo, each 256 rows x
+// 32 columns of BF16 in the tensor cores' K-major core-matrix order: element
+// (r, k) at byte (r / 8) * 512 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
+// Rows >= M and columns >= D are zero.  lo = bf16(x - float(hi)).
+// BF16 = the top 16 bits of an FP32, rounded to nearest even (finite inputs).
+__device__ __forceinline__ uint16_t bf16_rn(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return uint16_t((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+__device__ __forceinline__ float bf16_to_f32(uint16_t h) { return __uint_as_float(uint32_t(h) << 16); }
+
+__global__ void k_logistic_copy(TargetDev* tg, const float* __restrict__ X, const float* __restrict__ y, int m, int d,
+                                double prior_var, float* __restrict__ Xw, float* __restrict__ yw,
+                                uint16_t* __restrict__ ximg) {
+  const int m_pad = (m + kLgRows - 1) / kLgRows * kLgRows;
+  const int64_t total = int64_t(m_pad) * kLgK;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int r = int(e / kLgK), k = int(e % kLgK);
+    const float v = (r < m && k < d) ? X[int64_t(r) * d + k] : 0.0f;
+    if (r < m && k < d) Xw[int64_t(r) * d + k] = v;
+    if (k == 0 && r < m) yw[r] = y[r];
+    const uint16_t hi = bf16_rn(v);
+    const uint16_t lo = bf16_rn(v - bf16_to_f32(hi));
+    const int tile = r / kLgRows, rr = r % kLgRows;
+    const size_t off = (size_t(rr / 8) * 512 + size_t(k / 8) * 128 + size_t(rr % 8) * 16 + size_t(k % 8) * 2) / 2;
+    uint16_t* img = ximg + size_t(tile) * (kLgTileBytes / 2);
+    img[off] = hi;
+    img[off + kLgTileBytes / 4] = lo;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    tg->kind = SMC_LOGISTIC;
+    tg->d = d;
+    tg->X = Xw;
+    tg->y = yw;
+    tg->ximg = ximg;
+    tg->prior_var = prior_var;
+    tg->m = m;
+    tg->m_pad = m_pad;
+  }
+}
+
+// v_c = sum_m y_m X_mc in FP64, row order (one thread per column).
+__global__ void k_logistic_v(TargetDev* tg, const float* __restrict__ X, const float* __restrict__ y, int m, int d) {
+  const int c = threadIdx.x;
+  if (c >= kTgtMaxD) return;
+  double acc = 0.0;
+  if (c < d)
+    for (int r = 0; r < m; ++r) acc = fma(double(y[r]), double(X[int64_t(r) * d + c]), acc);
+  tg->v[c] = acc;
+}
+
 // ---------------------------------------------------------------- log targets
 // Gaussian, FP64: forward substitution z = L^-1 (x - mu), log pi = -1/2 |z|^2.
 template <int DMAX>
@@ -102,6 +154,51 @@ __device__ __forceinline__ float logpi_gauss(const float (&x)[DMAX], int d, cons
     }
   }
   return -0.5f * q;
+}
+
+// Bayesian logistic regression, one particle against all M data rows, in the
+// order of the definition: z_m = sum_c X_mc b_c, then s += y_m z_m - softplus(z_m) over
+// m, minus |b|^2 / (2 prior_var).  FP64: explicitly rounded operations;
+// FP32: FP32 z and softplus, FP64 accumulation over the rows.
+__device__ __forceinline__ double softplus64(double z) { return z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z)); }
+__device__ __forceinline__ float softplus32(float z) { return z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z)); }
+
+template <int DMAX>
+__device__ double logpi_logistic(const double (&x)[DMAX], int d, const TargetDev* __restrict__ tg) {
+  const float* __restrict__ X = tg->X;
+  const float* __restrict__ y = tg->y;
+  double s = 0.0;
+  for (int m = 0; m < tg->m; ++m) {
+    double z = 0.0;
+#pragma unroll
+    for (int c = 0; c < DMAX; ++c)
+      if (c < d) z = __dadd_rn(z, __dmul_rn(double(X[int64_t(m) * d + c]), x[c]));
+    s = __dadd_rn(s, __dsub_rn(__dmul_rn(double(y[m]), z), softplus64(z)));
+  }
+  double b2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < DMAX; ++c)
+    if (c < d) b2 = __dadd_rn(b2, __dmul_rn(x[c], x[c]));
+  return __dsub_rn(s, __ddiv_rn(b2, __dmul_rn(2.0, tg->prior_var)));
+}
+
+template <int DMAX>
+__device__ float logpi_logistic(const float (&x)[DMAX], int d, const TargetDev* __restrict__ tg) {
+  const float* __restrict__ X = tg->X;
+  const float* __restrict__ y = tg->y;
+  double s = 0.0;
+  for (int m = 0; m < tg->m; ++m) {
+    float z = 0.0f;
+#pragma unroll
+    for (int c = 0; c < DMAX; ++c)
+      if (c < d) z = fmaf(X[int64_t(m) * d + c], x[c], z);
+    s += double(y[m]) * double(z) - double(softplus32(z));
+  }
+  float b2 = 0.0f;
+#pragma unroll
+  for (int c = 0; c < DMAX; ++c)
+    if (c < d) b2 = fmaf(x[c], x[c], b2);
+  return float(s - double(b2) / (2.0 * tg->prior_var));
 }
 
 // Student-t, D = 1 (eq. (14) up to its constant).
@@ -220,8 +317,10 @@ __device__ __forceinline__ void load_target<float>(const TargetDev* __restrict__
 }
 
 template <typename T, int DMAX>
-__device__ __forceinline__ T eval_logpi(const T (&x)[DMAX], int d, int kind, const TargetSmem<T>& ts, T nu) {
+__device__ __forceinline__ T eval_logpi(const T (&x)[DMAX], int d, int kind, const TargetSmem<T>& ts, T nu,
+                                        const TargetDev* __restrict__ tg) {
   if (kind == SMC_STUDENT_T) return logpi_student(x[0], ts.mu[0], nu);
+  if (kind == SMC_LOGISTIC) return logpi_logistic<DMAX>(x, d, tg);
   return logpi_gauss<DMAX>(x, d, ts.F, ts.mu);
 }
 
@@ -249,7 +348,7 @@ __global__ void __launch_bounds__(kPThreads) k_init(ParticleArgs a) {
         xr[c] = c < a.d ? __dmul_rn(a.init_scale, z[c]) : 0.0;
         if (c < a.d) q = __fma_rn(xr[c], xr[c], q);
       }
-      const double lpi = eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu);
+      const double lpi = eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu, a.tg);
       const double lq0 = __ddiv_rn(__dmul_rn(-0.5, q), __dmul_rn(a.init_scale, a.init_scale));
       lw = __dsub_rn(lpi, lq0);
       lp[i] = lpi;
@@ -263,7 +362,7 @@ __global__ void __launch_bounds__(kPThreads) k_init(ParticleArgs a) {
         xr[c] = c < a.d ? s * z[c] : 0.0f;
         if (c < a.d) q = fmaf(xr[c], xr[c], q);
       }
-      const float lpi = eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu);
+      const float lpi = eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu, a.tg);
       const float lq0 = (-0.5f * q) / (s * s);
       lw = double(lpi) - double(lq0);
       lp[i] = lpi;
@@ -312,7 +411,7 @@ __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
       store_row<T, DMAX>(x + i * a.d, a.d, xr);
     }
     if (REWEIGHT) {
-      const T lpi = eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu);
+      const T lpi = eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu, a.tg);
       const T lpp = lp[i];
       double lw;
       if constexpr (sizeof(T) == 8)
@@ -816,6 +915,15 @@ cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream
 cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double* mu, const double* sigma, int d,
                                 DevState* st, cudaStream_t s) {
   k_target_setup<<<1, 32, 0, s>>>(tg, kind, nu, mu, sigma, d, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_logistic_setup(TargetDev* tg, const float* X, const float* y, int m, int d, double prior_var,
+                                  float* Xw, float* yw, uint16_t* ximg, cudaStream_t s) {
+  k_logistic_copy<<<256, 256, 0, s>>>(tg, X, y, m, d, prior_var, Xw, yw, ximg);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_logistic_v<<<1, 32, 0, s>>>(tg, X, y, m, d);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ int quant_shift(int64_t n) {
   return F > 62 ? 62 : F;
 }
 
-Layout layout_for(int64_t n, int d) {
+Layout layout_for(int64_t n, int d, int m = 0) {
   Layout L{};
   L.qblocks = int(div_up(n, kQTile));
   L.ntiles = int(div_up(n, kRTile));
@@ -55,9 +55,19 @@ Layout layout_for(int64_t n, int d) {
   p = align_up(p + size_t(n) * sizeof(uint64_t));
   L.tile_src = p;
   p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
+  // logistic data: X, y and the BF16 tile images
+  const size_t m_pad = size_t(m + kLgRows - 1) / kLgRows * kLgRows;
+  L.lg_x = p;
+  p = align_up(p + size_t(m) * size_t(d) * sizeof(float));
+  L.lg_y = p;
+  p = align_up(p + size_t(m) * sizeof(float));
+  L.lg_img = p;
+  p = align_up(p + m_pad / kLgRows * kLgTileBytes);
   L.total = p;
   return L;
 }
+
+int logistic_rows(const smc_config* c) { return c->target == SMC_LOGISTIC ? c->m : 0; }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -226,8 +236,10 @@ int check_config(const smc_config* c) {
   if (c->n < 1 || c->n > 2147483647LL) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
   if (c->d < 1 || c->d > kMaxD) return fail(nullptr, SMC_EINVAL, "d must be in [1, 32]");
   if (c->dtype != SMC_F32 && c->dtype != SMC_F64) return fail(nullptr, SMC_EINVAL, "dtype must be SMC_F32 or SMC_F64");
-  if (c->target != SMC_GAUSS && c->target != SMC_STUDENT_T)
-    return fail(nullptr, SMC_EINVAL, "target kind not supported by this build");
+  if (c->target != SMC_GAUSS && c->target != SMC_STUDENT_T && c->target != SMC_LOGISTIC)
+    return fail(nullptr, SMC_EINVAL, "unknown target kind");
+  if (c->target == SMC_LOGISTIC && (!c->X_dev || !c->y_dev || c->m < 1 || !(c->prior_var > 0.0)))
+    return fail(nullptr, SMC_EINVAL, "logistic target needs X_dev, y_dev, m >= 1 and prior_var > 0");
   if (c->target == SMC_STUDENT_T && (c->d != 1 || !(c->nu > 0.0)))
     return fail(nullptr, SMC_EINVAL, "Student-t target needs d == 1 and nu > 0");
   if (c->target == SMC_GAUSS && (!c->mu_dev || !c->sigma_dev))
@@ -246,7 +258,7 @@ int smc_workspace_bytes(const smc_config* cfg, size_t* bytes) {
   int rc = check_config(cfg);
   if (rc) return rc;
   if (!bytes) return fail(nullptr, SMC_EINVAL, "null bytes");
-  *bytes = layout_for(cfg->n, cfg->d).total;
+  *bytes = layout_for(cfg->n, cfg->d, logistic_rows(cfg)).total;
   return SMC_OK;
 }
 
@@ -264,7 +276,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   if (!aligned(x_dev, 16) || !aligned(x_alt_dev, 16) || !aligned(logw_dev, 8) || !aligned(logpi_dev, es) ||
       !aligned(logpi_alt_dev, es))
     return fail(nullptr, SMC_EINVAL, "particle buffers must be 16-byte aligned");
-  const Layout L = layout_for(cfg->n, cfg->d);
+  const Layout L = layout_for(cfg->n, cfg->d, logistic_rows(cfg));
   if (workspace_bytes < L.total) return fail(nullptr, SMC_ENOMEM, "workspace too small");
   cudaError_t e = upload_expfx_table();
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "upload_expfx_table");
@@ -304,8 +316,14 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   e = cudaMemsetAsync(h->tg, 0, sizeof(TargetDev), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->rs, 0xFF, size_t(h->n) * sizeof(int32_t), h->stream);
   if (e == cudaSuccess) e = launch_state_init(h->st, h->n, 0, quant_shift(h->n), h->stream);
-  if (e == cudaSuccess)
-    e = launch_target_setup(h->tg, cfg->target, cfg->nu, cfg->mu_dev, cfg->sigma_dev, h->d, h->st, h->stream);
+  if (e == cudaSuccess) {
+    if (cfg->target == SMC_LOGISTIC)
+      e = launch_logistic_setup(h->tg, cfg->X_dev, cfg->y_dev, cfg->m, h->d, cfg->prior_var,
+                                reinterpret_cast<float*>(h->ws + L.lg_x), reinterpret_cast<float*>(h->ws + L.lg_y),
+                                reinterpret_cast<uint16_t*>(h->ws + L.lg_img), h->stream);
+    else
+      e = launch_target_setup(h->tg, cfg->target, cfg->nu, cfg->mu_dev, cfg->sigma_dev, h->d, h->st, h->stream);
+  }
   if (e == cudaSuccess) e = launch_particles(OP_INIT, particle_args(h), h->grid_p, h->stream);
   if (e == cudaSuccess) e = launch_stats(h, 1);
   if (e == cudaSuccess && cfg->target == SMC_GAUSS && h->dtype == SMC_F32) {

@@ -24,7 +24,22 @@ struct alignas(256) TargetDev {
   double L[kTgtMaxD * kTgtMaxD];
   double P[kTgtMaxD * kTgtMaxD];
   float Pf[kTgtMaxD * kTgtMaxD];
+  // Bayesian logistic regression: log pi(b) = sum_m [y_m z_m - log(1 + e^z_m)]
+  // - |b|^2 / (2 prior_var), z = X b.  The data live in the sampler's workspace.
+  const float* X;         // M x D row-major (FP32 copy of the caller's data)
+  const float* y;         // M labels
+  const uint16_t* ximg;   // BF16 hi / lo images of X for the tensor-core likelihood
+  double v[kTgtMaxD];     // X^T y in FP64
+  double prior_var;
+  int32_t m;
+  int32_t m_pad;          // M rounded up to the likelihood's data tile
 };
+
+// Tensor-core logistic likelihood: data tile (rows of X per MMA) and the bytes
+// of one tile's BF16 hi + lo images (K = 32 columns, zero padded).
+constexpr int kLgRows = 256;
+constexpr int kLgK = 32;
+constexpr size_t kLgTileBytes = size_t(kLgRows) * kLgK * 2 * 2;
 
 enum { OP_INIT = 0, OP_MOVE = 1, OP_REWEIGHT = 2, OP_MOVE_REWEIGHT = 3 };
 
@@ -122,6 +137,10 @@ cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream
                              const GaussParamsF32* gp = nullptr);
 cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double* mu, const double* sigma, int d,
                                 DevState* st, cudaStream_t s);
+// Copies the logistic data into the workspace (Xw: M x D, yw: M), builds the
+// BF16 images (ximg: m_pad / kLgRows tiles) and v = X^T y, and points tg at them.
+cudaError_t launch_logistic_setup(TargetDev* tg, const float* X, const float* y, int m, int d, double prior_var,
+                                  float* Xw, float* yw, uint16_t* ximg, cudaStream_t s);
 cudaError_t launch_zero_cov(DevState* st, int d, cudaStream_t s);
 cudaError_t launch_max_finalize(const double* part, int nb, DevState* st, cudaStream_t s);
 cudaError_t launch_cov(const ParticleArgs& a, double* cov, int grid, cudaStream_t s);

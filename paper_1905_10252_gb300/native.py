@@ -18,6 +18,7 @@ SMC_OK, SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA, SMC_ETIMEOUT, SMC_ENONFINITE = range(
 SMC_F32, SMC_F64 = 1, 2
 SMC_GAUSS, SMC_LOGISTIC, SMC_STUDENT_T = 1, 2, 3
 RESAMPLE_ESS, RESAMPLE_ALWAYS, RESAMPLE_NEVER = 0, 1, 2
+FLAG_LOGISTIC_CUDA_CORES = 1  # SMC_FLAG_LOGISTIC_CUDA_CORES
 
 EXPORTED = [
     "smc_workspace_bytes", "smc_init", "smc_move", "smc_reweight", "smc_estimate", "smc_resample",
@@ -43,7 +44,7 @@ class smc_config(C.Structure):
         ("n", C.c_int64), ("d", C.c_int32), ("dtype", C.c_int32), ("seed", C.c_uint64),
         ("target", C.c_int32), ("resample_mode", C.c_int32), ("step", C.c_double), ("init_scale", C.c_double),
         ("mu_dev", C.c_void_p), ("sigma_dev", C.c_void_p), ("X_dev", C.c_void_p), ("y_dev", C.c_void_p),
-        ("m", C.c_int32), ("reserved", C.c_int32), ("prior_var", C.c_double), ("nu", C.c_double),
+        ("m", C.c_int32), ("flags", C.c_int32), ("prior_var", C.c_double), ("nu", C.c_double),
     ]
 
 
@@ -217,28 +218,38 @@ class Sampler:
     """Owns the device buffers of one sampler and a libsmc handle.
 
     target='gauss' needs mu [D] and sigma [D, D]; target='student_t' needs mu
-    (scalar) and nu.  dtype is torch.float32 or torch.float64 (particle state).
+    (scalar) and nu; target='logistic' needs X [M, D], y [M] and prior_var.
+    dtype is torch.float32 or torch.float64 (particle state).
     """
 
     def __init__(self, n: int, d: int, *, dtype=torch.float32, seed: int = 0, target: str = "gauss",
                  mu=None, sigma=None, nu: float = 0.0, step: float = 0.5, init_scale: float = 2.0,
-                 resample_mode: int = RESAMPLE_ESS, device="cuda", stream: torch.cuda.Stream | None = None):
+                 resample_mode: int = RESAMPLE_ESS, device="cuda", stream: torch.cuda.Stream | None = None,
+                 X=None, y=None, prior_var: float = 4.0, flags: int = 0):
         L = lib()
         self.n, self.d, self.dtype = int(n), int(d), dtype
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         cur = torch.cuda.current_stream(self.device)
-        kind = {"gauss": SMC_GAUSS, "student_t": SMC_STUDENT_T}[target]
-        self.mu = torch.as_tensor(mu, dtype=torch.float64).reshape(-1).to(self.device)
-        self.sigma = (torch.as_tensor(sigma, dtype=torch.float64).reshape(d, d).contiguous().to(self.device)
-                      if sigma is not None else None)
+        kind = {"gauss": SMC_GAUSS, "student_t": SMC_STUDENT_T, "logistic": SMC_LOGISTIC}[target]
         cfg = smc_config()
         cfg.n, cfg.d = self.n, self.d
         cfg.dtype = SMC_F64 if dtype == torch.float64 else SMC_F32
         cfg.seed, cfg.target, cfg.resample_mode = int(seed), kind, int(resample_mode)
         cfg.step, cfg.init_scale, cfg.nu = float(step), float(init_scale), float(nu)
-        cfg.mu_dev = self.mu.data_ptr()
-        cfg.sigma_dev = self.sigma.data_ptr() if self.sigma is not None else None
+        cfg.flags = int(flags)
+        self.mu = self.sigma = self.X = self.y = None
+        if target == "logistic":
+            self.X = torch.as_tensor(X, dtype=torch.float32).reshape(-1, d).contiguous().to(self.device)
+            self.y = torch.as_tensor(y, dtype=torch.float32).reshape(-1).contiguous().to(self.device)
+            cfg.X_dev, cfg.y_dev = self.X.data_ptr(), self.y.data_ptr()
+            cfg.m, cfg.prior_var = int(self.X.shape[0]), float(prior_var)
+        else:
+            self.mu = torch.as_tensor(mu, dtype=torch.float64).reshape(-1).to(self.device)
+            self.sigma = (torch.as_tensor(sigma, dtype=torch.float64).reshape(d, d).contiguous().to(self.device)
+                          if sigma is not None else None)
+            cfg.mu_dev = self.mu.data_ptr()
+            cfg.sigma_dev = self.sigma.data_ptr() if self.sigma is not None else None
         self.cfg = cfg
         nbytes = C.c_size_t()
         _check(L.smc_workspace_bytes(C.byref(cfg), C.byref(nbytes)))

@@ -43,6 +43,61 @@ def test_logistic_logpi_naive(orc):
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-10)
 
 
+def _logistic_target(orc, M=200, D=6, seed=4, prior_var=4.0):
+    X, y, _ = inputs.logistic_data(M, D, seed=seed)
+    return X.astype(np.float64), y.astype(np.float64), orc.Target.logistic(X.astype(np.float64),
+                                                                          y.astype(np.float64), prior_var)
+
+
+def test_logistic_logpi_at_zero_is_minus_m_log2(orc):
+    """b = 0: every z_m = 0 and each row contributes -log 2 whatever its label."""
+    X, y, tgt = _logistic_target(orc)
+    got = tgt.logpi(np.zeros((1, X.shape[1])))[0]
+    assert abs(got - (-X.shape[0] * math.log(2.0))) <= 1e-12 * X.shape[0]
+
+
+def test_logistic_logpi_is_bernoulli_loglik_plus_gaussian_prior(orc):
+    """log pi = sum_m log Bernoulli(y_m | sigmoid(z_m)) + log N(b | 0, v I) up to
+    the prior's constant: scipy's logistic log-probabilities (log_expit) and
+    normal log-density, an implementation independent of the oracle."""
+    sp = pytest.importorskip("scipy.special")
+    ss = pytest.importorskip("scipy.stats")
+    X, y, tgt = _logistic_target(orc, prior_var=2.5)
+    B = np.random.default_rng(1).standard_normal((15, X.shape[1])) * 1.5
+    got = tgt.logpi(B)
+    D = X.shape[1]
+    const = D * 0.5 * math.log(2.0 * math.pi * 2.5)
+    for b, g in zip(B, got):
+        z = X @ b
+        ll = np.sum(y * sp.log_expit(z) + (1.0 - y) * sp.log_expit(-z))
+        lp = np.sum(ss.norm.logpdf(b, scale=math.sqrt(2.5))) + const
+        assert abs(g - (ll + lp)) <= 1e-9 * (1.0 + abs(g))
+
+
+def test_logistic_logpi_gradient_matches_closed_form(orc):
+    """Central differences of the oracle's log pi against the closed-form
+    gradient X^T (y - sigmoid(X b)) - b / v (a dropped term, a wrong sign or a
+    transposed X shows up here)."""
+    X, y, tgt = _logistic_target(orc, M=120, D=5, prior_var=3.0)
+    b = np.array([0.3, -0.7, 1.1, 0.05, -1.4])
+    g = X.T @ (y - 1.0 / (1.0 + np.exp(-(X @ b)))) - b / 3.0
+    h = 1e-5
+    for c in range(5):
+        e = np.zeros(5)
+        e[c] = h
+        fd = (tgt.logpi((b + e)[None])[0] - tgt.logpi((b - e)[None])[0]) / (2 * h)
+        assert abs(fd - g[c]) <= 1e-5 * (1.0 + abs(g[c]))
+
+
+def test_logistic_logpi_label_flip_symmetry(orc):
+    """sigmoid(-z) = 1 - sigmoid(z): flipping every label and negating b leaves
+    the likelihood unchanged, and the prior is symmetric."""
+    X, y, tgt = _logistic_target(orc)
+    flip = orc.Target.logistic(X, 1.0 - y, 4.0)
+    B = np.random.default_rng(2).standard_normal((10, X.shape[1]))
+    np.testing.assert_allclose(tgt.logpi(B), flip.logpi(-B), rtol=1e-13, atol=1e-10)
+
+
 def test_student_t_logpi(orc):
     st = pytest.importorskip("scipy.stats")
     tgt = orc.Target.student_t(1.5, 5.0)
