@@ -1,0 +1,395 @@
+// k_logistic_tc.cu -- the Bayesian logistic-regression log-likelihood of every
+// particle on the 5th-generation tensor cores (sm_103a), fused with the
+// importance reweighting of eq. (5):
+//
+//   log pi(b) = b . v - sum_m softplus(z_m) - |b|^2 / (2 prior_var),
+//   z = X b,  v = X^T y  (so sum_m y_m z_m = b . v needs no per-row work).
+//
+// Contraction.  A CTA owns a tile of 128 particles (MMA M = 128) and streams
+// the data matrix through shared memory in tiles of 256 rows (MMA N = 256,
+// K = 32 features, zero padded).  FP32 accuracy from BF16 tensor cores by the
+// split x = hi + lo (hi = bf16(x), lo = bf16(x - hi)) on both operands:
+//   z ~= B_hi X_hi + B_lo X_hi + B_hi X_lo   (FP32 accumulation in TMEM),
+// dropping only B_lo X_lo (relative size 2^-16 of the product).
+//
+// Epilogue (the real cost: one transcendental per matrix element).  With
+// a = |z|:  softplus(z) = (z + a) / 2 + ln(1 + 2^(-a log2 e)), so
+//   sum_m softplus(z_m) = (b . w + sum_m a_m) / 2 + ln 2 * sum_m log2(1 + e_m),
+// w = column sums of X (FP64, once), e_m = ex2.approx(-a_m log2 e) on the
+// multi-function unit; the log2 is taken once per 8 rows of a running FP32
+// product prod(1 + e_m) (each factor in (1, 2], so the product stays below
+// 2^8).  Zero padding rows give z = 0 exactly and contribute exactly 1 to the
+// log2 sum, removed as (m_pad - m).
+//
+// Warp roles (12 warps): warp 0 lane 0 issues the bulk copies of the data
+// tiles (4-stage ring, mbarrier complete_tx); warp 1 owns the TMEM allocation
+// (512 columns: two 128 x 256 FP32 accumulators) and lane 0 issues the MMAs;
+// warps 4-11 stage the particle tile's BF16 hi / lo images and run the
+// epilogue, two warps per TMEM lane quarter (128 columns each).  Every
+// mbarrier wait is bounded: on a timeout the CTA records SMC_ETIMEOUT, every
+// role drains its remaining loop iterations without waiting (so the named
+// barriers still match), waits (bounded) for its own copies in flight, frees
+// TMEM and returns.
+#include "smc_internal.cuh"
+#include "smc_kernels.h"
+
+namespace smc {
+namespace {
+
+constexpr int kTcPT = 128;                                  // particles per tile
+constexpr int kTcStages = 4;                                // data tile ring
+constexpr int kTcWarps = 12;
+constexpr int kTcThreads = 32 * kTcWarps;
+constexpr int kTcEpiThreads = 256;                          // warps 4..11
+constexpr uint32_t kTcCols = 512;                           // TMEM columns
+constexpr size_t kTcAImg = size_t(kTcPT) * kLgK * 2;        // one BF16 A image (8 KB)
+constexpr size_t kTcHalf = kLgTileBytes / 2;                // one BF16 data image (16 KB)
+// data ring + A images + partial sums + barriers / TMEM slot / flags / warp
+// maxima (512 bytes) + alignment slack
+constexpr size_t kTcSmem = kTcStages * kLgTileBytes + 2 * kTcAImg + 2 * kTcPT * sizeof(double) + 512 + 1024;
+constexpr long long kWaitCycles = 1ll << 31;                // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// tcgen05 shared-memory matrix descriptor: K-major, no swizzle; LBO = byte
+// distance between core matrices adjacent in K, SBO = between 8-row groups.
+__device__ __forceinline__ uint64_t mat_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((saddr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false after ~1 s (or at once when the CTA is already aborting).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  if (*abort_flag) return false;
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(b, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ uint16_t bf16_rn(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return uint16_t((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+// byte offset of element (row r, column k) in a K-major core-matrix image
+__device__ __forceinline__ uint32_t img_off(int r, int k) {
+  return uint32_t((r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* xs = sm;                                         // kTcStages x (hi | lo) data tiles
+  uint8_t* ahi = xs + kTcStages * kLgTileBytes;             // particle tile, BF16 hi image
+  uint8_t* alo = ahi + kTcAImg;                             // ... lo image
+  double* s_abs = reinterpret_cast<double*>(alo + kTcAImg); // [128] partial sums of the second column half
+  double* s_lg = s_abs + kTcPT;
+  uint64_t* full = reinterpret_cast<uint64_t*>(s_lg + kTcPT);
+  uint64_t* empty = full + kTcStages;
+  uint64_t* tfull = empty + kTcStages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  long long* wmax = reinterpret_cast<long long*>(tslot + 4);  // [kTcWarps]
+  int* wnan = reinterpret_cast<int*>(wmax + kTcWarps);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TargetDev* __restrict__ tg = a.tg;
+  const int cur = a.st->cur;
+  const float* __restrict__ x = static_cast<const float*>(cur ? a.x[1] : a.x[0]);
+  float* __restrict__ lp = static_cast<float*>(cur ? a.logpi[1] : a.logpi[0]);
+  const int64_t n = a.n;
+  const int d = a.d;
+  const int nx = tg->m_pad / kLgRows;
+  const int64_t npt = (n + kTcPT - 1) / kTcPT;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kTcEpiThreads / 32);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  MaxTracker mt;
+  mt.init();
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t g = 0;
+      const uint8_t* img = reinterpret_cast<const uint8_t*>(tg->ximg);
+      for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x) {
+        for (int j = 0; j < nx; ++j, ++g) {
+          const int s = int(g % kTcStages);
+          const uint32_t r = g / kTcStages;
+          if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) continue;
+          mbar_expect_tx(&full[s], uint32_t(kLgTileBytes));
+          bulk_g2s(xs + size_t(s) * kLgTileBytes, img + size_t(j) * kLgTileBytes, uint32_t(kLgTileBytes), &full[s]);
+        }
+      }
+      // after an abort: let copies still in flight land before the CTA exits
+      if (*abort_flag) {
+        const uint32_t last = g;
+        for (uint32_t k = (last > kTcStages ? last - kTcStages : 0); k < last; ++k) {
+          const int s = int(k % kTcStages);
+          const long long t0 = clock64();
+          while (!mbar_try(&full[s], (k / kTcStages) & 1) && clock64() - t0 < kWaitCycles) {
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    uint32_t g = 0, u = 0;
+    for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x) {
+      named_sync(1, 32 + kTcEpiThreads);  // the particle tile's images are in shared memory
+      tc_fence_after();
+      if (lane == 0) {
+        for (int j = 0; j < nx; ++j, ++g, ++u) {
+          const int s = int(g % kTcStages);
+          const int b = int(u & 1);
+          if (!mbar_wait(&full[s], (g / kTcStages) & 1, abort_flag)) continue;
+          if (!mbar_wait(&tempty[b], ((u >> 1) & 1) ^ 1, abort_flag)) continue;
+          tc_fence_after();
+          const uint32_t dcol = tmem + uint32_t(b) * 256;
+          const uint32_t xh = su32(xs + size_t(s) * kLgTileBytes), xl = xh + uint32_t(kTcHalf);
+          const uint32_t ah = su32(ahi), al = su32(alo);
+          uint32_t acc = 0;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            mma_bf16(dcol, mat_desc(ah + kk * 256, 128, 512), mat_desc(xh + kk * 256, 128, 512), acc);
+            acc = 1;
+            mma_bf16(dcol, mat_desc(al + kk * 256, 128, 512), mat_desc(xh + kk * 256, 128, 512), 1);
+            mma_bf16(dcol, mat_desc(ah + kk * 256, 128, 512), mat_desc(xl + kk * 256, 128, 512), 1);
+          }
+          mma_commit(&empty[s]);
+          mma_commit(&tfull[b]);
+        }
+      }
+      __syncwarp();
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------ stage + epilogue
+    const int et = threadIdx.x - 128;
+    const int q = warp & 3, h = (warp - 4) >> 2;
+    const int row = 32 * q + lane;
+    uint32_t u = 0;
+    const double log2_pad = double(tg->m_pad - tg->m);
+    for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x) {
+      // particle tile -> BF16 hi / lo images (thread et: row et % 128, 16 columns)
+      {
+        const int r = et & (kTcPT - 1), k0 = (et >> 7) * 16;
+        const int64_t i = pt * kTcPT + r;
+#pragma unroll
+        for (int k = k0; k < k0 + 16; ++k) {
+          const float v = (i < n && k < d) ? x[i * d + k] : 0.0f;
+          const uint16_t hi = bf16_rn(v);
+          const uint16_t lo = bf16_rn(v - __uint_as_float(uint32_t(hi) << 16));
+          *reinterpret_cast<uint16_t*>(ahi + img_off(r, k)) = hi;
+          *reinterpret_cast<uint16_t*>(alo + img_off(r, k)) = lo;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      named_sync(1, 32 + kTcEpiThreads);
+      double acc_abs = 0.0, acc_lg = 0.0;
+      for (int j = 0; j < nx; ++j, ++u) {
+        const int b = int(u & 1);
+        // warp-uniform outcome: tcgen05.ld below is a warp-collective
+        const bool ready = __all_sync(0xffffffffu, mbar_wait(&tfull[b], (u >> 1) & 1, abort_flag));
+        if (ready) {
+          tc_fence_after();
+          float sabs = 0.0f, slg = 0.0f;
+#pragma unroll 1
+          for (int c = 0; c < 4; ++c) {
+            float z[32];
+            tmem_ld32(tmem + (uint32_t(32 * q) << 16) + uint32_t(b * 256 + h * 128 + c * 32), z);
+#pragma unroll
+            for (int g8 = 0; g8 < 4; ++g8) {
+              float prod = 1.0f;
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const float az = fabsf(z[8 * g8 + e]);
+                sabs += az;
+                prod = fmaf(prod, ex2_approx(az * -1.4426950408889634f), prod);
+              }
+              slg += lg2_approx(prod);
+            }
+          }
+          acc_abs += double(sabs);
+          acc_lg += double(slg);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+      }
+      if (h == 1) {
+        s_abs[row] = acc_abs;
+        s_lg[row] = acc_lg;
+      }
+      named_sync(2, kTcEpiThreads);
+      if (h == 0) {
+        const int64_t i = pt * kTcPT + row;
+        if (i < n && !*abort_flag) {
+          const double sum_abs = acc_abs + s_abs[row];
+          const double sum_lg = acc_lg + s_lg[row] - log2_pad;
+          double bv = 0.0, bw = 0.0, b2 = 0.0;
+          for (int c = 0; c < d; ++c) {
+            const double bc = double(x[i * d + c]);
+            bv = fma(bc, tg->v[c], bv);
+            bw = fma(bc, tg->xsum[c], bw);
+            b2 = fma(bc, bc, b2);
+          }
+          const double sp = 0.5 * (bw + sum_abs) + 0.6931471805599453 * sum_lg;
+          const float lpn = float(bv - sp - b2 / (2.0 * tg->prior_var));
+          // eq. (5): the log-target difference in FP32 (exact when the two
+          // values are within a factor of two), one FP64 addition
+          const double lw = a.logw[i] + double(lpn - lp[i]);
+          lp[i] = lpn;
+          a.logw[i] = lw;
+          mt.add(lw);
+        }
+      }
+      // s_abs / s_lg are rewritten only after the next tile's staging barrier
+    }
+  }
+
+  // ------------------------------------------------------------ block maximum, teardown
+  __syncwarp();
+  {
+    const long long wm = warp_max_ll(mt.best);
+    const int wn = __any_sync(0xffffffffu, mt.nan);
+    if (lane == 0) {
+      wmax[warp] = wm;
+      wnan[warp] = wn;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long v = wmax[0];
+    int nan = wnan[0];
+    for (int w = 1; w < kTcWarps; ++w) {
+      v = wmax[w] > v ? wmax[w] : v;
+      nan |= wnan[w];
+    }
+    a.part[2 * blockIdx.x] = from_ordered_key(v);
+    a.part[2 * blockIdx.x + 1] = 1.0;
+    if (nan) record_error(a.st, SMC_ENONFINITE);
+    if (*abort_flag) record_error(a.st, SMC_ETIMEOUT);
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+  }
+}
+
+}  // namespace
+
+int logistic_tc_grid(int64_t n, int sms) {
+  const int64_t npt = (n + kTcPT - 1) / kTcPT;
+  return int(npt < sms ? npt : sms);
+}
+
+cudaError_t launch_logistic_tc(const ParticleArgs& a, int grid, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_logistic_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_logistic_tc<<<grid, kTcThreads, kTcSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace smc

@@ -106,14 +106,20 @@ __global__ void k_logistic_copy(TargetDev* tg, const float* __restrict__ X, cons
   }
 }
 
-// v_c = sum_m y_m X_mc in FP64, row order (one thread per column).
+// v_c = sum_m y_m X_mc and the column sums of X, in FP64, row order (one
+// thread per column).
 __global__ void k_logistic_v(TargetDev* tg, const float* __restrict__ X, const float* __restrict__ y, int m, int d) {
   const int c = threadIdx.x;
   if (c >= kTgtMaxD) return;
-  double acc = 0.0;
+  double acc = 0.0, sum = 0.0;
   if (c < d)
-    for (int r = 0; r < m; ++r) acc = fma(double(y[r]), double(X[int64_t(r) * d + c]), acc);
+    for (int r = 0; r < m; ++r) {
+      const double xv = double(X[int64_t(r) * d + c]);
+      acc = fma(double(y[r]), xv, acc);
+      sum += xv;
+    }
   tg->v[c] = acc;
+  tg->xsum[c] = sum;
 }
 
 // ---------------------------------------------------------------- log targets
@@ -238,44 +244,6 @@ __device__ __forceinline__ void store_row(T* __restrict__ p, int d, const T (&x)
     for (int c = 0; c < DMAX; ++c)
       if (c < d) p[c] = x[c];
   }
-}
-
-// ---------------------------------------------------------------- running maximum of log w
-// Doubles compared as integers (order-preserving map of the bit pattern): the
-// FP64 pipe of GB300 runs at a small fraction of its integer rate.
-__device__ __forceinline__ long long ordered_key(double v) {
-  const long long b = __double_as_longlong(v);
-  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
-}
-__device__ __forceinline__ double from_ordered_key(long long k) {
-  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFll));
-}
-
-struct MaxTracker {
-  long long best;
-  bool nan;
-  __device__ __forceinline__ void init() {
-    best = ordered_key(-INFINITY);
-    nan = false;
-  }
-  __device__ __forceinline__ void add(double v) {
-    const long long b = __double_as_longlong(v);
-    if ((b & 0x7FF0000000000000ll) == 0x7FF0000000000000ll && (b & 0x000FFFFFFFFFFFFFll)) {
-      nan = true;
-      return;
-    }
-    const long long k = b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
-    best = k > best ? k : best;
-  }
-};
-
-__device__ __forceinline__ long long warp_max_ll(long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
 }
 
 // One record per block: rec[0] = max log w of the block, rec[1] = 1.

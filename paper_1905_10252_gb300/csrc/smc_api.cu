@@ -188,9 +188,9 @@ RedistArgs redist_args(const smc_sampler* h, int force) {
 namespace {
 
 // Weighted statistics after a reweight: max, quantised sums with the mean of
-// eq. (7), decision.
-cudaError_t launch_stats(smc_sampler* h, int set_lse_prev) {
-  cudaError_t e = launch_max_finalize(h->part, h->grid_p, h->st, h->stream);
+// eq. (7), decision.  nb: max records written by the reweighting kernel.
+cudaError_t launch_stats(smc_sampler* h, int set_lse_prev, int nb) {
+  cudaError_t e = launch_max_finalize(h->part, nb, h->st, h->stream);
   if (e != cudaSuccess) return e;
   const QuantArgs q = quant_args(h, 0, nullptr);
   e = launch_quant_reduce(q, h->stream);
@@ -198,12 +198,26 @@ cudaError_t launch_stats(smc_sampler* h, int set_lse_prev) {
   return launch_quant_finalize(q, set_lse_prev, h->stream);
 }
 
+// Move and reweight of one iteration (Algorithm 2, line 4; eq. (5)); returns
+// the number of max records written.
+cudaError_t launch_move_reweight(smc_sampler* h, const ParticleArgs& a, int* nb) {
+  if (h->lg_tc) {
+    cudaError_t e = launch_particles(OP_MOVE, a, h->grid_p, h->stream);
+    if (e == cudaSuccess) e = launch_logistic_tc(a, h->grid_lg, h->stream);
+    *nb = h->grid_lg;
+    return e;
+  }
+  *nb = h->grid_p;
+  return launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, h->stream, gauss_params(h));
+}
+
 // One iteration of Algorithm 2 (lines 3-10), all on h->stream.
 cudaError_t launch_iteration(smc_sampler* h, bool with_cov) {
   const ParticleArgs a = particle_args(h);
+  int nb = 0;
   cudaError_t e = launch_begin(h->st, h->stream);
-  if (e == cudaSuccess) e = launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, h->stream, gauss_params(h));
-  if (e == cudaSuccess) e = launch_max_finalize(h->part, h->grid_p, h->st, h->stream);
+  if (e == cudaSuccess) e = launch_move_reweight(h, a, &nb);
+  if (e == cudaSuccess) e = launch_max_finalize(h->part, nb, h->st, h->stream);
   const QuantArgs q = quant_args(h, 0, nullptr);
   if (e == cudaSuccess) e = launch_quant_reduce(q, h->stream);
   if (e == cudaSuccess) e = launch_quant_finalize(q, 0, h->stream);
@@ -308,6 +322,8 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   h->grid_p = int(std::min<int64_t>(div_up(h->n * lanes_per_particle(h->dtype, h->d), kPThreads),
                                     int64_t(sm_count()) * 8));
   if (h->grid_p > kMaxPartBlocks) h->grid_p = kMaxPartBlocks;
+  h->lg_tc = cfg->target == SMC_LOGISTIC && cfg->dtype == SMC_F32 && !(cfg->flags & SMC_FLAG_LOGISTIC_CUDA_CORES);
+  h->grid_lg = logistic_tc_grid(h->n, sm_count());
   h->g_iter[0] = h->g_iter[1] = nullptr;
   h->have_gp = false;
   h->err = "ok";
@@ -325,7 +341,10 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
       e = launch_target_setup(h->tg, cfg->target, cfg->nu, cfg->mu_dev, cfg->sigma_dev, h->d, h->st, h->stream);
   }
   if (e == cudaSuccess) e = launch_particles(OP_INIT, particle_args(h), h->grid_p, h->stream);
-  if (e == cudaSuccess) e = launch_stats(h, 1);
+  // the tensor-core likelihood replaces the CUDA-core log pi of x_0, so that
+  // every later difference of eq. (5) compares values of one method
+  if (e == cudaSuccess && h->lg_tc) e = launch_logistic_tc(particle_args(h), h->grid_lg, h->stream);
+  if (e == cudaSuccess) e = launch_stats(h, 1, h->lg_tc ? h->grid_lg : h->grid_p);
   if (e == cudaSuccess && cfg->target == SMC_GAUSS && h->dtype == SMC_F32) {
     // the FP32 factor becomes a kernel parameter of the move / reweight kernel
     static thread_local float Pf[kTgtMaxD * kTgtMaxD], muf[kTgtMaxD];
@@ -357,8 +376,13 @@ int smc_move(smc_sampler* h) {
 
 int smc_reweight(smc_sampler* h) {
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
-  SMC_TRY(h, launch_particles(OP_REWEIGHT, particle_args(h), h->grid_p, h->stream, gauss_params(h)));
-  SMC_TRY(h, launch_stats(h, 0));
+  if (h->lg_tc) {
+    SMC_TRY(h, launch_logistic_tc(particle_args(h), h->grid_lg, h->stream));
+    SMC_TRY(h, launch_stats(h, 0, h->grid_lg));
+  } else {
+    SMC_TRY(h, launch_particles(OP_REWEIGHT, particle_args(h), h->grid_p, h->stream, gauss_params(h)));
+    SMC_TRY(h, launch_stats(h, 0, h->grid_p));
+  }
   return SMC_OK;
 }
 
@@ -433,11 +457,12 @@ int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host,
   SMC_TRY(h, launch_step_setup(h->st, nullptr, mean_dev, nullptr, nullptr, s));
   const ParticleArgs a = particle_args(h);
   const QuantArgs q = quant_args(h, 0, nullptr);
+  int nb = 0;
   SMC_TRY(h, rec(0));
   SMC_TRY(h, launch_begin(h->st, s));
-  SMC_TRY(h, launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, s, gauss_params(h)));
+  SMC_TRY(h, launch_move_reweight(h, a, &nb));
   SMC_TRY(h, rec(1));
-  SMC_TRY(h, launch_max_finalize(h->part, h->grid_p, h->st, s));
+  SMC_TRY(h, launch_max_finalize(h->part, nb, h->st, s));
   SMC_TRY(h, rec(2));
   SMC_TRY(h, launch_quant_reduce(q, s));
   SMC_TRY(h, rec(3));

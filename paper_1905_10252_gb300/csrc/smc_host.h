@@ -39,6 +39,9 @@ struct smc_sampler {
   uint64_t* wbuf;
   int32_t* tile_src;
   int grid_p;
+  // FP32 logistic samplers: likelihood on the tensor cores (its own grid)
+  bool lg_tc;
+  int grid_lg;
   // FP32 Gaussian factor for the move / reweight kernel's parameters
   smc::GaussParamsF32 gp;
   bool have_gp;

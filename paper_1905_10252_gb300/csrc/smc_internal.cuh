@@ -349,4 +349,43 @@ __device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t* sc
   return r;
 }
 
+// ---------------------------------------------------------------- running maximum of log w
+// Doubles compared as integers (order-preserving map of the bit pattern): the
+// FP64 pipe of GB300 runs at a small fraction of its integer rate.
+__device__ __forceinline__ long long ordered_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double from_ordered_key(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFll));
+}
+
+struct MaxTracker {
+  long long best;
+  bool nan;
+  __device__ __forceinline__ void init() {
+    best = ordered_key(-INFINITY);
+    nan = false;
+  }
+  __device__ __forceinline__ void add(double v) {
+    const long long b = __double_as_longlong(v);
+    if ((b & 0x7FF0000000000000ll) == 0x7FF0000000000000ll && (b & 0x000FFFFFFFFFFFFFll)) {
+      nan = true;
+      return;
+    }
+    const long long k = b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+    best = k > best ? k : best;
+  }
+};
+
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+
 }  // namespace smc

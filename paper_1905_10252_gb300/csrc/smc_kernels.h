@@ -30,6 +30,7 @@ struct alignas(256) TargetDev {
   const float* y;         // M labels
   const uint16_t* ximg;   // BF16 hi / lo images of X for the tensor-core likelihood
   double v[kTgtMaxD];     // X^T y in FP64
+  double xsum[kTgtMaxD];  // column sums of X in FP64
   double prior_var;
   int32_t m;
   int32_t m_pad;          // M rounded up to the likelihood's data tile
@@ -149,6 +150,12 @@ cudaError_t launch_commit(DevState* st, int d, int force_flip, int recycle, cuda
 cudaError_t launch_copy_mean(const DevState* st, double* out, int d, cudaStream_t s);
 cudaError_t launch_step_setup(DevState* st, smc_iter_stats* trace, double* mean_out, double* fhat_out,
                               double* cov_out, cudaStream_t s);
+
+// Logistic likelihood on the tensor cores, fused with the reweight of eq. (5)
+// (k_logistic_tc.cu): log pi of the current particles, log w += new - old,
+// one max record per CTA in a.part (grid = logistic_tc_grid(n, SMs)).
+int logistic_tc_grid(int64_t n, int sms);
+cudaError_t launch_logistic_tc(const ParticleArgs& a, int grid, cudaStream_t s);
 
 // batched launches (one per stage for many samplers; int4 map = {sampler, block, blocks, 0})
 cudaError_t launch_move_reweight_batch(const ParticleArgs* pa, const GaussParamsF32* gps, const int4* map, int nblocks,
