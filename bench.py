@@ -17,6 +17,9 @@ stepped by one batched launch per stage (CUDA graph, autotuned launch shapes),
 against the same samplers stepped one sampler per launch (each its own graph
 on its own stream, all streams concurrent; and one after another);
 a step is one iteration of every sampler (--steps 50 is the workload's K).
+--workload logistic: Bayesian logistic regression, N = 2^18 FP32 particles,
+M = 8192 rows, D = 32 features; the likelihood on the tensor cores (tcgen05,
+BF16 hi / lo split) next to the CUDA-core FP32 likelihood of the same sampler.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (rank 0 only).
 Multi-GPU (torchrun): independent replicas, one sampler per GPU, no collective
@@ -50,7 +53,8 @@ def parse():
     p.add_argument("--steps", type=int, default=400)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="iteration", choices=["iteration", "redistribute", "batch"])
+    p.add_argument("--workload", default="iteration", choices=["iteration", "redistribute", "batch", "logistic"])
+    p.add_argument("--m", type=int, default=8192, help="logistic workload: data rows")
     p.add_argument("--count", type=int, default=256, help="batch workload: samplers")
     p.add_argument("--n", type=int, default=1 << 24)
     p.add_argument("--d", type=int, default=16)
@@ -564,6 +568,101 @@ def run_batch(args):
         m.close()
 
 
+def run_logistic(args):
+    """Bayesian logistic regression sampler: tensor-core likelihood."""
+    import torch
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1905_10252_gb300 import build as B
+
+    B.build()
+    from paper_1905_10252_gb300 import inputs, native
+
+    n, d, m = (args.n if args.n != (1 << 24) else 1 << 18), 32, args.m
+    X, y, _ = inputs.logistic_data(m, d, seed=0)
+
+    def sampler(flags):
+        return native.Sampler(n, d, dtype=torch.float32, seed=rank, target="logistic", X=X, y=y, prior_var=4.0,
+                              step=0.02, init_scale=0.5, flags=flags)
+
+    S = sampler(0)
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        S.step_profile()
+    n_prof = 10
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(n_prof)]
+    for row in ev:
+        for e in row:
+            e.record(S.stream)
+    for row in ev:
+        S.step_profile(row)
+    torch.cuda.synchronize()
+    stage_ms = {name: float(np.mean([row[j].elapsed_time(row[j + 1]) for row in ev])) for j, name in enumerate(STAGES)}
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_host0 = time.time()
+    start.record(S.stream)
+    S.step(K)
+    stop.record(S.stream)
+    torch.cuda.synchronize()
+    t_host1 = time.time()
+    time.sleep(0.15)
+    clocks.stop()
+    S.sync()
+    total_ms = max_over_ranks(start.elapsed_time(stop), ws, device="cuda")
+    # the CUDA-core FP32 likelihood on the same workload (a few iterations)
+    C = sampler(native.FLAG_LOGISTIC_CUDA_CORES)
+    cev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(3)]
+    for row in cev:
+        for e in row:
+            e.record(C.stream)
+    C.step_profile()
+    for row in cev:
+        C.step_profile(row)
+    torch.cuda.synchronize()
+    cc_ms = float(np.mean([row[0].elapsed_time(row[1]) for row in cev]))
+    C.close()
+    clk = clocks.summary(t_host0, t_host1)
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    lik_ms = stage_ms["move_reweight"]
+    elems = float(n) * float(((m + 255) // 256) * 256)
+    mufu_peak = 152 * 16 * sm_mhz * 1e6 / 1.125  # elements/s: one ex2 + 1/8 lg2 per element on 16 MUFU lanes / SM
+    tensor_flops = 3 * 2.0 * elems * 32
+    meas = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            meas = json.load(f)
+    except OSError:
+        pass
+    bf16_peak = float(meas.get("bf16_tflops", 1900.0))
+    value = job_value(n, K, ws, total_ms)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 state / bf16x3 tensor contraction, f32 accumulate / f64 weights", "data": "synthetic",
+            "config": {"workload": f"logistic regression N=2^{int(np.log2(n))} M={m} D={d} fp32 resample when "
+                                   "N_eff < N/2", "n": n, "m": m, "d": d, "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "alu", "achieved": round(elems / (lik_ms * 1e-3) / 1e9, 1),
+                         "peak": round(mufu_peak / 1e9, 1), "unit": "Gelem/s",
+                         "frac": round(elems / (lik_ms * 1e-3) / mufu_peak, 4), "traffic": None,
+                         "note": "move + likelihood stage; peak = MUFU rate at the sampled SM clock / 1.125 ops "
+                                 "per element"},
+            "tensor": {"achieved_tflops": round(tensor_flops / (lik_ms * 1e-3) / 1e12, 1),
+                       "peak_tflops": bf16_peak, "frac": round(tensor_flops / (lik_ms * 1e-3) / 1e12 / bf16_peak, 4)},
+            "likelihood_ms": {"tensor_cores": round(lik_ms, 4), "cuda_cores_fp32": round(cc_ms, 4),
+                              "speedup": round(cc_ms / lik_ms, 2)},
+            "stages_ms": {k: round(v, 5) for k, v in stage_ms.items()},
+            "gpu_launches": 9 * K,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    S.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -572,6 +671,8 @@ def main():
         run_redistribute(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "logistic":
+        run_logistic(args)
     else:
         run_iteration(args)
 
