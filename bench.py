@@ -629,7 +629,7 @@ def run_logistic(args):
     sm_mhz = clk.get("sm_mhz") or 2070.0
     lik_ms = stage_ms["move_reweight"]
     elems = float(n) * float(((m + 255) // 256) * 256)
-    mufu_peak = 152 * 16 * sm_mhz * 1e6 / 1.125  # elements/s: one ex2 + 1/8 lg2 per element on 16 MUFU lanes / SM
+    mufu_peak = 152 * 16 * sm_mhz * 1e6 / 1.0625  # elements/s: one ex2 + 1/16 lg2 per element, 16 MUFU lanes / SM
     tensor_flops = 3 * 2.0 * elems * 32
     meas = {}
     try:
@@ -649,7 +649,7 @@ def run_logistic(args):
             "roofline": {"bound": "alu", "achieved": round(elems / (lik_ms * 1e-3) / 1e9, 1),
                          "peak": round(mufu_peak / 1e9, 1), "unit": "Gelem/s",
                          "frac": round(elems / (lik_ms * 1e-3) / mufu_peak, 4), "traffic": None,
-                         "note": "move + likelihood stage; peak = MUFU rate at the sampled SM clock / 1.125 ops "
+                         "note": "move + likelihood stage; peak = MUFU rate at the sampled SM clock / 1.0625 ops "
                                  "per element"},
             "tensor": {"achieved_tflops": round(tensor_flops / (lik_ms * 1e-3) / 1e12, 1),
                        "peak_tflops": bf16_peak, "frac": round(tensor_flops / (lik_ms * 1e-3) / 1e12 / bf16_peak, 4)},

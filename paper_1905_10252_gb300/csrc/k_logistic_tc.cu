@@ -16,16 +16,18 @@
 // a = |z|:  softplus(z) = (z + a) / 2 + ln(1 + 2^(-a log2 e)), so
 //   sum_m softplus(z_m) = (b . w + sum_m a_m) / 2 + ln 2 * sum_m log2(1 + e_m),
 // w = column sums of X (FP64, once), e_m = ex2.approx(-a_m log2 e) on the
-// multi-function unit; the log2 is taken once per 8 rows of a running FP32
+// multi-function unit; the log2 is taken once per 16 rows of a running FP32
 // product prod(1 + e_m) (each factor in (1, 2], so the product stays below
-// 2^8).  Zero padding rows give z = 0 exactly and contribute exactly 1 to the
+// 2^16).  Zero padding rows give z = 0 exactly and contribute exactly 1 to the
 // log2 sum, removed as (m_pad - m).
 //
-// Warp roles (12 warps): warp 0 lane 0 issues the bulk copies of the data
+// Warp roles (20 warps): warp 0 lane 0 issues the bulk copies of the data
 // tiles (4-stage ring, mbarrier complete_tx); warp 1 owns the TMEM allocation
 // (512 columns: two 128 x 256 FP32 accumulators) and lane 0 issues the MMAs;
-// warps 4-11 stage the particle tile's BF16 hi / lo images and run the
-// epilogue, two warps per TMEM lane quarter (128 columns each).  Every
+// warps 2-3 stage each particle tile's BF16 hi / lo images (double buffered,
+// so the next tile is staged while the current one is contracted); warps
+// 4-19 run the epilogue, four warps per TMEM lane quarter (64 columns each).
+// Every
 // mbarrier wait is bounded: on a timeout the CTA records SMC_ETIMEOUT, every
 // role drains its remaining loop iterations without waiting (so the named
 // barriers still match), waits (bounded) for its own copies in flight, frees
@@ -38,15 +40,19 @@ namespace {
 
 constexpr int kTcPT = 128;                                  // particles per tile
 constexpr int kTcStages = 4;                                // data tile ring
-constexpr int kTcWarps = 12;
+constexpr int kTcWarps = 20;
 constexpr int kTcThreads = 32 * kTcWarps;
-constexpr int kTcEpiThreads = 256;                          // warps 4..11
+constexpr int kTcStageThreads = 64;                         // warps 2..3
+constexpr int kTcEpiWarps = 16;                             // warps 4..19
+constexpr int kTcEpiThreads = 32 * kTcEpiWarps;
+constexpr int kTcEpiCols = 256 / (kTcEpiWarps / 4);         // accumulator columns per epilogue warp
 constexpr uint32_t kTcCols = 512;                           // TMEM columns
 constexpr size_t kTcAImg = size_t(kTcPT) * kLgK * 2;        // one BF16 A image (8 KB)
 constexpr size_t kTcHalf = kLgTileBytes / 2;                // one BF16 data image (16 KB)
-// data ring + A images + partial sums + barriers / TMEM slot / flags / warp
-// maxima (512 bytes) + alignment slack
-constexpr size_t kTcSmem = kTcStages * kLgTileBytes + 2 * kTcAImg + 2 * kTcPT * sizeof(double) + 512 + 1024;
+// data ring + two (hi, lo) A image pairs + partial sums of the column groups
+// 1..3 + barriers / TMEM slot / flags / warp maxima (1 KB) + alignment slack
+constexpr size_t kTcSmem =
+    kTcStages * kLgTileBytes + 4 * kTcAImg + 2 * (kTcEpiWarps / 4 - 1) * kTcPT * sizeof(double) + 1024 + 1024;
 constexpr long long kWaitCycles = 1ll << 31;                // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -153,15 +159,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* xs = sm;                                         // kTcStages x (hi | lo) data tiles
-  uint8_t* ahi = xs + kTcStages * kLgTileBytes;             // particle tile, BF16 hi image
-  uint8_t* alo = ahi + kTcAImg;                             // ... lo image
-  double* s_abs = reinterpret_cast<double*>(alo + kTcAImg); // [128] partial sums of the second column half
-  double* s_lg = s_abs + kTcPT;
-  uint64_t* full = reinterpret_cast<uint64_t*>(s_lg + kTcPT);
+  uint8_t* aimg = xs + kTcStages * kLgTileBytes;            // [2] x (hi, lo) particle tile images
+  constexpr int kGroups = kTcEpiWarps / 4;                  // column groups per lane quarter
+  double* s_abs = reinterpret_cast<double*>(aimg + 4 * kTcAImg);  // [kGroups - 1][128]
+  double* s_lg = s_abs + (kGroups - 1) * kTcPT;
+  uint64_t* full = reinterpret_cast<uint64_t*>(s_lg + (kGroups - 1) * kTcPT);
   uint64_t* empty = full + kTcStages;
   uint64_t* tfull = empty + kTcStages;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* afull = tempty + 2;
+  uint64_t* aempty = afull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   long long* wmax = reinterpret_cast<long long*>(tslot + 4);  // [kTcWarps]
   int* wnan = reinterpret_cast<int*>(wmax + kTcWarps);
@@ -183,7 +191,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], kTcEpiThreads / 32);
+      mbar_init(&tempty[b], kTcEpiWarps);
+      mbar_init(&afull[b], kTcStageThreads);
+      mbar_init(&aempty[b], 1);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -230,20 +240,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
     __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    uint32_t g = 0, u = 0;
-    for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x) {
-      named_sync(1, 32 + kTcEpiThreads);  // the particle tile's images are in shared memory
-      tc_fence_after();
-      if (lane == 0) {
+    if (lane == 0) {
+      uint32_t g = 0, u = 0, v = 0;
+      for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x, ++v) {
+        const int ab = int(v & 1);
+        const bool have_a = mbar_wait(&afull[ab], (v >> 1) & 1, abort_flag);
+        tc_fence_after();
+        const uint32_t ah = su32(aimg + size_t(2 * ab) * kTcAImg), al = ah + uint32_t(kTcAImg);
         for (int j = 0; j < nx; ++j, ++g, ++u) {
           const int s = int(g % kTcStages);
           const int b = int(u & 1);
+          if (!have_a) continue;
           if (!mbar_wait(&full[s], (g / kTcStages) & 1, abort_flag)) continue;
           if (!mbar_wait(&tempty[b], ((u >> 1) & 1) ^ 1, abort_flag)) continue;
           tc_fence_after();
           const uint32_t dcol = tmem + uint32_t(b) * 256;
           const uint32_t xh = su32(xs + size_t(s) * kLgTileBytes), xl = xh + uint32_t(kTcHalf);
-          const uint32_t ah = su32(ahi), al = su32(alo);
           uint32_t acc = 0;
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
@@ -255,32 +267,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
           mma_commit(&empty[s]);
           mma_commit(&tfull[b]);
         }
+        // the A images of this tile are free once its MMAs have completed
+        if (have_a) mma_commit(&aempty[ab]);
       }
-      __syncwarp();
     }
-  } else if (warp >= 4) {
-    // ------------------------------------------------------------ stage + epilogue
-    const int et = threadIdx.x - 128;
+    __syncwarp();
+  } else if (warp < 4) {
+    // ------------------------------------------------------------ A image stager
+    const int t = threadIdx.x - 64;
+    uint32_t v = 0;
+    for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x, ++v) {
+      const int ab = int(v & 1);
+      const bool free_buf = __all_sync(0xffffffffu, mbar_wait(&aempty[ab], ((v >> 1) & 1) ^ 1, abort_flag));
+      if (free_buf) {
+        uint8_t* ahi = aimg + size_t(2 * ab) * kTcAImg;
+        uint8_t* alo = ahi + kTcAImg;
+        for (int e = t; e < kTcPT * kLgK; e += kTcStageThreads) {
+          const int r = e / kLgK, k = e % kLgK;
+          const int64_t i = pt * kTcPT + r;
+          const float val = (i < n && k < d) ? x[i * d + k] : 0.0f;
+          const uint16_t hi = bf16_rn(val);
+          const uint16_t lo = bf16_rn(val - __uint_as_float(uint32_t(hi) << 16));
+          *reinterpret_cast<uint16_t*>(ahi + img_off(r, k)) = hi;
+          *reinterpret_cast<uint16_t*>(alo + img_off(r, k)) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      mbar_arrive(&afull[ab]);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
     const int q = warp & 3, h = (warp - 4) >> 2;
     const int row = 32 * q + lane;
     uint32_t u = 0;
     const double log2_pad = double(tg->m_pad - tg->m);
     for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x) {
-      // particle tile -> BF16 hi / lo images (thread et: row et % 128, 16 columns)
-      {
-        const int r = et & (kTcPT - 1), k0 = (et >> 7) * 16;
-        const int64_t i = pt * kTcPT + r;
-#pragma unroll
-        for (int k = k0; k < k0 + 16; ++k) {
-          const float v = (i < n && k < d) ? x[i * d + k] : 0.0f;
-          const uint16_t hi = bf16_rn(v);
-          const uint16_t lo = bf16_rn(v - __uint_as_float(uint32_t(hi) << 16));
-          *reinterpret_cast<uint16_t*>(ahi + img_off(r, k)) = hi;
-          *reinterpret_cast<uint16_t*>(alo + img_off(r, k)) = lo;
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      named_sync(1, 32 + kTcEpiThreads);
       double acc_abs = 0.0, acc_lg = 0.0;
       for (int j = 0; j < nx; ++j, ++u) {
         const int b = int(u & 1);
@@ -290,15 +311,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
           tc_fence_after();
           float sabs = 0.0f, slg = 0.0f;
 #pragma unroll 1
-          for (int c = 0; c < 4; ++c) {
+          for (int c = 0; c < kTcEpiCols / 32; ++c) {
             float z[32];
-            tmem_ld32(tmem + (uint32_t(32 * q) << 16) + uint32_t(b * 256 + h * 128 + c * 32), z);
+            tmem_ld32(tmem + (uint32_t(32 * q) << 16) + uint32_t(b * 256 + h * kTcEpiCols + c * 32), z);
 #pragma unroll
-            for (int g8 = 0; g8 < 4; ++g8) {
+            for (int g16 = 0; g16 < 2; ++g16) {
               float prod = 1.0f;
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const float az = fabsf(z[8 * g8 + e]);
+              for (int e = 0; e < 16; ++e) {
+                const float az = fabsf(z[16 * g16 + e]);
                 sabs += az;
                 prod = fmaf(prod, ex2_approx(az * -1.4426950408889634f), prod);
               }
@@ -312,16 +333,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
       }
-      if (h == 1) {
-        s_abs[row] = acc_abs;
-        s_lg[row] = acc_lg;
+      if (h > 0) {
+        s_abs[(h - 1) * kTcPT + row] = acc_abs;
+        s_lg[(h - 1) * kTcPT + row] = acc_lg;
       }
       named_sync(2, kTcEpiThreads);
       if (h == 0) {
         const int64_t i = pt * kTcPT + row;
         if (i < n && !*abort_flag) {
-          const double sum_abs = acc_abs + s_abs[row];
-          const double sum_lg = acc_lg + s_lg[row] - log2_pad;
+          double sum_abs = acc_abs, sum_lg = acc_lg - log2_pad;
+#pragma unroll
+          for (int g2 = 0; g2 < kGroups - 1; ++g2) {
+            sum_abs += s_abs[g2 * kTcPT + row];
+            sum_lg += s_lg[g2 * kTcPT + row];
+          }
           double bv = 0.0, bw = 0.0, b2 = 0.0;
           for (int c = 0; c < d; ++c) {
             const double bc = double(x[i * d + c]);
@@ -339,7 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
           mt.add(lw);
         }
       }
-      // s_abs / s_lg are rewritten only after the next tile's staging barrier
+      named_sync(2, kTcEpiThreads);  // partial sums read before the next tile writes them
     }
   }
 
