@@ -12,11 +12,13 @@
 //   z ~= B_hi X_hi + B_lo X_hi + B_hi X_lo   (FP32 accumulation in TMEM),
 // dropping only B_lo X_lo (relative size 2^-16 of the product).
 //
-// Epilogue (the real cost: one transcendental per matrix element).  With
-// a = |z|:  softplus(z) = (z + a) / 2 + ln(1 + 2^(-a log2 e)), so
-//   sum_m softplus(z_m) = (b . w + sum_m a_m) / 2 + ln 2 * sum_m log2(1 + e_m),
-// w = column sums of X (FP64, once), e_m = ex2.approx(-a_m log2 e) on the
-// multi-function unit; the log2 is taken once per 16 rows of a running FP32
+// Epilogue (the real cost: one transcendental per matrix element).  The data
+// images hold X log2(e), so the accumulator holds z' = z log2 e and, with
+// a = |z'|:  softplus(z) = (z + a ln 2) / 2 + ln(1 + 2^-a), so
+//   sum_m softplus(z_m) = (b . w + ln 2 sum_m a_m) / 2 + ln 2 sum_m log2(1 + e_m),
+// w = column sums of X (FP64, once), e_m = ex2.approx(-a_m) on the
+// multi-function unit (three instructions per element: |.| accumulate, ex2,
+// product); the log2 is taken once per 16 rows of a running FP32
 // product prod(1 + e_m) (each factor in (1, 2], so the product stays below
 // 2^16).  Zero padding rows give z = 0 exactly and contribute exactly 1 to the
 // log2 sum, removed as (m_pad - m).
@@ -319,9 +321,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
               float prod = 1.0f;
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
-                const float az = fabsf(z[16 * g16 + e]);
+                const float az = fabsf(z[16 * g16 + e]);  // |z| log2 e (the images are scaled)
                 sabs += az;
-                prod = fmaf(prod, ex2_approx(az * -1.4426950408889634f), prod);
+                prod = fmaf(prod, ex2_approx(-az), prod);
               }
               slg += lg2_approx(prod);
             }
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
             bw = fma(bc, tg->xsum[c], bw);
             b2 = fma(bc, bc, b2);
           }
-          const double sp = 0.5 * (bw + sum_abs) + 0.6931471805599453 * sum_lg;
+          const double sp = 0.5 * (bw + 0.6931471805599453 * sum_abs) + 0.6931471805599453 * sum_lg;
           const float lpn = float(bv - sp - b2 / (2.0 * tg->prior_var));
           // eq. (5): the log-target difference in FP32 (exact when the two
           // values are within a factor of two), one FP64 addition

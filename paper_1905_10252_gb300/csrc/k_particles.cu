@@ -64,11 +64,12 @@ __global__ void k_target_setup(TargetDev* tg, int kind, double nu, const double*
   for (int i = 0; i < kMaxD * kMaxD; ++i) tg->Pf[i] = float(tg->P[i]);
 }
 
-// Logistic data: FP32 copies, BF16 hi / lo images and v = X^T y.  Image of
+// Logistic data: FP32 copies, BF16 hi / lo images of X log2(e) (the tensor-core
+// likelihood works in base 2) and v = X^T y.  Image of
 // data tile j (rows 256 j ..): kLgTileBytes bytes, hi then lo, each 256 rows x
 // 32 columns of BF16 in the tensor cores' K-major core-matrix order: element
 // (r, k) at byte (r / 8) * 512 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
-// Rows >= M and columns >= D are zero.  lo = bf16(x - float(hi)).
+// Rows >= M and columns >= D are zero.  lo = bf16(x' - float(hi)), x' = x log2 e.
 // BF16 = the top 16 bits of an FP32, rounded to nearest even (finite inputs).
 __device__ __forceinline__ uint16_t bf16_rn(float f) {
   const uint32_t u = __float_as_uint(f);
@@ -83,8 +84,9 @@ __global__ void k_logistic_copy(TargetDev* tg, const float* __restrict__ X, cons
   const int64_t total = int64_t(m_pad) * kLgK;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
     const int r = int(e / kLgK), k = int(e % kLgK);
-    const float v = (r < m && k < d) ? X[int64_t(r) * d + k] : 0.0f;
-    if (r < m && k < d) Xw[int64_t(r) * d + k] = v;
+    const float xv = (r < m && k < d) ? X[int64_t(r) * d + k] : 0.0f;
+    if (r < m && k < d) Xw[int64_t(r) * d + k] = xv;
+    const float v = xv * 1.4426950408889634f;  // the images hold X log2(e)
     if (k == 0 && r < m) yw[r] = y[r];
     const uint16_t hi = bf16_rn(v);
     const uint16_t lo = bf16_rn(v - bf16_to_f32(hi));
