@@ -20,6 +20,12 @@ a step is one iteration of every sampler (--steps 50 is the workload's K).
 --workload logistic: Bayesian logistic regression, N = 2^18 FP32 particles,
 M = 8192 rows, D = 32 features; the likelihood on the tensor cores (tcgen05,
 BF16 hi / lo split) next to the CUDA-core FP32 likelihood of the same sampler.
+--workload serve: a Poisson stream of sampler jobs (--rate per second, --jobs
+jobs): Gaussian jobs of the batched workload (K = 50) mixed with logistic jobs
+(N = 2^18, M in {1024, 8192}, D = 32, K = 100; --logistic-frac of the stream),
+admitted by free HBM, served with continuous batching; p50 / p99
+time-to-posterior and particle-iterations/s, next to the same stream served one
+sampler per launch.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (rank 0 only).
 Multi-GPU (torchrun): independent replicas, one sampler per GPU, no collective
@@ -53,8 +59,12 @@ def parse():
     p.add_argument("--steps", type=int, default=400)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="iteration", choices=["iteration", "redistribute", "batch", "logistic"])
+    p.add_argument("--workload", default="iteration",
+                   choices=["iteration", "redistribute", "batch", "logistic", "serve"])
     p.add_argument("--m", type=int, default=8192, help="logistic workload: data rows")
+    p.add_argument("--jobs", type=int, default=2000, help="serve workload: jobs in the Poisson stream")
+    p.add_argument("--rate", type=float, default=200.0, help="serve workload: arrivals per second")
+    p.add_argument("--logistic-frac", type=float, default=0.05, help="serve workload: share of logistic jobs")
     p.add_argument("--count", type=int, default=256, help="batch workload: samplers")
     p.add_argument("--n", type=int, default=1 << 24)
     p.add_argument("--d", type=int, default=16)
@@ -663,6 +673,80 @@ def run_logistic(args):
     S.close()
 
 
+def serve_jobs(count: int, rate: float, logistic_frac: float, seed: int = 0):
+    from paper_1905_10252_gb300 import inputs
+    from paper_1905_10252_gb300.serve import Job, poisson_arrivals
+
+    arr = poisson_arrivals(count, rate, seed=seed)
+    g = np.random.default_rng(seed + 1)
+    kinds = g.uniform(size=count) < logistic_frac
+    shapes = inputs.batch_shapes(count, seed=seed + 2)
+    datasets = {m: inputs.logistic_data(m, 32, seed=m)[:2] for m in (1024, 8192)}
+    targets = {}
+    jobs = []
+    for i in range(count):
+        if kinds[i]:
+            m = 1024 if g.uniform() < 0.5 else 8192
+            X, y = datasets[m]
+            jobs.append(Job(jid=i, kind="logistic", n=1 << 18, d=32, k=100, seed=i, arrival=float(arr[i]), X=X, y=y,
+                            step=0.02, init_scale=0.5))
+        else:
+            n, d = shapes[i]
+            if (d, i % 8) not in targets:
+                targets[(d, i % 8)] = inputs.gaussian_target(d, seed=1000 + 8 * d + i % 8)
+            mu, sig = targets[(d, i % 8)]
+            jobs.append(Job(jid=i, kind="gauss", n=n, d=d, k=50, seed=i, arrival=float(arr[i]), mu=mu, sigma=sig))
+    return jobs
+
+
+def run_serve(args):
+    """Continuous-batching server on a Poisson stream of jobs."""
+    import torch
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_1905_10252_gb300 import build as B
+
+    B.build()
+    from paper_1905_10252_gb300.serve import GpuEngine, Scheduler, latency_summary
+
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.6, 64 << 30))
+    out = {}
+    # warm-up: a short stream through both engines (kernels, allocator, graphs)
+    for batched in (True, False):
+        Scheduler(GpuEngine(batched=batched), budget_bytes=budget).run(serve_jobs(40, 400.0, args.logistic_frac, 99))
+    for batched in (True, False):
+        jobs = serve_jobs(args.jobs, args.rate, args.logistic_frac, seed=rank)
+        eng = GpuEngine(batched=batched)
+        sch = Scheduler(eng, budget_bytes=budget, round_iters=5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = sch.run(jobs, t0=t0)
+        wall = time.perf_counter() - t0
+        pits = sum(j.n * j.k for j in done)
+        out["batched" if batched else "one_sampler_per_launch"] = dict(
+            latency_summary(done), wall_s=round(wall, 3), particle_iters_per_s=pits / wall, rounds=sch.rounds,
+            jobs_per_s=len(done) / wall)
+    b = out["batched"]
+    if rank == 0:
+        line = {
+            "metric": "served p50/p99 time-to-posterior; particle-iters/s", "value": b["particle_iters_per_s"],
+            "unit": METRIC, "n_gpus": ws, "steps": args.jobs, "warmup": 40, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 state / f64 weights", "data": "synthetic",
+            "config": {"workload": f"serve Poisson {args.rate:g} jobs/s x {args.jobs}: gauss (batched workload, "
+                                   f"K=50) + {args.logistic_frac:.0%} logistic (N=2^18, M in {{1024,8192}}, D=32, "
+                                   "K=100)", "budget_bytes": budget, "round_iters": 5,
+                       "parallelism": f"replicas x{ws}"},
+            "p50_s": b["p50_s"], "p99_s": b["p99_s"],
+            "serving": out,
+            "speedup_vs_one_sampler_per_launch": b["particle_iters_per_s"] /
+                                                 out["one_sampler_per_launch"]["particle_iters_per_s"],
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -673,6 +757,8 @@ def main():
         run_batch(args)
     elif args.workload == "logistic":
         run_logistic(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_iteration(args)
 

@@ -1,0 +1,257 @@
+"""Serving many sampler jobs on one GPU with continuous batching.
+
+A job is one SMC run (Algorithm 2 for K iterations) of its own target, N and
+D; its answer is the weighted mean f_K of eq. (7).  The server keeps every
+admitted job's particles, weights, log-targets and RNG counter (the iteration
+index t, the Philox key is the job's seed) resident in HBM, and advances all
+resident jobs together in rounds of a few iterations:
+
+  * Gaussian FP32 jobs share one batched launch per stage (``native.Batch``,
+    one CUDA graph of the batched iteration); the batch is rebuilt whenever
+    jobs join or leave, between rounds;
+  * logistic-regression jobs run their own iterations (tensor-core
+    likelihood) on their own streams, concurrently with the batch.
+
+Jobs that arrive while others are on the GPU wait in a queue and are admitted
+as soon as their device memory fits in the budget (first fit in arrival
+order: a small job may pass a large one that does not fit yet, but a job that
+has waited longer than ``max_wait_rounds`` rounds blocks everything behind it
+until it is admitted).  A job's results do not depend on the jobs around it:
+batched and solo iterations are bit-identical (tests/test_gpu_serve.py).
+
+The scheduling policy (``Scheduler``) is plain host logic over an ``Engine``
+interface, so it is tested on the CPU with a fake engine; ``GpuEngine`` is the
+CUDA implementation.  Nothing here computes any part of the sampler.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Job:
+    """One sampler run: kind 'gauss' (mu, sigma) or 'logistic' (X, y)."""
+
+    jid: int
+    kind: str
+    n: int
+    d: int
+    k: int
+    seed: int
+    arrival: float = 0.0           # seconds since the start of the stream
+    mu: np.ndarray | None = None
+    sigma: np.ndarray | None = None
+    X: np.ndarray | None = None
+    y: np.ndarray | None = None
+    prior_var: float = 4.0
+    step: float = 0.5
+    init_scale: float = 2.0
+    # filled in by the scheduler
+    admitted: float = math.nan
+    finished: float = math.nan
+    done_iters: int = 0
+    result: np.ndarray | None = None
+    waited_rounds: int = 0
+
+    @property
+    def m(self) -> int:
+        return 0 if self.X is None else int(self.X.shape[0])
+
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Engine:
+    """What the scheduler needs from a device (see GpuEngine)."""
+
+    def bytes_needed(self, job: Job) -> int:
+        raise NotImplementedError
+
+    def admit(self, job: Job) -> None:
+        raise NotImplementedError
+
+    def step(self, jobs: list[Job], iters: dict[int, int]) -> None:
+        """Advance each job by iters[job.jid] iterations (asynchronously)."""
+        raise NotImplementedError
+
+    def wait(self) -> None:
+        raise NotImplementedError
+
+    def result(self, job: Job) -> np.ndarray:
+        raise NotImplementedError
+
+    def release(self, job: Job) -> None:
+        raise NotImplementedError
+
+
+@dataclass
+class Scheduler:
+    engine: Engine
+    budget_bytes: int
+    round_iters: int = 5
+    max_wait_rounds: int = 50
+    clock: callable = time.perf_counter
+    queue: list[Job] = field(default_factory=list)
+    active: list[Job] = field(default_factory=list)
+    finished: list[Job] = field(default_factory=list)
+    used_bytes: int = 0
+    rounds: int = 0
+
+    def _admit(self, now: float) -> None:
+        blocked = False
+        still = []
+        for job in self.queue:
+            need = self.engine.bytes_needed(job)
+            if need > self.budget_bytes:
+                raise ValueError(f"job {job.jid} needs {need} bytes, more than the whole budget")
+            if not blocked and self.used_bytes + need <= self.budget_bytes:
+                self.engine.admit(job)
+                job.admitted = now
+                self.used_bytes += need
+                self.active.append(job)
+            else:
+                job.waited_rounds += 1
+                still.append(job)
+                if job.waited_rounds > self.max_wait_rounds:
+                    blocked = True  # no overtaking a job that has waited too long
+        self.queue = still
+
+    def run(self, jobs: list[Job], t0: float | None = None) -> list[Job]:
+        """Serves jobs (sorted by arrival); arrivals are released by the
+        clock, so jobs arriving during a round wait for its end."""
+        pending = sorted(jobs, key=lambda j: j.arrival)
+        start = self.clock() if t0 is None else t0
+        i = 0
+        while i < len(pending) or self.queue or self.active:
+            now = self.clock() - start
+            while i < len(pending) and pending[i].arrival <= now:
+                self.queue.append(pending[i])
+                i += 1
+            self._admit(now)
+            if not self.active:
+                if i < len(pending):  # idle until the next arrival
+                    wait = pending[i].arrival - (self.clock() - start)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.01))
+                continue
+            iters = {j.jid: min(self.round_iters, j.k - j.done_iters) for j in self.active}
+            self.engine.step(self.active, iters)
+            self.engine.wait()
+            self.rounds += 1
+            now = self.clock() - start
+            still = []
+            for j in self.active:
+                j.done_iters += iters[j.jid]
+                if j.done_iters >= j.k:
+                    j.result = self.engine.result(j)
+                    j.finished = self.clock() - start
+                    self.engine.release(j)
+                    self.used_bytes -= self.engine.bytes_needed(j)
+                    self.finished.append(j)
+                else:
+                    still.append(j)
+            self.active = still
+        return self.finished
+
+
+def latency_summary(jobs: list[Job]) -> dict:
+    lat = np.array([j.latency() for j in jobs])
+    return {"jobs": len(jobs), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "max_s": float(lat.max())}
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 0) -> np.ndarray:
+    """Arrival times of a Poisson stream (exponential gaps, mean 1 / rate)."""
+    g = np.random.default_rng(np.random.SeedSequence([int(seed), 0x5E7]))
+    return np.cumsum(g.exponential(1.0 / rate, size=count))
+
+
+class GpuEngine(Engine):
+    """Jobs as libsmc samplers on one GPU (see the module docstring)."""
+
+    def __init__(self, batched: bool = True, device: str = "cuda"):
+        import torch
+
+        from . import native
+
+        self.torch, self.native = torch, native
+        self.batched = batched
+        self.device = device
+        self.samplers: dict[int, object] = {}
+        self.means: dict[int, object] = {}
+        self.batch = None
+        self.batch_ids: tuple = ()
+        self.stream = torch.cuda.Stream(device=device)
+
+    def bytes_needed(self, job: Job) -> int:
+        # particle state (two buffers), log w, two log pi buffers, workspace
+        # (its logistic data included) and the batch's per-member arguments
+        es = 4
+        ws = 2 * job.n * job.d * es + job.n * 8 + 2 * job.n * es
+        ws += 32 * job.n + 12 * job.n + 64 * job.d * job.d + (1 << 16)
+        if job.kind == "logistic":
+            m_pad = (job.m + 255) // 256 * 256
+            ws += job.m * job.d * 4 + job.m * 4 + m_pad * 128
+        return int(ws)
+
+    def admit(self, job: Job) -> None:
+        nat = self.native
+        if job.kind == "gauss":
+            s = nat.Sampler(job.n, job.d, dtype=self.torch.float32, seed=job.seed, mu=job.mu, sigma=job.sigma,
+                            step=job.step, init_scale=job.init_scale)
+        else:
+            s = nat.Sampler(job.n, job.d, dtype=self.torch.float32, seed=job.seed, target="logistic", X=job.X,
+                            y=job.y, prior_var=job.prior_var, step=job.step, init_scale=job.init_scale)
+        self.samplers[job.jid] = s
+        self.means[job.jid] = self.torch.empty(job.d, dtype=self.torch.float64, device=self.device)
+
+    def _batch_for(self, jobs: list[Job]):
+        ids = tuple(sorted(j.jid for j in jobs))
+        if ids != self.batch_ids:
+            if self.batch is not None:
+                self.batch.sync()
+                self.batch.close()
+            self.batch = self.native.Batch([self.samplers[i] for i in ids], stream=self.stream) if ids else None
+            self.batch_ids = ids
+        return self.batch
+
+    def step(self, jobs: list[Job], iters: dict[int, int]) -> None:
+        nat = self.native
+        L = nat.lib()
+        gauss = [j for j in jobs if j.kind == "gauss"]
+        others = [j for j in jobs if j.kind != "gauss"]
+        if self.batched and gauss:
+            # the batch advances every member by the same count: jobs needing
+            # fewer iterations this round (their last) step alone
+            k = min(iters[j.jid] for j in gauss)
+            full = [j for j in gauss if iters[j.jid] == k]
+            rest = [j for j in gauss if iters[j.jid] != k]
+            b = self._batch_for(full)
+            b.step_raw(k, means=[self.means[j.jid] for j in full])
+            others = rest + others
+        elif gauss:
+            others = gauss + others
+        for j in others:
+            s = self.samplers[j.jid]
+            s.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+            nat._check(L.smc_step(s.h, int(iters[j.jid]), nat._ptr(self.means[j.jid]), None, None, None), s.h)
+
+    def wait(self) -> None:
+        if self.batch is not None:
+            self.batch.sync()
+        self.torch.cuda.synchronize()
+
+    def result(self, job: Job) -> np.ndarray:
+        return self.means[job.jid].cpu().numpy().copy()
+
+    def release(self, job: Job) -> None:
+        if self.batch is not None and job.jid in self.batch_ids:
+            self.batch.sync()
+            self.batch.close()
+            self.batch, self.batch_ids = None, ()
+        self.samplers.pop(job.jid).close()
+        self.means.pop(job.jid)
