@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--jobs", type=int, default=2000, help="serve workload: jobs in the Poisson stream")
     p.add_argument("--rate", type=float, default=200.0, help="serve workload: arrivals per second")
     p.add_argument("--logistic-frac", type=float, default=0.05, help="serve workload: share of logistic jobs")
+    p.add_argument("--sat-jobs", type=int, default=300, help="serve workload: jobs of the saturated run")
     p.add_argument("--count", type=int, default=256, help="batch workload: samplers")
     p.add_argument("--n", type=int, default=1 << 24)
     p.add_argument("--d", type=int, default=16)
@@ -728,6 +729,21 @@ def run_serve(args):
         out["batched" if batched else "one_sampler_per_launch"] = dict(
             latency_summary(done), wall_s=round(wall, 3), particle_iters_per_s=pits / wall, rounds=sch.rounds,
             jobs_per_s=len(done) / wall)
+    # saturation: the same mix with every job waiting at t = 0 (throughput)
+    sat = {}
+    for batched in (True, False):
+        jobs = serve_jobs(args.sat_jobs, args.rate, args.logistic_frac, seed=rank + 7)
+        for j in jobs:
+            j.arrival = 0.0
+        sch = Scheduler(GpuEngine(batched=batched), budget_bytes=budget, round_iters=5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = sch.run(jobs, t0=t0)
+        wall = time.perf_counter() - t0
+        sat["batched" if batched else "one_sampler_per_launch"] = {
+            "jobs": len(done), "wall_s": round(wall, 3), "particle_iters_per_s": sum(j.n * j.k for j in done) / wall,
+            "rounds": sch.rounds}
+    out["saturated"] = sat
     b = out["batched"]
     if rank == 0:
         line = {
@@ -741,8 +757,8 @@ def run_serve(args):
                        "parallelism": f"replicas x{ws}"},
             "p50_s": b["p50_s"], "p99_s": b["p99_s"],
             "serving": out,
-            "speedup_vs_one_sampler_per_launch": b["particle_iters_per_s"] /
-                                                 out["one_sampler_per_launch"]["particle_iters_per_s"],
+            "saturated_speedup_vs_one_sampler_per_launch": sat["batched"]["particle_iters_per_s"] /
+                                                           sat["one_sampler_per_launch"]["particle_iters_per_s"],
         }
         print(json.dumps(line), flush=True)
 

@@ -231,7 +231,8 @@ class GpuEngine(Engine):
             full = [j for j in gauss if iters[j.jid] == k]
             rest = [j for j in gauss if iters[j.jid] != k]
             b = self._batch_for(full)
-            b.step_raw(k, means=[self.means[j.jid] for j in full])
+            # outputs in the batch's member order
+            b.step_raw(k, means=[self.means[i] for i in self.batch_ids])
             others = rest + others
         elif gauss:
             others = gauss + others

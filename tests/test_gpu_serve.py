@@ -25,7 +25,9 @@ def nat():
 def make_jobs():
     from paper_1905_10252_gb300.serve import Job, poisson_arrivals
 
-    arr = poisson_arrivals(18, rate=400.0, seed=5)
+    # arrival order differs from job-id order, so the scheduler's list of
+    # active jobs and the batch's member order (sorted ids) differ
+    arr = poisson_arrivals(18, rate=400.0, seed=5)[::-1].copy()
     jobs = []
     shapes = inputs.batch_shapes(14, seed=9, n_min=1 << 8, n_max=1 << 14)
     for i, (n, d) in enumerate(shapes):
