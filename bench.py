@@ -729,21 +729,25 @@ def run_serve(args):
         out["batched" if batched else "one_sampler_per_launch"] = dict(
             latency_summary(done), wall_s=round(wall, 3), particle_iters_per_s=pits / wall, rounds=sch.rounds,
             jobs_per_s=len(done) / wall)
-    # saturation: the same mix with every job waiting at t = 0 (throughput)
-    sat = {}
-    for batched in (True, False):
-        jobs = serve_jobs(args.sat_jobs, args.rate, args.logistic_frac, seed=rank + 7)
-        for j in jobs:
-            j.arrival = 0.0
-        sch = Scheduler(GpuEngine(batched=batched), budget_bytes=budget, round_iters=5)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        done = sch.run(jobs, t0=t0)
-        wall = time.perf_counter() - t0
-        sat["batched" if batched else "one_sampler_per_launch"] = {
-            "jobs": len(done), "wall_s": round(wall, 3), "particle_iters_per_s": sum(j.n * j.k for j in done) / wall,
-            "rounds": sch.rounds}
-    out["saturated"] = sat
+    # saturation: every job waiting at t = 0 (throughput), the mix and the
+    # Gaussian jobs alone
+    for name, frac in (("saturated", args.logistic_frac), ("saturated_gauss_only", 0.0)):
+        sat = {}
+        for batched in (True, False):
+            jobs = serve_jobs(args.sat_jobs, args.rate, frac, seed=rank + 7)
+            for j in jobs:
+                j.arrival = 0.0
+            sch = Scheduler(GpuEngine(batched=batched), budget_bytes=budget, round_iters=5)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            done = sch.run(jobs, t0=t0)
+            wall = time.perf_counter() - t0
+            sat["batched" if batched else "one_sampler_per_launch"] = {
+                "jobs": len(done), "wall_s": round(wall, 3),
+                "particle_iters_per_s": sum(j.n * j.k for j in done) / wall, "rounds": sch.rounds}
+        sat["speedup"] = sat["batched"]["particle_iters_per_s"] / sat["one_sampler_per_launch"]["particle_iters_per_s"]
+        out[name] = sat
+    sat = out["saturated"]
     b = out["batched"]
     if rank == 0:
         line = {

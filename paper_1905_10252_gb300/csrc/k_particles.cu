@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kPThreads) k_init(ParticleArgs a) {
         xr[c] = c < a.d ? __dmul_rn(a.init_scale, z[c]) : 0.0;
         if (c < a.d) q = __fma_rn(xr[c], xr[c], q);
       }
-      const double lpi = eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu, a.tg);
+      const double lpi = (a.flags & PA_INIT_SKIP_LOGPI) ? 0.0 : eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu, a.tg);
       const double lq0 = __ddiv_rn(__dmul_rn(-0.5, q), __dmul_rn(a.init_scale, a.init_scale));
       lw = __dsub_rn(lpi, lq0);
       lp[i] = lpi;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kPThreads) k_init(ParticleArgs a) {
         xr[c] = c < a.d ? s * z[c] : 0.0f;
         if (c < a.d) q = fmaf(xr[c], xr[c], q);
       }
-      const float lpi = eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu, a.tg);
+      const float lpi = (a.flags & PA_INIT_SKIP_LOGPI) ? 0.0f : eval_logpi<T, DMAX>(xr, a.d, a.kind, ts, nu, a.tg);
       const float lq0 = (-0.5f * q) / (s * s);
       lw = double(lpi) - double(lq0);
       lp[i] = lpi;

@@ -340,9 +340,12 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
     else
       e = launch_target_setup(h->tg, cfg->target, cfg->nu, cfg->mu_dev, cfg->sigma_dev, h->d, h->st, h->stream);
   }
-  if (e == cudaSuccess) e = launch_particles(OP_INIT, particle_args(h), h->grid_p, h->stream);
-  // the tensor-core likelihood replaces the CUDA-core log pi of x_0, so that
-  // every later difference of eq. (5) compares values of one method
+  // with the tensor-core likelihood, init leaves log pi(x_0) = 0 and the
+  // likelihood pass adds it (log w_0 = log pi - log q0 either way), so every
+  // later difference of eq. (5) compares values of one method
+  ParticleArgs ia = particle_args(h);
+  if (h->lg_tc) ia.flags |= PA_INIT_SKIP_LOGPI;
+  if (e == cudaSuccess) e = launch_particles(OP_INIT, ia, h->grid_p, h->stream);
   if (e == cudaSuccess && h->lg_tc) e = launch_logistic_tc(particle_args(h), h->grid_lg, h->stream);
   if (e == cudaSuccess) e = launch_stats(h, 1, h->lg_tc ? h->grid_lg : h->grid_p);
   if (e == cudaSuccess && cfg->target == SMC_GAUSS && h->dtype == SMC_F32) {

@@ -56,12 +56,15 @@ struct GaussParamsF32 {
 // path (the FP32 path holds up to 32 coordinates in one lane's registers).
 inline int lanes_per_particle(int, int) { return 1; }
 
+// ParticleArgs.flags
+enum { PA_INIT_SKIP_LOGPI = 1 };  // init writes log pi = 0 (a later likelihood pass adds it)
+
 struct ParticleArgs {
   int64_t n;
   int32_t d;
   int32_t dtype;
   int32_t kind;
-  int32_t pad;
+  int32_t flags;
   uint64_t seed;
   double step;
   double init_scale;

@@ -74,11 +74,14 @@ class Engine:
     def admit(self, job: Job) -> None:
         raise NotImplementedError
 
-    def step(self, jobs: list[Job], iters: dict[int, int]) -> None:
-        """Advance each job by iters[job.jid] iterations (asynchronously)."""
+    def step(self, jobs: list[Job], iters: dict[int, int]) -> list[int]:
+        """Launches iters[job.jid] iterations of jobs (asynchronously) and
+        returns the ids it launched (the others stay idle for now)."""
         raise NotImplementedError
 
-    def wait(self) -> None:
+    def completed(self) -> list[int]:
+        """Ids of jobs whose launched iterations have all completed since the
+        last call; blocks until at least one has, when any work is pending."""
         raise NotImplementedError
 
     def result(self, job: Job) -> np.ndarray:
@@ -122,9 +125,11 @@ class Scheduler:
 
     def run(self, jobs: list[Job], t0: float | None = None) -> list[Job]:
         """Serves jobs (sorted by arrival); arrivals are released by the
-        clock, so jobs arriving during a round wait for its end."""
+        clock.  A job gets new iterations as soon as its previous ones have
+        completed, so short and long jobs progress independently."""
         pending = sorted(jobs, key=lambda j: j.arrival)
         start = self.clock() if t0 is None else t0
+        busy: dict[int, int] = {}
         i = 0
         while i < len(pending) or self.queue or self.active:
             now = self.clock() - start
@@ -132,20 +137,23 @@ class Scheduler:
                 self.queue.append(pending[i])
                 i += 1
             self._admit(now)
-            if not self.active:
+            idle = [j for j in self.active if j.jid not in busy]
+            if idle:
+                iters = {j.jid: min(self.round_iters, j.k - j.done_iters) for j in idle}
+                launched = self.engine.step(idle, iters)
+                busy.update({jid: iters[jid] for jid in launched})
+                self.rounds += 1 if launched else 0
+            if not busy:
                 if i < len(pending):  # idle until the next arrival
                     wait = pending[i].arrival - (self.clock() - start)
                     if wait > 0:
-                        time.sleep(min(wait, 0.01))
+                        time.sleep(min(wait, 0.005))
                 continue
-            iters = {j.jid: min(self.round_iters, j.k - j.done_iters) for j in self.active}
-            self.engine.step(self.active, iters)
-            self.engine.wait()
-            self.rounds += 1
-            now = self.clock() - start
+            done_ids = set(self.engine.completed())
             still = []
             for j in self.active:
-                j.done_iters += iters[j.jid]
+                if j.jid in done_ids:
+                    j.done_iters += busy.pop(j.jid)
                 if j.done_iters >= j.k:
                     j.result = self.engine.result(j)
                     j.finished = self.clock() - start
@@ -186,6 +194,8 @@ class GpuEngine(Engine):
         self.batch = None
         self.batch_ids: tuple = ()
         self.stream = torch.cuda.Stream(device=device)
+        self.pending: list = []  # (event, job ids, is the batch) of launched work
+        self.batch_busy = False
 
     def bytes_needed(self, job: Job) -> int:
         # particle state (two buffers), log w, two log pi buffers, workspace
@@ -219,32 +229,57 @@ class GpuEngine(Engine):
             self.batch_ids = ids
         return self.batch
 
-    def step(self, jobs: list[Job], iters: dict[int, int]) -> None:
+    def step(self, jobs: list[Job], iters: dict[int, int]) -> list[int]:
         nat = self.native
         L = nat.lib()
+        torch = self.torch
         gauss = [j for j in jobs if j.kind == "gauss"]
         others = [j for j in jobs if j.kind != "gauss"]
+        launched = []
         if self.batched and gauss:
-            # the batch advances every member by the same count: jobs needing
-            # fewer iterations this round (their last) step alone
-            k = min(iters[j.jid] for j in gauss)
-            full = [j for j in gauss if iters[j.jid] == k]
-            rest = [j for j in gauss if iters[j.jid] != k]
-            b = self._batch_for(full)
-            # outputs in the batch's member order
-            b.step_raw(k, means=[self.means[i] for i in self.batch_ids])
-            others = rest + others
+            if self.batch_busy:
+                # the batch is still running its round: idle Gaussian jobs join
+                # the next one (no batch is split while it runs)
+                gauss = []
+            else:
+                # the batch advances every member by the same count: jobs
+                # needing fewer iterations this round (their last) step alone
+                k = min(iters[j.jid] for j in gauss)
+                full = [j for j in gauss if iters[j.jid] == k]
+                rest = [j for j in gauss if iters[j.jid] != k]
+                b = self._batch_for(full)
+                # outputs in the batch's member order
+                b.step_raw(k, means=[self.means[i] for i in self.batch_ids])
+                ev = torch.cuda.Event()
+                ev.record(self.stream)
+                self.pending.append((ev, [j.jid for j in full], True))
+                self.batch_busy = True
+                launched += [j.jid for j in full]
+                others = rest + others
         elif gauss:
             others = gauss + others
         for j in others:
             s = self.samplers[j.jid]
-            s.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+            s.stream.wait_stream(torch.cuda.current_stream(self.device))
             nat._check(L.smc_step(s.h, int(iters[j.jid]), nat._ptr(self.means[j.jid]), None, None, None), s.h)
+            ev = torch.cuda.Event()
+            ev.record(s.stream)
+            self.pending.append((ev, [j.jid], False))
+            launched.append(j.jid)
+        return launched
 
-    def wait(self) -> None:
-        if self.batch is not None:
-            self.batch.sync()
-        self.torch.cuda.synchronize()
+    def completed(self) -> list[int]:
+        if not self.pending:
+            return []
+        while True:
+            done = [p for p in self.pending if p[0].query()]
+            if done:
+                break
+            self.pending[0][0].synchronize()  # the oldest launch
+        self.pending = [p for p in self.pending if p not in done]
+        if any(p[2] for p in done):
+            self.batch_busy = False
+        return [jid for _, ids, _ in done for jid in ids]
 
     def result(self, job: Job) -> np.ndarray:
         return self.means[job.jid].cpu().numpy().copy()

@@ -37,9 +37,12 @@ class FakeEngine(Engine):
         for j in jobs:
             assert 1 <= iters[j.jid] <= j.k - j.done_iters
             self.iters[j.jid] += iters[j.jid]
+        self.pending = [j.jid for j in jobs]
+        return list(self.pending)
 
-    def wait(self):
-        pass
+    def completed(self):
+        out, self.pending = self.pending, []
+        return out
 
     def result(self, job):
         return np.array([float(self.iters[job.jid])])
