@@ -51,10 +51,11 @@ constexpr int kTcEpiCols = 256 / (kTcEpiWarps / 4);         // accumulator colum
 constexpr uint32_t kTcCols = 512;                           // TMEM columns
 constexpr size_t kTcAImg = size_t(kTcPT) * kLgK * 2;        // one BF16 A image (8 KB)
 constexpr size_t kTcHalf = kLgTileBytes / 2;                // one BF16 data image (16 KB)
-// data ring + two (hi, lo) A image pairs + partial sums of the column groups
-// 1..3 + barriers / TMEM slot / flags / warp maxima (1 KB) + alignment slack
-constexpr size_t kTcSmem =
-    kTcStages * kLgTileBytes + 4 * kTcAImg + 2 * (kTcEpiWarps / 4 - 1) * kTcPT * sizeof(double) + 1024 + 1024;
+// data ring + two (hi, lo) A image pairs + two partial sums per particle of
+// the column groups 1..3 + the ring of per-particle constant terms +
+// barriers / TMEM slot / flags / warp maxima (1 KB) + alignment slack
+constexpr size_t kTcSmem = kTcStages * kLgTileBytes + 4 * kTcAImg +
+                           (2 * (kTcEpiWarps / 4 - 1) + 4) * kTcPT * sizeof(double) + 1024 + 1024;
 constexpr long long kWaitCycles = 1ll << 31;                // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -163,15 +164,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
   uint8_t* xs = sm;                                         // kTcStages x (hi | lo) data tiles
   uint8_t* aimg = xs + kTcStages * kLgTileBytes;            // [2] x (hi, lo) particle tile images
   constexpr int kGroups = kTcEpiWarps / 4;                  // column groups per lane quarter
-  double* s_abs = reinterpret_cast<double*>(aimg + 4 * kTcAImg);  // [kGroups - 1][128]
-  double* s_lg = s_abs + (kGroups - 1) * kTcPT;
-  uint64_t* full = reinterpret_cast<uint64_t*>(s_lg + (kGroups - 1) * kTcPT);
+  // [kGroups - 1][128][2]: |z| and log2 sums of the column groups 1..3
+  double* s_part = reinterpret_cast<double*>(aimg + 4 * kTcAImg);
+  // [4][128]: per particle b.v - b.w / 2 - |b|^2 / (2 prior_var), a ring of
+  // 4 particle tiles written by the stager warps
+  double* s_pre = s_part + (kGroups - 1) * kTcPT * 2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(s_pre + 4 * kTcPT);
   uint64_t* empty = full + kTcStages;
   uint64_t* tfull = empty + kTcStages;
   uint64_t* tempty = tfull + 2;
   uint64_t* afull = tempty + 2;
   uint64_t* aempty = afull + 2;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + 2);
+  uint64_t* prefull = aempty + 2;  // [4]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(prefull + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   long long* wmax = reinterpret_cast<long long*>(tslot + 4);  // [kTcWarps]
   int* wnan = reinterpret_cast<int*>(wmax + kTcWarps);
@@ -197,6 +202,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
       mbar_init(&afull[b], kTcStageThreads);
       mbar_init(&aempty[b], 1);
     }
+    for (int r = 0; r < 4; ++r) mbar_init(&prefull[r], kTcStageThreads);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -296,22 +302,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
       mbar_arrive(&afull[ab]);
+      // the FP64 part of log pi for each particle (two per thread), kept off
+      // the epilogue warps: b.v - (b.w) / 2 - |b|^2 / (2 prior_var).  Slot
+      // v % 4 is free: writing tile v requires the MMAs of tile v - 2 to have
+      // completed, hence the epilogue to have finished tile v - 4.
+      if (!*abort_flag) {
+        double* pre = s_pre + size_t(v & 3) * kTcPT;
+        for (int r = t; r < kTcPT; r += kTcStageThreads) {
+          const int64_t i = pt * kTcPT + r;
+          double bv = 0.0, bw = 0.0, b2 = 0.0;
+          if (i < n)
+            for (int c = 0; c < d; ++c) {
+              const double bc = double(x[i * d + c]);
+              bv = fma(bc, tg->v[c], bv);
+              bw = fma(bc, tg->xsum[c], bw);
+              b2 = fma(bc, bc, b2);
+            }
+          pre[r] = bv - 0.5 * bw - b2 / (2.0 * tg->prior_var);
+        }
+      }
+      mbar_arrive(&prefull[v & 3]);
     }
   } else {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3, h = (warp - 4) >> 2;
     const int row = 32 * q + lane;
-    uint32_t u = 0;
+    uint32_t u = 0, v = 0;
     const double log2_pad = double(tg->m_pad - tg->m);
-    for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x) {
+    for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x, ++v) {
+      const int64_t i = pt * kTcPT + row;
       double acc_abs = 0.0, acc_lg = 0.0;
+      float fabs4 = 0.0f, flg4 = 0.0f;  // FP32 sums over up to 8 data tiles
       for (int j = 0; j < nx; ++j, ++u) {
         const int b = int(u & 1);
         // warp-uniform outcome: tcgen05.ld below is a warp-collective
         const bool ready = __all_sync(0xffffffffu, mbar_wait(&tfull[b], (u >> 1) & 1, abort_flag));
         if (ready) {
           tc_fence_after();
-          float sabs = 0.0f, slg = 0.0f;
 #pragma unroll 1
           for (int c = 0; c < kTcEpiCols / 32; ++c) {
             float z[32];
@@ -322,42 +349,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
                 const float az = fabsf(z[16 * g16 + e]);  // |z| log2 e (the images are scaled)
-                sabs += az;
+                fabs4 += az;
                 prod = fmaf(prod, ex2_approx(-az), prod);
               }
-              slg += lg2_approx(prod);
+              flg4 += lg2_approx(prod);
             }
           }
-          acc_abs += double(sabs);
-          acc_lg += double(slg);
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
+        if ((j & 7) == 7 || j == nx - 1) {
+          acc_abs += double(fabs4);
+          acc_lg += double(flg4);
+          fabs4 = flg4 = 0.0f;
+        }
       }
       if (h > 0) {
-        s_abs[(h - 1) * kTcPT + row] = acc_abs;
-        s_lg[(h - 1) * kTcPT + row] = acc_lg;
+        double* sp = s_part + ((h - 1) * kTcPT + row) * 2;
+        sp[0] = acc_abs;
+        sp[1] = acc_lg;
       }
       named_sync(2, kTcEpiThreads);
       if (h == 0) {
-        const int64_t i = pt * kTcPT + row;
-        if (i < n && !*abort_flag) {
+        // the constant term of this tile (written by the stager warps)
+        const bool have_pre = __all_sync(0xffffffffu, mbar_wait(&prefull[v & 3], (v >> 2) & 1, abort_flag));
+        if (i < n && have_pre && !*abort_flag) {
           double sum_abs = acc_abs, sum_lg = acc_lg - log2_pad;
 #pragma unroll
           for (int g2 = 0; g2 < kGroups - 1; ++g2) {
-            sum_abs += s_abs[g2 * kTcPT + row];
-            sum_lg += s_lg[g2 * kTcPT + row];
+            const double* sp = s_part + (g2 * kTcPT + row) * 2;
+            sum_abs += sp[0];
+            sum_lg += sp[1];
           }
-          double bv = 0.0, bw = 0.0, b2 = 0.0;
-          for (int c = 0; c < d; ++c) {
-            const double bc = double(x[i * d + c]);
-            bv = fma(bc, tg->v[c], bv);
-            bw = fma(bc, tg->xsum[c], bw);
-            b2 = fma(bc, bc, b2);
-          }
-          const double sp = 0.5 * (bw + 0.6931471805599453 * sum_abs) + 0.6931471805599453 * sum_lg;
-          const float lpn = float(bv - sp - b2 / (2.0 * tg->prior_var));
+          const double ln2 = 0.6931471805599453;
+          const float lpn = float(s_pre[(v & 3) * kTcPT + row] - 0.5 * ln2 * sum_abs - ln2 * sum_lg);
           // eq. (5): the log-target difference in FP32 (exact when the two
           // values are within a factor of two), one FP64 addition
           const double lw = a.logw[i] + double(lpn - lp[i]);
