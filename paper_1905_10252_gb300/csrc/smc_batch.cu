@@ -22,8 +22,6 @@ constexpr size_t kAl = 256;
 constexpr int kMoveBudget[SMC_BATCH_MOVE_VARIANTS] = {2, 4, 8, 16, 0};  // blocks per SM; 0: one per particle
 constexpr int kMaxMoveBlocks = 4096;  // per member: the size of its partials buffer
 constexpr int kDefaultMove = 2, kDefaultCopy = 1;
-// one map serves the quantise, scan and copy launches
-static_assert(kQTile == kRTile, "quantise blocks and copy tiles must cover the same rows");
 
 size_t up(size_t v) { return (v + kAl - 1) / kAl * kAl; }
 int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -33,7 +31,8 @@ thread_local std::string g_batch_err = "ok";
 // Host-side block maps of a member list (independent of device addresses).
 struct Plan {
   int count = 0;
-  std::vector<int4> qmap;                               // quantise / scan / copy tiles
+  std::vector<int4> qmap;                               // quantise / scan blocks
+  std::vector<int4> rmap;                               // copy tiles
   std::vector<int4> mmap[SMC_BATCH_MOVE_VARIANTS];      // move / reweight blocks
   std::vector<int32_t> nb[SMC_BATCH_MOVE_VARIANTS];     // move blocks per member
 };
@@ -59,6 +58,8 @@ Plan make_plan(smc_sampler* const* m, int count, int sms) {
   for (int s : order) {
     const int nq = int(div_up(m[s]->n, kQTile));
     for (int j = 0; j < nq; ++j) p.qmap.push_back(make_int4(s, j, nq, 0));
+    const int nr = int(div_up(m[s]->n, kRTile));
+    for (int j = 0; j < nr; ++j) p.rmap.push_back(make_int4(s, j, nr, 0));
   }
   for (int v = 0; v < SMC_BATCH_MOVE_VARIANTS; ++v) {
     p.nb[v].assign(count, 1);
@@ -77,7 +78,7 @@ Plan make_plan(smc_sampler* const* m, int count, int sms) {
 
 // Byte offsets in the batch workspace.
 struct BatchLayout {
-  size_t pa, pa_dry, qa, ra, ra_dry, gp, outs, errs, nb, qmap, mmap[SMC_BATCH_MOVE_VARIANTS], dry_st, total;
+  size_t pa, pa_dry, qa, ra, ra_dry, gp, outs, errs, nb, qmap, rmap, mmap[SMC_BATCH_MOVE_VARIANTS], dry_st, total;
 };
 
 BatchLayout batch_layout(const Plan& p) {
@@ -99,6 +100,7 @@ BatchLayout batch_layout(const Plan& p) {
   L.errs = take(c * sizeof(int32_t));
   L.nb = take(SMC_BATCH_MOVE_VARIANTS * c * sizeof(int32_t));
   L.qmap = take(p.qmap.size() * sizeof(int4));
+  L.rmap = take(p.rmap.size() * sizeof(int4));
   for (int v = 0; v < SMC_BATCH_MOVE_VARIANTS; ++v) L.mmap[v] = take(p.mmap[v].size() * sizeof(int4));
   L.dry_st = take(devstate_bytes());
   L.total = o;
@@ -182,7 +184,9 @@ cudaError_t launch_batch_iteration(const smc_batch* b) {
   if (e == cudaSuccess) e = launch_quant_reduce_batch(qa, qmap, nq, s);
   if (e == cudaSuccess) e = launch_quant_finalize_batch(qa, c, s);
   if (e == cudaSuccess) e = launch_quant_scan_batch(qa, qmap, nq, s);
-  if (e == cudaSuccess) e = launch_redistribute_batch(b->at<RedistArgs>(b->L.ra), qmap, nq, b->copy_v, s);
+  if (e == cudaSuccess)
+    e = launch_redistribute_batch(b->at<RedistArgs>(b->L.ra), b->at<int4>(b->L.rmap), int(b->plan.rmap.size()),
+                                  b->copy_v, s);
   if (e == cudaSuccess) e = launch_commit_batch(pa, c, s);
   return e;
 }
@@ -297,6 +301,8 @@ int smc_batch_create(smc_batch** out, smc_sampler* const* members, int32_t count
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->ws + L.nb, nb.data(), nb.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->ws + L.qmap, b->plan.qmap.data(), b->plan.qmap.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->ws + L.rmap, b->plan.rmap.data(), b->plan.rmap.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
   for (int v = 0; v < SMC_BATCH_MOVE_VARIANTS && e == cudaSuccess; ++v)
     e = cudaMemcpyAsync(b->ws + L.mmap[v], b->plan.mmap[v].data(), b->plan.mmap[v].size() * sizeof(int4),
                         cudaMemcpyHostToDevice, st);
@@ -367,7 +373,8 @@ int smc_batch_step_profile(smc_batch* b, void* const* events_host, int32_t n_eve
   BATCH_TRY(b, rec(4));
   BATCH_TRY(b, launch_quant_scan_batch(qa, qmap, nq, s));
   BATCH_TRY(b, rec(5));
-  BATCH_TRY(b, launch_redistribute_batch(b->at<RedistArgs>(b->L.ra), qmap, nq, b->copy_v, s));
+  BATCH_TRY(b, launch_redistribute_batch(b->at<RedistArgs>(b->L.ra), b->at<int4>(b->L.rmap),
+                                         int(b->plan.rmap.size()), b->copy_v, s));
   BATCH_TRY(b, rec(6));
   BATCH_TRY(b, launch_commit_batch(pa, c, s));
   BATCH_TRY(b, rec(7));
@@ -440,14 +447,14 @@ int smc_batch_tune(smc_batch* b, int32_t reps, int32_t* choice_host) {
   // needs it clear
   if (e == cudaSuccess) e = cudaMemsetAsync(b->at<DevState>(b->L.dry_st), 0, devstate_bytes(), s);
   const RedistArgs* rdry = b->at<RedistArgs>(b->L.ra_dry);
-  const int4* qmap = b->at<int4>(b->L.qmap);
-  const int nq = int(b->plan.qmap.size());
+  const int4* rmap = b->at<int4>(b->L.rmap);
+  const int nr = int(b->plan.rmap.size());
   for (int v = 0; v < SMC_BATCH_COPY_VARIANTS && e == cudaSuccess; ++v) {
     std::vector<float> t;
     for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
-      e = launch_identity_runs_batch(rdry, qmap, nq, s);
+      e = launch_identity_runs_batch(rdry, rmap, nr, s);
       if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-      if (e == cudaSuccess) e = launch_redistribute_batch(rdry, qmap, nq, v, s);
+      if (e == cudaSuccess) e = launch_redistribute_batch(rdry, rmap, nr, v, s);
       if (e == cudaSuccess) e = cudaEventRecord(e1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.0f;

@@ -27,7 +27,7 @@ constexpr int kMaxD = 32;
 constexpr int kQTile = 4096;          // elements per block of the quantise / scan passes
 constexpr int kQThreads = 256;        // 16 consecutive elements per thread
 constexpr int kQItems = kQTile / kQThreads;
-constexpr int kRTile = 4096;          // output rows per block of the redistribute copy
+constexpr int kRTile = 2048;          // output rows per block of the redistribute copy
 constexpr int kRThreads = 256;
 constexpr int kPThreads = 256;        // particle kernels (init / move / reweight)
 constexpr int kFinThreads = 1024;     // single-block finalisers
