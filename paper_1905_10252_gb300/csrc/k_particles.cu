@@ -841,45 +841,49 @@ __global__ void k_step_setup(DevState* st, smc_iter_stats* trace, double* mean_o
 
 // ---------------------------------------------------------------- launchers
 template <typename T, int DMAX>
-static cudaError_t launch_particles_t(int op, const ParticleArgs& a, int grid, cudaStream_t s) {
+static cudaError_t launch_particles_t(int op, const ParticleArgs& a, int grid, int threads, cudaStream_t s) {
   switch (op) {
-    case OP_INIT: k_init<T, DMAX><<<grid, kPThreads, 0, s>>>(a); break;
-    case OP_MOVE: k_move_reweight<T, DMAX, true, false><<<grid, kPThreads, 0, s>>>(a); break;
-    case OP_REWEIGHT: k_move_reweight<T, DMAX, false, true><<<grid, kPThreads, 0, s>>>(a); break;
-    case OP_MOVE_REWEIGHT: k_move_reweight<T, DMAX, true, true><<<grid, kPThreads, 0, s>>>(a); break;
+    case OP_INIT: k_init<T, DMAX><<<grid, threads, 0, s>>>(a); break;
+    case OP_MOVE: k_move_reweight<T, DMAX, true, false><<<grid, threads, 0, s>>>(a); break;
+    case OP_REWEIGHT: k_move_reweight<T, DMAX, false, true><<<grid, threads, 0, s>>>(a); break;
+    case OP_MOVE_REWEIGHT: k_move_reweight<T, DMAX, true, true><<<grid, threads, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t launch_particles_d(int op, const ParticleArgs& a, int grid, cudaStream_t s) {
-  if (a.d <= 1) return launch_particles_t<T, 1>(op, a, grid, s);
-  if (a.d <= 2) return launch_particles_t<T, 2>(op, a, grid, s);
-  if (a.d <= 4) return launch_particles_t<T, 4>(op, a, grid, s);
-  if (a.d <= 8) return launch_particles_t<T, 8>(op, a, grid, s);
-  if (a.d <= 16) return launch_particles_t<T, 16>(op, a, grid, s);
-  return launch_particles_t<T, 32>(op, a, grid, s);
+static cudaError_t launch_particles_d(int op, const ParticleArgs& a, int grid, int threads, cudaStream_t s) {
+  if (a.d <= 1) return launch_particles_t<T, 1>(op, a, grid, threads, s);
+  if (a.d <= 2) return launch_particles_t<T, 2>(op, a, grid, threads, s);
+  if (a.d <= 4) return launch_particles_t<T, 4>(op, a, grid, threads, s);
+  if (a.d <= 8) return launch_particles_t<T, 8>(op, a, grid, threads, s);
+  if (a.d <= 16) return launch_particles_t<T, 16>(op, a, grid, threads, s);
+  return launch_particles_t<T, 32>(op, a, grid, threads, s);
 }
 
 template <int DPL>
-static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, cudaStream_t s, const GaussParamsF32& gp) {
+static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, int threads, cudaStream_t s,
+                                const GaussParamsF32& gp) {
   switch (op) {
-    case OP_MOVE: k_move_reweight_lanes<DPL, true, false><<<grid, kPThreads, 0, s>>>(a, gp); break;
-    case OP_REWEIGHT: k_move_reweight_lanes<DPL, false, true><<<grid, kPThreads, 0, s>>>(a, gp); break;
-    case OP_MOVE_REWEIGHT: k_move_reweight_lanes<DPL, true, true><<<grid, kPThreads, 0, s>>>(a, gp); break;
+    case OP_MOVE: k_move_reweight_lanes<DPL, true, false><<<grid, threads, 0, s>>>(a, gp); break;
+    case OP_REWEIGHT: k_move_reweight_lanes<DPL, false, true><<<grid, threads, 0, s>>>(a, gp); break;
+    case OP_MOVE_REWEIGHT: k_move_reweight_lanes<DPL, true, true><<<grid, threads, 0, s>>>(a, gp); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s, const GaussParamsF32* gp) {
+cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, int threads, cudaStream_t s,
+                             const GaussParamsF32* gp) {
+  if (threads < 32 || threads > kPThreads || threads % 32) return cudaErrorInvalidValue;
   if (a.dtype == SMC_F32 && op != OP_INIT && a.kind == SMC_GAUSS && gp) {
-    if (a.d <= 8) return launch_lanes<8>(op, a, grid, s, *gp);
-    if (a.d <= 16) return launch_lanes<16>(op, a, grid, s, *gp);
-    return launch_lanes<32>(op, a, grid, s, *gp);
+    if (a.d <= 8) return launch_lanes<8>(op, a, grid, threads, s, *gp);
+    if (a.d <= 16) return launch_lanes<16>(op, a, grid, threads, s, *gp);
+    return launch_lanes<32>(op, a, grid, threads, s, *gp);
   }
-  return a.dtype == SMC_F64 ? launch_particles_d<double>(op, a, grid, s) : launch_particles_d<float>(op, a, grid, s);
+  return a.dtype == SMC_F64 ? launch_particles_d<double>(op, a, grid, threads, s)
+                            : launch_particles_d<float>(op, a, grid, threads, s);
 }
 
 cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double* mu, const double* sigma, int d,

@@ -348,10 +348,19 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
       tpart[lt] = part;
     }
     __syncthreads();
-    if (int(threadIdx.x) < a.d) {
-      double t = 0.0;
-      for (int k = threadIdx.x; k < stride; k += a.d) t += tpart[k];
-      sxsum[threadIdx.x] = t;
+    // column c's stride / d partials (tpart[c + d j]) summed by warps
+    // c, c + nw, ...: lane l adds j = l, l + 32, ... in order, then a fixed
+    // shuffle tree -- deterministic, and a short FP64 dependency chain
+    {
+      const int per_col = stride / a.d;
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+      for (int c = wid; c < a.d; c += nwarps) {
+        double t = 0.0;
+        for (int j = lane; j < per_col; j += 32) t += tpart[c + a.d * j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sxsum[c] = t;
+      }
     }
     __syncthreads();
   }

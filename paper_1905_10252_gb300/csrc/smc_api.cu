@@ -202,13 +202,13 @@ cudaError_t launch_stats(smc_sampler* h, int set_lse_prev, int nb) {
 // the number of max records written.
 cudaError_t launch_move_reweight(smc_sampler* h, const ParticleArgs& a, int* nb) {
   if (h->lg_tc) {
-    cudaError_t e = launch_particles(OP_MOVE, a, h->grid_p, h->stream);
+    cudaError_t e = launch_particles(OP_MOVE, a, h->grid_p, h->threads_p, h->stream);
     if (e == cudaSuccess) e = launch_logistic_tc(a, h->grid_lg, h->stream);
     *nb = h->grid_lg;
     return e;
   }
   *nb = h->grid_p;
-  return launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, h->stream, gauss_params(h));
+  return launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, h->threads_p, h->stream, gauss_params(h));
 }
 
 // One iteration of Algorithm 2 (lines 3-10), all on h->stream.
@@ -319,9 +319,16 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   h->rs = reinterpret_cast<int32_t*>(h->ws + L.rs);
   h->wbuf = reinterpret_cast<uint64_t*>(h->ws + L.wbuf);
   h->tile_src = reinterpret_cast<int32_t*>(h->ws + L.tile_src);
-  h->grid_p = int(std::min<int64_t>(div_up(h->n * lanes_per_particle(h->dtype, h->d), kPThreads),
-                                    int64_t(sm_count()) * 8));
-  if (h->grid_p > kMaxPartBlocks) h->grid_p = kMaxPartBlocks;
+  // particle kernels: 256-thread blocks, at most 8 per SM (grid-stride);
+  // samplers of fewer than 256 particles per SM use one-warp blocks so that
+  // their work (FP64 in particular) spreads over the SMs
+  {
+    const int64_t units = h->n * lanes_per_particle(h->dtype, h->d);
+    const int64_t sms = sm_count();
+    h->threads_p = units < int64_t(kPThreads) * sms ? 32 : kPThreads;
+    h->grid_p = int(std::min<int64_t>(div_up(units, h->threads_p), sms * 8));
+    if (h->grid_p > kMaxPartBlocks) h->grid_p = kMaxPartBlocks;
+  }
   h->lg_tc = cfg->target == SMC_LOGISTIC && cfg->dtype == SMC_F32 && !(cfg->flags & SMC_FLAG_LOGISTIC_CUDA_CORES);
   h->grid_lg = logistic_tc_grid(h->n, sm_count());
   h->g_iter[0] = h->g_iter[1] = nullptr;
@@ -345,7 +352,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   // later difference of eq. (5) compares values of one method
   ParticleArgs ia = particle_args(h);
   if (h->lg_tc) ia.flags |= PA_INIT_SKIP_LOGPI;
-  if (e == cudaSuccess) e = launch_particles(OP_INIT, ia, h->grid_p, h->stream);
+  if (e == cudaSuccess) e = launch_particles(OP_INIT, ia, h->grid_p, h->threads_p, h->stream);
   if (e == cudaSuccess && h->lg_tc) e = launch_logistic_tc(particle_args(h), h->grid_lg, h->stream);
   if (e == cudaSuccess) e = launch_stats(h, 1, h->lg_tc ? h->grid_lg : h->grid_p);
   if (e == cudaSuccess && cfg->target == SMC_GAUSS && h->dtype == SMC_F32) {
@@ -373,7 +380,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
 int smc_move(smc_sampler* h) {
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   SMC_TRY(h, launch_begin(h->st, h->stream));
-  SMC_TRY(h, launch_particles(OP_MOVE, particle_args(h), h->grid_p, h->stream, gauss_params(h)));
+  SMC_TRY(h, launch_particles(OP_MOVE, particle_args(h), h->grid_p, h->threads_p, h->stream, gauss_params(h)));
   return SMC_OK;
 }
 
@@ -383,7 +390,7 @@ int smc_reweight(smc_sampler* h) {
     SMC_TRY(h, launch_logistic_tc(particle_args(h), h->grid_lg, h->stream));
     SMC_TRY(h, launch_stats(h, 0, h->grid_lg));
   } else {
-    SMC_TRY(h, launch_particles(OP_REWEIGHT, particle_args(h), h->grid_p, h->stream, gauss_params(h)));
+    SMC_TRY(h, launch_particles(OP_REWEIGHT, particle_args(h), h->grid_p, h->threads_p, h->stream, gauss_params(h)));
     SMC_TRY(h, launch_stats(h, 0, h->grid_p));
   }
   return SMC_OK;

@@ -39,6 +39,7 @@ struct smc_sampler {
   uint64_t* wbuf;
   int32_t* tile_src;
   int grid_p;
+  int threads_p;  // block size of the particle kernels
   // FP32 logistic samplers: likelihood on the tensor cores (its own grid)
   bool lg_tc;
   int grid_lg;

@@ -137,7 +137,9 @@ size_t devstate_bytes();
 // Message returned by smc_last_error(NULL) (smc_api.cu).
 void set_global_error(const char* msg);
 
-cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, cudaStream_t s,
+// threads: block size, a multiple of 32 up to kPThreads (small samplers use
+// small blocks so that their particles spread over more SMs)
+cudaError_t launch_particles(int op, const ParticleArgs& a, int grid, int threads, cudaStream_t s,
                              const GaussParamsF32* gp = nullptr);
 cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double* mu, const double* sigma, int d,
                                 DevState* st, cudaStream_t s);
