@@ -34,6 +34,8 @@
 // role drains its remaining loop iterations without waiting (so the named
 // barriers still match), waits (bounded) for its own copies in flight, frees
 // TMEM and returns.
+#include <atomic>
+
 #include "smc_internal.cuh"
 #include "smc_kernels.h"
 
@@ -434,12 +436,16 @@ int logistic_tc_grid(int64_t n, int sms) {
 }
 
 cudaError_t launch_logistic_tc(const ParticleArgs& a, int grid, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_logistic_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
+  // the dynamic shared-memory limit is a per-device attribute of the kernel
+  static std::atomic<bool> configured[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!configured[dev].load()) {
+    e = cudaFuncSetAttribute(k_logistic_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured[dev].store(true);
   }
   k_logistic_tc<<<grid, kTcThreads, kTcSmem, s>>>(a);
   return cudaGetLastError();
