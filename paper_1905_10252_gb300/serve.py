@@ -10,7 +10,9 @@ resident jobs together in rounds of a few iterations:
     one CUDA graph of the batched iteration); the batch is rebuilt whenever
     jobs join or leave, between rounds;
   * logistic-regression jobs run their own iterations (tensor-core
-    likelihood) on their own streams, concurrently with the batch.
+    likelihood) on their own streams, concurrently with the batch;
+  * Gaussian work runs on high-priority streams, so that its short kernels
+    are scheduled between the long logistic ones (shortest job first).
 
 Jobs that arrive while others are on the GPU wait in a queue and are admitted
 as soon as their device memory fits in the budget (first fit in arrival
@@ -193,7 +195,12 @@ class GpuEngine(Engine):
         self.means: dict[int, object] = {}
         self.batch = None
         self.batch_ids: tuple = ()
-        self.stream = torch.cuda.Stream(device=device)
+        # short jobs first: Gaussian work (the batch, or each Gaussian job in
+        # one-per-launch mode) runs on high-priority streams, so that its small
+        # kernels are scheduled between the long logistic likelihood kernels
+        lo_prio, hi_prio = torch.cuda.Stream.priority_range()
+        self.hi_prio = hi_prio
+        self.stream = torch.cuda.Stream(device=device, priority=hi_prio)
         self.pending: list = []  # (event, job ids, is the batch) of launched work
         self.batch_busy = False
 
@@ -212,7 +219,8 @@ class GpuEngine(Engine):
         nat = self.native
         if job.kind == "gauss":
             s = nat.Sampler(job.n, job.d, dtype=self.torch.float32, seed=job.seed, mu=job.mu, sigma=job.sigma,
-                            step=job.step, init_scale=job.init_scale)
+                            step=job.step, init_scale=job.init_scale,
+                            stream=self.torch.cuda.Stream(device=self.device, priority=self.hi_prio))
         else:
             s = nat.Sampler(job.n, job.d, dtype=self.torch.float32, seed=job.seed, target="logistic", X=job.X,
                             y=job.y, prior_var=job.prior_var, step=job.step, init_scale=job.init_scale)
@@ -271,11 +279,18 @@ class GpuEngine(Engine):
     def completed(self) -> list[int]:
         if not self.pending:
             return []
+        # poll every launch: blocking on one long logistic run would leave
+        # the (short) batch idle until it ends; the batch's own event is the
+        # one worth waiting on directly
         while True:
             done = [p for p in self.pending if p[0].query()]
             if done:
                 break
-            self.pending[0][0].synchronize()  # the oldest launch
+            batch = [p for p in self.pending if p[2]]
+            if batch:
+                batch[0][0].synchronize()
+            else:
+                time.sleep(50e-6)
         self.pending = [p for p in self.pending if p not in done]
         if any(p[2] for p in done):
             self.batch_busy = False
