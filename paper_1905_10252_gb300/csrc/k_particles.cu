@@ -407,9 +407,9 @@ __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
 // while the current one is computed.
 __device__ __forceinline__ void bm_pair_fast(uint32_t h0, uint32_t h1, float& z0, float& z1) {
   const float a = float(h0 >> 8) * 0x1p-24f;  // u1 = 1 - a
-  float p = fmaf(a, 1.0f / 7.0f, 1.0f / 6.0f);
-  p = fmaf(a, p, 0.2f);
-  p = fmaf(a, p, 0.25f);
+  // -ln(1 - a) = a (1 + a/2 + a^2/3 + a^3/4 + a^4/5 + ...): for a < 1/16 the
+  // truncation error is below 1.7e-7 relative (about 1.4 FP32 ulp)
+  float p = fmaf(a, 0.2f, 0.25f);
   p = fmaf(a, p, 1.0f / 3.0f);
   p = fmaf(a, p, 0.5f);
   p = fmaf(a, p, 1.0f);
