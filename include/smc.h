@@ -63,6 +63,11 @@ typedef enum { SMC_RESAMPLE_ESS = 0, SMC_RESAMPLE_ALWAYS = 1, SMC_RESAMPLE_NEVER
  * of the default tensor-core contraction (BF16 hi/lo split, FP32 accumulation);
  * FP64 samplers always use the CUDA cores in FP64. */
 #define SMC_FLAG_LOGISTIC_CUDA_CORES 1
+/* Test hook for the failure path: the tensor-core likelihood never issues its
+ * data copies, so every wait on them runs out (after about one second);
+ * the kernel then drains, frees its tensor memory and returns, and the next
+ * smc_sync reports SMC_ETIMEOUT.  The GPU context stays usable. */
+#define SMC_FLAG_TEST_STALL_LIKELIHOOD 2
 
 typedef struct {
   int64_t n;              /* N particles */

@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
       const uint8_t* img = reinterpret_cast<const uint8_t*>(tg->ximg);
       for (int64_t pt = blockIdx.x; pt < npt; pt += gridDim.x) {
         for (int j = 0; j < nx; ++j, ++g) {
+          if (a.flags & PA_STALL_COPIES) continue;  // test hook: the consumers' waits run out
           const int s = int(g % kTcStages);
           const uint32_t r = g / kTcStages;
           if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) continue;

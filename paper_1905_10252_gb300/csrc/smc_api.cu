@@ -130,6 +130,7 @@ ParticleArgs particle_args(const smc_sampler* h) {
   a.part = h->part;
   a.tg = h->tg;
   a.st = h->st;
+  if (h->cfg.flags & SMC_FLAG_TEST_STALL_LIKELIHOOD) a.flags |= PA_STALL_COPIES;
   return a;
 }
 

@@ -57,7 +57,10 @@ struct GaussParamsF32 {
 inline int lanes_per_particle(int, int) { return 1; }
 
 // ParticleArgs.flags
-enum { PA_INIT_SKIP_LOGPI = 1 };  // init writes log pi = 0 (a later likelihood pass adds it)
+enum {
+  PA_INIT_SKIP_LOGPI = 1,  // init writes log pi = 0 (a later likelihood pass adds it)
+  PA_STALL_COPIES = 2,     // test hook: the tensor-core likelihood issues no data copies
+};
 
 struct ParticleArgs {
   int64_t n;

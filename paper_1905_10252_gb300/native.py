@@ -19,6 +19,7 @@ SMC_F32, SMC_F64 = 1, 2
 SMC_GAUSS, SMC_LOGISTIC, SMC_STUDENT_T = 1, 2, 3
 RESAMPLE_ESS, RESAMPLE_ALWAYS, RESAMPLE_NEVER = 0, 1, 2
 FLAG_LOGISTIC_CUDA_CORES = 1  # SMC_FLAG_LOGISTIC_CUDA_CORES
+FLAG_TEST_STALL_LIKELIHOOD = 2  # SMC_FLAG_TEST_STALL_LIKELIHOOD
 
 EXPORTED = [
     "smc_workspace_bytes", "smc_init", "smc_move", "smc_reweight", "smc_estimate", "smc_resample",

@@ -85,3 +85,21 @@ def test_tc_run_is_sane(nat):
     for rec in tr:
         assert np.isfinite(rec["lse"]) and 0 < rec["ess"] <= N
     assert np.all(np.isfinite(host(r["mean"])))
+
+
+def test_tc_timeout_is_reported_and_the_context_survives(nat):
+    """Failure path without a GPU fault: with the test hook the likelihood's
+    data copies are never issued, its bounded waits run out (~1 s), it
+    drains and frees its tensor memory, and smc_sync reports SMC_ETIMEOUT.
+    A normal sampler then runs on the same context."""
+    X, y, _ = inputs.logistic_data(300, 8, seed=2)
+    S = nat.Sampler(1000, 8, dtype=torch.float32, seed=1, target="logistic", X=X, y=y,
+                    flags=nat.FLAG_TEST_STALL_LIKELIHOOD)
+    with pytest.raises(nat.SmcError) as e:
+        S.sync()
+    assert e.value.code == nat.SMC_ETIMEOUT
+    S.close()
+    T = nat.Sampler(1000, 8, dtype=torch.float32, seed=1, target="logistic", X=X, y=y)
+    r = T.step(2)
+    T.sync()
+    assert np.all(np.isfinite(host(r["mean"])))
