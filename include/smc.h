@@ -178,6 +178,32 @@ int smc_current(smc_sampler* h, int32_t* which_host);
 /* Frees the handle (host memory only). */
 int smc_destroy(smc_sampler* h);
 
+/* ---------------------------------------------------------------------------
+ * Checkpoint / resume.  The state of Algorithm 2 between two iterations is the
+ * particles x, their log pi, the log-weights (eq. 5), the iteration index t,
+ * LSE_{t-1} and the recycling sums of eq. (6).  Random numbers are
+ * counter-based (Philox keyed by seed, t and particle index), so a sampler
+ * restored from a checkpoint taken after iteration t continues bit for bit as
+ * the original would have.
+ *
+ * smc_checkpoint_bytes: size of a checkpoint of h (host bytes) in *bytes.
+ *   Layout: a 56-byte header (magic "SMCCKPT1", version, D, N, dtype, target,
+ *   seed, state-block bytes, row bytes), the device state block, x (N x D, row-major, the sampler's dtype),
+ *   log pi (N, the sampler's dtype), log w (N doubles).
+ * smc_checkpoint_save: waits for the work queued on the sampler's stream,
+ *   then copies the state into host_dst (caller-owned, `bytes` long, any host
+ *   memory).  Returns SMC_EINVAL if bytes is too small, the pending device
+ *   error (nothing saved) if one is recorded, SMC_ECUDA on a failed copy.
+ * smc_checkpoint_load: restores a checkpoint into h, which must have been
+ *   created with the same N, D, dtype, target and seed (SMC_EINVAL otherwise,
+ *   and h is untouched).  The particles land in x_dev / logpi_dev (buffer 0);
+ *   outputs requested from earlier calls are not written.  Synchronous: the
+ *   host buffer may be freed when it returns.  The target's parameters are
+ *   not part of the checkpoint: h's own are used. */
+int smc_checkpoint_bytes(const smc_sampler* h, size_t* bytes);
+int smc_checkpoint_save(smc_sampler* h, void* host_dst, size_t bytes);
+int smc_checkpoint_load(smc_sampler* h, const void* host_src, size_t bytes);
+
 /* Message of the last error on this handle (or of the last handle-less call
  * when h is NULL); never NULL. */
 const char* smc_last_error(const smc_sampler* h);

@@ -691,10 +691,23 @@ __global__ void __launch_bounds__(kFinBatchThreads) k_max_finalize_batch(const P
 }
 
 // ---------------------------------------------------------------- covariance
-// cov_ab = sum_i w~_i (x_ia - mean_a)(x_ib - mean_b), w~_i = e^{log w_i - m} / s;
-// a block stages 256 rows, each thread owns (a, b) pairs; atomics into cov.
+// cov_ab = sum_i w~_i (x_ia - mean_a)(x_ib - mean_b), w~_i = e^{log w_i - m} / s.
+// A block stages 128 rows at a time; each thread owns up to three (a <= b)
+// pairs and writes its block's sums to covpart[block][pair]; k_cov_finalize
+// adds the blocks in index order (no atomics: the result does not depend on
+// the order in which blocks run).
+__device__ __forceinline__ void cov_pair(int p, int d, int& pa, int& pb) {
+  int r = 0;
+  while (p >= d - r) {
+    p -= d - r;
+    ++r;
+  }
+  pa = r;
+  pb = r + p;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kPThreads) k_cov(ParticleArgs a, double* cov) {
+__global__ void __launch_bounds__(kPThreads) k_cov(ParticleArgs a, double* cov, double* __restrict__ covpart) {
   constexpr int kChunk = 128;
   if (!cov) cov = a.st->cov_out;
   if (!cov || a.st->err) return;
@@ -708,17 +721,9 @@ __global__ void __launch_bounds__(kPThreads) k_cov(ParticleArgs a, double* cov) 
   double acc[3] = {0.0, 0.0, 0.0};
   int pa[3], pb[3];
   for (int k = 0; k < 3; ++k) {
-    int p = threadIdx.x + k * blockDim.x;
+    const int p = threadIdx.x + k * blockDim.x;
     pa[k] = pb[k] = -1;
-    if (p < npairs) {
-      int r = 0;
-      while (p >= d - r) {
-        p -= d - r;
-        ++r;
-      }
-      pa[k] = r;
-      pb[k] = r + p;
-    }
+    if (p < npairs) cov_pair(p, d, pa[k], pb[k]);
   }
   for (int64_t base = int64_t(blockIdx.x) * kChunk; base < a.n; base += int64_t(gridDim.x) * kChunk) {
     if (threadIdx.x < kChunk) {
@@ -741,11 +746,24 @@ __global__ void __launch_bounds__(kPThreads) k_cov(ParticleArgs a, double* cov) 
     }
     __syncthreads();
   }
-  for (int k = 0; k < 3; ++k) {
-    if (pa[k] < 0) continue;
-    atomicAdd(&cov[pa[k] * d + pb[k]], acc[k]);
-    if (pa[k] != pb[k]) atomicAdd(&cov[pb[k] * d + pa[k]], acc[k]);
-  }
+  for (int k = 0; k < 3; ++k)
+    if (pa[k] >= 0) covpart[size_t(blockIdx.x) * npairs + threadIdx.x + k * blockDim.x] = acc[k];
+}
+
+// Sums the per-block covariance partials in block order; fills both triangles.
+__global__ void k_cov_finalize(const DevState* st, double* cov, const double* __restrict__ covpart, int nblocks,
+                               int d) {
+  if (!cov) cov = st->cov_out;
+  if (!cov || st->err) return;
+  const int npairs = d * (d + 1) / 2;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  double v = 0.0;
+  for (int b = 0; b < nblocks; ++b) v += covpart[size_t(b) * npairs + p];
+  int pa, pb;
+  cov_pair(p, d, pa, pb);
+  cov[pa * d + pb] = v;
+  cov[pb * d + pa] = v;
 }
 
 // ---------------------------------------------------------------- bookkeeping
@@ -814,13 +832,6 @@ __global__ void k_take_errors_batch(const ParticleArgs* __restrict__ pa, int32_t
   if (s >= count) return;
   errs[s] = pa[s].st->err;
   pa[s].st->err = 0;
-}
-
-// Zeroes the covariance output named by the running smc_step.
-__global__ void k_zero_cov(DevState* st, int d) {
-  double* c = st->cov_out;
-  if (!c) return;
-  for (int i = threadIdx.x; i < d * d; i += blockDim.x) c[i] = 0.0;
 }
 
 // Copies f_t out (piecewise API).
@@ -906,16 +917,15 @@ cudaError_t launch_max_finalize(const double* part, int nb, DevState* st, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_cov(const ParticleArgs& a, double* cov, int grid, cudaStream_t s) {
+cudaError_t launch_cov(const ParticleArgs& a, double* cov, double* covpart, int grid, cudaStream_t s) {
   if (a.dtype == SMC_F64)
-    k_cov<double><<<grid, kPThreads, 0, s>>>(a, cov);
+    k_cov<double><<<grid, kPThreads, 0, s>>>(a, cov, covpart);
   else
-    k_cov<float><<<grid, kPThreads, 0, s>>>(a, cov);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_zero_cov(DevState* st, int d, cudaStream_t s) {
-  k_zero_cov<<<1, 256, 0, s>>>(st, d);
+    k_cov<float><<<grid, kPThreads, 0, s>>>(a, cov, covpart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int npairs = a.d * (a.d + 1) / 2;
+  k_cov_finalize<<<(npairs + 127) / 128, 128, 0, s>>>(a.st, cov, covpart, grid, a.d);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@
 #include <string>
 
 #include "smc_host.h"
+#include "smc_trace.h"
 
 using namespace smc;
 
@@ -63,6 +64,10 @@ Layout layout_for(int64_t n, int d, int m = 0) {
   p = align_up(p + size_t(m) * sizeof(float));
   L.lg_img = p;
   p = align_up(p + m_pad / kLgRows * kLgTileBytes);
+  // per-block covariance partials
+  L.cov_blocks = int(std::min<int64_t>(kCovMaxBlocks, div_up(n, 128)));
+  L.covpart = p;
+  p = align_up(p + size_t(L.cov_blocks) * size_t(d * (d + 1) / 2) * sizeof(double));
   L.total = p;
   return L;
 }
@@ -222,8 +227,8 @@ cudaError_t launch_iteration(smc_sampler* h, bool with_cov) {
   const QuantArgs q = quant_args(h, 0, nullptr);
   if (e == cudaSuccess) e = launch_quant_reduce(q, h->stream);
   if (e == cudaSuccess) e = launch_quant_finalize(q, 0, h->stream);
-  if (e == cudaSuccess && with_cov) e = launch_zero_cov(h->st, h->d, h->stream);
-  if (e == cudaSuccess && with_cov) e = launch_cov(a, nullptr, h->grid_p, h->stream);
+  if (e == cudaSuccess && with_cov)
+    e = launch_cov(a, nullptr, reinterpret_cast<double*>(h->ws + h->L.covpart), h->L.cov_blocks, h->stream);
   if (e == cudaSuccess) e = launch_quant_scan(q, h->stream);
   if (e == cudaSuccess) e = launch_redistribute(redist_args(h, 0), h->stream);
   if (e == cudaSuccess) e = launch_commit(h->st, h->d, 0, 1, h->stream);
@@ -280,6 +285,7 @@ int smc_workspace_bytes(const smc_config* cfg, size_t* bytes) {
 int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_dev, double* logw_dev,
              void* logpi_dev, void* logpi_alt_dev, void* workspace_dev, size_t workspace_bytes,
              smc_stream_t stream) {
+  SMC_RANGE("smc_init");
   if (!out) return fail(nullptr, SMC_EINVAL, "null out");
   *out = nullptr;
   int rc = check_config(cfg);
@@ -379,6 +385,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
 }
 
 int smc_move(smc_sampler* h) {
+  SMC_RANGE("smc_move");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   SMC_TRY(h, launch_begin(h->st, h->stream));
   SMC_TRY(h, launch_particles(OP_MOVE, particle_args(h), h->grid_p, h->threads_p, h->stream, gauss_params(h)));
@@ -386,6 +393,7 @@ int smc_move(smc_sampler* h) {
 }
 
 int smc_reweight(smc_sampler* h) {
+  SMC_RANGE("smc_reweight");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   if (h->lg_tc) {
     SMC_TRY(h, launch_logistic_tc(particle_args(h), h->grid_lg, h->stream));
@@ -398,16 +406,17 @@ int smc_reweight(smc_sampler* h) {
 }
 
 int smc_estimate(smc_sampler* h, double* mean_dev, double* cov_dev) {
+  SMC_RANGE("smc_estimate");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   if (mean_dev) SMC_TRY(h, launch_copy_mean(h->st, mean_dev, h->d, h->stream));
-  if (cov_dev) {
-    SMC_TRY(h, cudaMemsetAsync(cov_dev, 0, sizeof(double) * h->d * h->d, h->stream));
-    SMC_TRY(h, launch_cov(particle_args(h), cov_dev, h->grid_p, h->stream));
-  }
+  if (cov_dev)
+    SMC_TRY(h, launch_cov(particle_args(h), cov_dev, reinterpret_cast<double*>(h->ws + h->L.covpart),
+                          h->L.cov_blocks, h->stream));
   return SMC_OK;
 }
 
 int smc_resample(smc_sampler* h, int32_t* ncopies_dev, int32_t* did_resample_dev) {
+  SMC_RANGE("smc_resample");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   if (ncopies_dev) SMC_TRY(h, launch_quant_scan(quant_args(h, 1, ncopies_dev), h->stream));
   if (did_resample_dev)
@@ -417,6 +426,7 @@ int smc_resample(smc_sampler* h, int32_t* ncopies_dev, int32_t* did_resample_dev
 }
 
 int smc_redistribute(smc_sampler* h, const int32_t* ncopies_dev) {
+  SMC_RANGE("smc_redistribute");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   if (!ncopies_dev) return fail(h, SMC_EINVAL, "null ncopies");
   NcScanArgs s{};
@@ -439,6 +449,7 @@ int smc_redistribute(smc_sampler* h, const int32_t* ncopies_dev) {
 
 int smc_step(smc_sampler* h, int32_t k, double* mean_dev, double* cov_dev, smc_iter_stats* trace_dev,
              double* fhat_dev) {
+  SMC_RANGE("smc_step");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   if (k < 0) return fail(h, SMC_EINVAL, "k must be >= 0");
   if (k == 0) return SMC_OK;
@@ -458,6 +469,7 @@ int smc_step(smc_sampler* h, int32_t k, double* mean_dev, double* cov_dev, smc_i
 }
 
 int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host, int32_t n_events) {
+  SMC_RANGE("smc_step_profile");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   if (n_events != 0 && n_events != 8) return fail(h, SMC_EINVAL, "n_events must be 0 or 8");
   if (n_events && !events_host) return fail(h, SMC_EINVAL, "null events");
@@ -470,25 +482,47 @@ int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host,
   const QuantArgs q = quant_args(h, 0, nullptr);
   int nb = 0;
   SMC_TRY(h, rec(0));
-  SMC_TRY(h, launch_begin(h->st, s));
-  SMC_TRY(h, launch_move_reweight(h, a, &nb));
+  {
+    SMC_RANGE("move+reweight");
+    SMC_TRY(h, launch_begin(h->st, s));
+    SMC_TRY(h, launch_move_reweight(h, a, &nb));
+  }
   SMC_TRY(h, rec(1));
-  SMC_TRY(h, launch_max_finalize(h->part, nb, h->st, s));
+  {
+    SMC_RANGE("max finalise");
+    SMC_TRY(h, launch_max_finalize(h->part, nb, h->st, s));
+  }
   SMC_TRY(h, rec(2));
-  SMC_TRY(h, launch_quant_reduce(q, s));
+  {
+    SMC_RANGE("quantise reduce");
+    SMC_TRY(h, launch_quant_reduce(q, s));
+  }
   SMC_TRY(h, rec(3));
-  SMC_TRY(h, launch_quant_finalize(q, 0, s));
+  {
+    SMC_RANGE("quantise finalise");
+    SMC_TRY(h, launch_quant_finalize(q, 0, s));
+  }
   SMC_TRY(h, rec(4));
-  SMC_TRY(h, launch_quant_scan(q, s));
+  {
+    SMC_RANGE("systematic scan");
+    SMC_TRY(h, launch_quant_scan(q, s));
+  }
   SMC_TRY(h, rec(5));
-  SMC_TRY(h, launch_redistribute(redist_args(h, 0), s));
+  {
+    SMC_RANGE("redistribute");
+    SMC_TRY(h, launch_redistribute(redist_args(h, 0), s));
+  }
   SMC_TRY(h, rec(6));
-  SMC_TRY(h, launch_commit(h->st, h->d, 0, 1, s));
+  {
+    SMC_RANGE("commit");
+    SMC_TRY(h, launch_commit(h->st, h->d, 0, 1, s));
+  }
   SMC_TRY(h, rec(7));
   return SMC_OK;
 }
 
 int smc_sync(smc_sampler* h) {
+  SMC_RANGE("smc_sync");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   SMC_TRY(h, cudaStreamSynchronize(h->stream));
   int32_t err = 0;
@@ -564,6 +598,7 @@ int smc_redistribute_ws_bytes(int64_t n, size_t* bytes) {
 
 int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
                          void* out_dev, void* ws_dev, smc_stream_t stream) {
+  SMC_RANGE("smc_redistribute_raw");
   if (n < 1 || n > 2147483647LL) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
   if (row_bytes < 4 || row_bytes % 4) return fail(nullptr, SMC_EINVAL, "row_bytes must be a positive multiple of 4");
   if (!ncopies_dev || !in_dev || !out_dev || !ws_dev) return fail(nullptr, SMC_EINVAL, "null pointer");
@@ -609,6 +644,7 @@ int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_de
 
 int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t t, int32_t mode,
                      int32_t* ncopies_dev, smc_iter_stats* stats_dev, void* ws_dev, smc_stream_t stream) {
+  SMC_RANGE("smc_resample_raw");
   if (n < 1 || n > 2147483647LL) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
   if (!logw_dev || !ncopies_dev || !ws_dev) return fail(nullptr, SMC_EINVAL, "null pointer");
   if (mode < 0 || mode > 2) return fail(nullptr, SMC_EINVAL, "bad mode");

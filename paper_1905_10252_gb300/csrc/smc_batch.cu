@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "smc_host.h"
+#include "smc_trace.h"
 
 using namespace smc;
 
@@ -234,6 +235,7 @@ int smc_batch_ws_bytes(smc_sampler* const* members, int32_t count, size_t* bytes
 
 int smc_batch_create(smc_batch** out, smc_sampler* const* members, int32_t count, void* ws_dev, size_t ws_bytes,
                      smc_stream_t stream) {
+  SMC_RANGE("smc_batch_create");
   if (!out) return bfail(nullptr, SMC_EINVAL, "null out");
   *out = nullptr;
   const int rc = check_members(members, count);
@@ -318,6 +320,7 @@ int smc_batch_create(smc_batch** out, smc_sampler* const* members, int32_t count
 
 int smc_batch_step(smc_batch* b, int32_t k, double* const* mean_dev, smc_iter_stats* const* trace_dev,
                    double* const* fhat_dev) {
+  SMC_RANGE("smc_batch_step");
   if (!b) return bfail(nullptr, SMC_EINVAL, "null handle");
   if (k < 0) return bfail(b, SMC_EINVAL, "k must be >= 0");
   if (k == 0) return SMC_OK;
@@ -344,6 +347,7 @@ int smc_batch_step(smc_batch* b, int32_t k, double* const* mean_dev, smc_iter_st
 }
 
 int smc_batch_step_profile(smc_batch* b, void* const* events_host, int32_t n_events) {
+  SMC_RANGE("smc_batch_step_profile");
   if (!b) return bfail(nullptr, SMC_EINVAL, "null handle");
   if (n_events != 0 && n_events != 8) return bfail(b, SMC_EINVAL, "n_events must be 0 or 8");
   if (n_events && !events_host) return bfail(b, SMC_EINVAL, "null events");
@@ -392,6 +396,7 @@ int smc_batch_set_variant(smc_batch* b, int32_t move_variant, int32_t copy_varia
 }
 
 int smc_batch_tune(smc_batch* b, int32_t reps, int32_t* choice_host) {
+  SMC_RANGE("smc_batch_tune");
   if (!b) return bfail(nullptr, SMC_EINVAL, "null handle");
   if (reps < 1) return bfail(b, SMC_EINVAL, "reps must be >= 1");
   const int c = b->count;
@@ -479,6 +484,7 @@ int smc_batch_tune(smc_batch* b, int32_t reps, int32_t* choice_host) {
 }
 
 int smc_batch_sync(smc_batch* b, int32_t* which_host) {
+  SMC_RANGE("smc_batch_sync");
   if (!b) return bfail(nullptr, SMC_EINVAL, "null handle");
   if (which_host) *which_host = -1;
   const int c = b->count;

@@ -11,9 +11,12 @@ namespace smc {
 
 // Byte offsets of the stateful sampler's workspace.
 struct Layout {
-  size_t st, tg, part, qpart, cbase, xpart, rs, wbuf, tile_src, lg_x, lg_y, lg_img, total;
-  int qblocks, ntiles;
+  size_t st, tg, part, qpart, cbase, xpart, rs, wbuf, tile_src, lg_x, lg_y, lg_img, covpart, total;
+  int qblocks, ntiles, cov_blocks;
 };
+
+// Blocks of the covariance kernel (each writes D(D+1)/2 partial sums).
+constexpr int kCovMaxBlocks = 304;
 
 }  // namespace smc
 

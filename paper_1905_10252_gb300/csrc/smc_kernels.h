@@ -150,9 +150,9 @@ cudaError_t launch_target_setup(TargetDev* tg, int kind, double nu, const double
 // BF16 images (ximg: m_pad / kLgRows tiles) and v = X^T y, and points tg at them.
 cudaError_t launch_logistic_setup(TargetDev* tg, const float* X, const float* y, int m, int d, double prior_var,
                                   float* Xw, float* yw, uint16_t* ximg, cudaStream_t s);
-cudaError_t launch_zero_cov(DevState* st, int d, cudaStream_t s);
 cudaError_t launch_max_finalize(const double* part, int nb, DevState* st, cudaStream_t s);
-cudaError_t launch_cov(const ParticleArgs& a, double* cov, int grid, cudaStream_t s);
+// eq. (7) covariance: grid blocks write covpart[grid][D(D+1)/2], then a fixed-order sum
+cudaError_t launch_cov(const ParticleArgs& a, double* cov, double* covpart, int grid, cudaStream_t s);
 cudaError_t launch_begin(DevState* st, cudaStream_t s);
 cudaError_t launch_commit(DevState* st, int d, int force_flip, int recycle, cudaStream_t s);
 cudaError_t launch_copy_mean(const DevState* st, double* out, int d, cudaStream_t s);

@@ -27,6 +27,7 @@ EXPORTED = [
     "smc_last_error", "smc_redistribute_ws_bytes", "smc_redistribute_raw", "smc_resample_raw", "smc_ws_status",
     "smc_redistribute_raw_noalloc", "smc_batch_ws_bytes", "smc_batch_create", "smc_batch_step",
     "smc_batch_step_profile", "smc_batch_set_variant", "smc_batch_tune", "smc_batch_sync", "smc_batch_destroy", "smc_batch_last_error",
+    "smc_checkpoint_bytes", "smc_checkpoint_save", "smc_checkpoint_load",
 ]
 
 BATCH_MOVE_VARIANTS, BATCH_COPY_VARIANTS = 5, 3  # SMC_BATCH_MOVE_VARIANTS, SMC_BATCH_COPY_VARIANTS
@@ -116,6 +117,9 @@ def _declare(L: C.CDLL) -> None:
     L.smc_batch_destroy.argtypes = [vp]
     L.smc_batch_last_error.argtypes = [vp]
     L.smc_batch_last_error.restype = C.c_char_p
+    L.smc_checkpoint_bytes.argtypes = [vp, C.POINTER(sz)]
+    L.smc_checkpoint_save.argtypes = [vp, vp, sz]
+    L.smc_checkpoint_load.argtypes = [vp, vp, sz]
     for name in EXPORTED:
         if name not in ("smc_last_error", "smc_batch_last_error"):
             getattr(L, name).restype = C.c_int
@@ -333,6 +337,21 @@ class Sampler:
         w = C.c_int32()
         _check(lib().smc_current(self.h, C.byref(w)), self.h)
         return (self.x, self.logpi) if w.value == 0 else (self.x_alt, self.logpi_alt)
+
+    def checkpoint(self) -> bytes:
+        """The sampler's state between iterations as bytes (smc_checkpoint_save)."""
+        L = lib()
+        nb = C.c_size_t()
+        _check(L.smc_checkpoint_bytes(self.h, C.byref(nb)), self.h)
+        buf = C.create_string_buffer(nb.value)
+        self._enter()
+        _check(L.smc_checkpoint_save(self.h, buf, nb.value), self.h)
+        return buf.raw
+
+    def restore(self, blob: bytes) -> None:
+        """Continues from a checkpoint of a sampler with this configuration."""
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        self._call(lib().smc_checkpoint_load, buf, len(blob))
 
     def close(self):
         if getattr(self, "h", None):

@@ -21,6 +21,12 @@ has waited longer than ``max_wait_rounds`` rounds blocks everything behind it
 until it is admitted).  A job's results do not depend on the jobs around it:
 batched and solo iterations are bit-identical (tests/test_gpu_serve.py).
 
+A job can be cancelled, by ``Scheduler.cancel`` (from any thread) or by its
+own ``deadline`` (seconds after arrival): a queued job leaves the queue; a
+resident one is released as soon as the iterations already launched for it
+have completed (no kernel is interrupted), and its memory returns to the
+budget.  Cancelled jobs end in ``Scheduler.cancelled`` with no result.
+
 The scheduling policy (``Scheduler``) is plain host logic over an ``Engine``
 interface, so it is tested on the CPU with a fake engine; ``GpuEngine`` is the
 CUDA implementation.  Nothing here computes any part of the sampler.
@@ -28,6 +34,7 @@ CUDA implementation.  Nothing here computes any part of the sampler.
 from __future__ import annotations
 
 import math
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -52,12 +59,14 @@ class Job:
     prior_var: float = 4.0
     step: float = 0.5
     init_scale: float = 2.0
+    deadline: float = math.inf     # cancelled if not finished this long after arrival
     # filled in by the scheduler
     admitted: float = math.nan
     finished: float = math.nan
     done_iters: int = 0
     result: np.ndarray | None = None
     waited_rounds: int = 0
+    status: str = "new"            # queued, resident, done or cancelled
 
     @property
     def m(self) -> int:
@@ -103,8 +112,51 @@ class Scheduler:
     queue: list[Job] = field(default_factory=list)
     active: list[Job] = field(default_factory=list)
     finished: list[Job] = field(default_factory=list)
+    cancelled: list[Job] = field(default_factory=list)
     used_bytes: int = 0
     rounds: int = 0
+    _cancel_ids: set = field(default_factory=set)
+    _lock: threading.Lock = field(default_factory=threading.Lock)
+
+    def cancel(self, jid: int) -> None:
+        """Requests the cancellation of job jid (takes effect in the serving
+        loop; a job that has already finished is left as it is)."""
+        with self._lock:
+            self._cancel_ids.add(int(jid))
+
+    def _take_cancels(self, now: float, busy: dict[int, int]) -> None:
+        with self._lock:
+            ids = set(self._cancel_ids)
+        ids |= {j.jid for j in self.queue + self.active if now - j.arrival > j.deadline}
+        if not ids:
+            return
+        keep_q = []
+        for j in self.queue:
+            if j.jid in ids:
+                self._drop(j, now)
+            else:
+                keep_q.append(j)
+        self.queue = keep_q
+        keep_a = []
+        for j in self.active:
+            if j.jid in ids and j.jid not in busy:  # nothing of it in flight
+                self.engine.release(j)
+                self.used_bytes -= self.engine.bytes_needed(j)
+                self._drop(j, now)
+            else:
+                keep_a.append(j)
+        self.active = keep_a
+        # requests for jobs that have ended are spent; those for jobs not yet
+        # arrived, or with iterations in flight, stay
+        ended = {j.jid for j in self.cancelled} | {j.jid for j in self.finished}
+        with self._lock:
+            self._cancel_ids -= ended
+
+    def _drop(self, job: Job, now: float) -> None:
+        job.status = "cancelled"
+        job.finished = now
+        job.result = None
+        self.cancelled.append(job)
 
     def _admit(self, now: float) -> None:
         blocked = False
@@ -116,6 +168,7 @@ class Scheduler:
             if not blocked and self.used_bytes + need <= self.budget_bytes:
                 self.engine.admit(job)
                 job.admitted = now
+                job.status = "resident"
                 self.used_bytes += need
                 self.active.append(job)
             else:
@@ -136,8 +189,10 @@ class Scheduler:
         while i < len(pending) or self.queue or self.active:
             now = self.clock() - start
             while i < len(pending) and pending[i].arrival <= now:
+                pending[i].status = "queued"
                 self.queue.append(pending[i])
                 i += 1
+            self._take_cancels(now, busy)
             self._admit(now)
             idle = [j for j in self.active if j.jid not in busy]
             if idle:
@@ -159,6 +214,7 @@ class Scheduler:
                 if j.done_iters >= j.k:
                     j.result = self.engine.result(j)
                     j.finished = self.clock() - start
+                    j.status = "done"
                     self.engine.release(j)
                     self.used_bytes -= self.engine.bytes_needed(j)
                     self.finished.append(j)
@@ -210,6 +266,7 @@ class GpuEngine(Engine):
         es = 4
         ws = 2 * job.n * job.d * es + job.n * 8 + 2 * job.n * es
         ws += 32 * job.n + 12 * job.n + 64 * job.d * job.d + (1 << 16)
+        ws += min(304, -(-job.n // 128)) * job.d * (job.d + 1) // 2 * 8  # covariance partials
         if job.kind == "logistic":
             m_pad = (job.m + 255) // 256 * 256
             ws += job.m * job.d * 4 + job.m * 4 + m_pad * 128

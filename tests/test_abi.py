@@ -66,3 +66,51 @@ def test_no_oracle_in_product_package():
     for p in list(pkg.rglob("*.py")) + list(pkg.rglob("*.cu")) + list(pkg.rglob("*.cuh")) + list(pkg.rglob("*.h")):
         text = p.read_text()
         assert "oracle" not in text.lower(), p
+
+
+def test_init_rejects_bad_arguments_host_only(built):
+    """smc_init validates everything before its first CUDA call: bad sizes,
+    dtypes, targets and pointers give SMC_EINVAL, a workspace smaller than
+    smc_workspace_bytes gives SMC_ENOMEM (admission refused), and no handle is
+    returned.  The fake device addresses are never dereferenced."""
+    from paper_1905_10252_gb300 import native
+
+    L = native.load_library()
+    A = 1 << 24  # 256-byte aligned fake device addresses
+
+    def cfg(**kw):
+        c = native.smc_config()
+        c.n, c.d, c.dtype, c.target = 1024, 4, native.SMC_F32, native.SMC_GAUSS
+        c.step, c.init_scale = 0.5, 2.0
+        c.mu_dev, c.sigma_dev = A, A + 4096
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+
+    def init(c, ws_bytes=None, x=A, ws=A + (1 << 20)):
+        if ws_bytes is None:
+            need = ctypes.c_size_t()
+            assert L.smc_workspace_bytes(ctypes.byref(c), ctypes.byref(need)) == 0
+            ws_bytes = need.value
+        h = ctypes.c_void_p(7)
+        rc = L.smc_init(ctypes.byref(h), ctypes.byref(c), x, x, A, A, A, ws, ws_bytes, None)
+        assert h.value is None  # no handle on failure
+        return rc
+
+    bad = [dict(n=0), dict(n=2 ** 31), dict(d=0), dict(d=33), dict(dtype=7), dict(target=9),
+           dict(resample_mode=3), dict(step=-1.0), dict(init_scale=0.0), dict(mu_dev=None),
+           dict(target=native.SMC_STUDENT_T, d=2, nu=5.0), dict(target=native.SMC_STUDENT_T, nu=0.0, d=1),
+           dict(target=native.SMC_LOGISTIC, X_dev=None, y_dev=A, m=10, prior_var=1.0),
+           dict(target=native.SMC_LOGISTIC, X_dev=A, y_dev=A, m=10, prior_var=0.0)]
+    for kw in bad:
+        c = cfg(**kw)
+        assert L.smc_workspace_bytes(ctypes.byref(c), ctypes.byref(ctypes.c_size_t())) == native.SMC_EINVAL, kw
+        assert init(c, ws_bytes=1 << 30) == native.SMC_EINVAL, kw
+    c = cfg()
+    assert init(c, x=0) == native.SMC_EINVAL  # null buffer
+    assert init(c, x=A + 4) == native.SMC_EINVAL  # particle buffer not 16-byte aligned
+    assert init(c, ws=A + 128) == native.SMC_EINVAL  # workspace not 256-byte aligned
+    need = ctypes.c_size_t()
+    L.smc_workspace_bytes(ctypes.byref(c), ctypes.byref(need))
+    assert init(c, ws_bytes=need.value - 1) == native.SMC_ENOMEM
+    assert b"workspace too small" in L.smc_last_error(None)

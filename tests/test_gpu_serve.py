@@ -70,3 +70,37 @@ def test_served_results_equal_alone(nat, batched):
         assert np.array_equal(j.result, alone(nat, j)), (j.jid, j.kind)
     s = latency_summary(done)
     assert s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_cancelled_jobs_leave_the_others_unchanged(nat):
+    """Jobs cancelled mid-run (resident, in the batch or on their own stream)
+    and while queued free their memory; the jobs that finish still give the
+    solo answers."""
+    from paper_1905_10252_gb300.serve import GpuEngine, Scheduler
+
+    class Canceller(GpuEngine):
+        def __init__(self, ids, after):
+            super().__init__(batched=True)
+            self.ids, self.after, self.calls, self.sch = ids, after, 0, None
+
+        def step(self, jobs, iters):
+            self.calls += 1
+            if self.calls == self.after:
+                for jid in self.ids:
+                    self.sch.cancel(jid)
+            return super().step(jobs, iters)
+
+    jobs = make_jobs()
+    for j in jobs:
+        j.k *= 3  # long enough to be cancelled while resident
+    victims = [0, 3, 15, 17]
+    eng = Canceller(victims, after=3)
+    need = sum(eng.bytes_needed(j) for j in jobs)
+    sch = Scheduler(eng, budget_bytes=need // 3, round_iters=3)
+    eng.sch = sch
+    done = sch.run(jobs)
+    assert sorted(j.jid for j in done) == sorted(j.jid for j in jobs if j.jid not in victims)
+    assert sorted(j.jid for j in sch.cancelled) == victims
+    assert sch.used_bytes == 0 and not eng.samplers and eng.batch is None
+    for j in done:
+        assert np.array_equal(j.result, alone(nat, j)), (j.jid, j.kind)

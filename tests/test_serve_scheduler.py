@@ -2,6 +2,8 @@
 engine and a fake clock: admission within the memory budget, first fit in
 arrival order with the no-overtaking rule for jobs that waited too long,
 every job run for exactly its K iterations, latency accounting."""
+import math
+
 import numpy as np
 import pytest
 
@@ -106,3 +108,68 @@ def test_latency_summary_and_poisson_stream():
         j.finished = j.arrival + lat
     s = latency_summary(jobs)
     assert s["p50_s"] == 1.0 and s["max_s"] == 3.0
+
+
+class CancellingEngine(FakeEngine):
+    """Requests cancellations from inside the serving loop: after `after`
+    step calls it cancels the listed ids; release never happens while a
+    job's iterations are in flight."""
+
+    def __init__(self, sch_ref, after, ids):
+        super().__init__()
+        self.sch_ref, self.after, self.ids, self.calls = sch_ref, after, ids, 0
+        self.pending = []
+
+    def step(self, jobs, iters):
+        self.calls += 1
+        if self.calls == self.after:
+            for jid in self.ids:
+                self.sch_ref[0].cancel(jid)
+        return super().step(jobs, iters)
+
+    def release(self, job):
+        assert job.jid not in self.pending, "released with iterations in flight"
+        super().release(job)
+
+
+def test_cancel_resident_queued_and_future_jobs():
+    # job 0 resident (long), job 1 resident (short), job 2 queued behind the
+    # budget, job 3 arrives later; cancel 0, 2 and 3 after the second round
+    jobs = make_jobs([400, 400, 500, 100], [100, 10, 5, 5], [0.0, 0.0, 0.0, 1.0])
+    ref = [None]
+    eng = CancellingEngine(ref, after=2, ids=[0, 2, 3])
+    sch = Scheduler(eng, budget_bytes=1000, round_iters=5, clock=FakeClock())
+    ref[0] = sch
+    done = sch.run(jobs)
+    assert [j.jid for j in done] == [1]
+    assert sorted(j.jid for j in sch.cancelled) == [0, 2, 3]
+    by = {j.jid: j for j in jobs}
+    assert by[0].status == "cancelled" and by[0].result is None and 0 < by[0].done_iters < 100
+    assert by[2].status == "cancelled" and math.isnan(by[2].admitted)  # never admitted
+    assert by[3].status == "cancelled" and by[3].done_iters == 0
+    assert by[1].status == "done" and by[1].done_iters == 10
+    assert sch.used_bytes == 0 and not eng.resident
+    assert not sch._cancel_ids
+
+
+def test_cancelling_a_finished_job_changes_nothing():
+    jobs = make_jobs([100], [5], [0.0])
+    eng = FakeEngine()
+    sch = Scheduler(eng, budget_bytes=1000, clock=FakeClock())
+    done = sch.run(jobs)
+    sch.cancel(0)
+    assert done[0].status == "done" and float(done[0].result[0]) == 5 and not sch.cancelled
+
+
+def test_deadline_cancels_jobs_that_would_finish_late():
+    # one slot: the first job runs 200 iterations (one round = 5 iterations =
+    # a few clock ticks), the others wait; a short deadline cancels the waiters
+    jobs = make_jobs([900, 900, 900], [200, 5, 5], [0.0, 0.0, 0.0])
+    jobs[1].deadline = 0.01
+    eng = FakeEngine()
+    sch = Scheduler(eng, budget_bytes=1000, round_iters=5, clock=FakeClock())
+    done = sch.run(jobs)
+    assert sorted(j.jid for j in done) == [0, 2]
+    assert [j.jid for j in sch.cancelled] == [1]
+    assert jobs[1].finished - jobs[1].arrival > 0.01
+    assert sch.used_bytes == 0 and not eng.resident
