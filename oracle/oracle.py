@@ -87,6 +87,7 @@ def _declare(L: C.CDLL) -> None:
     L.orc_resample_u.restype = C.c_uint64
     L.orc_systematic.argtypes = [C.c_int64, _u64p, C.c_uint64, C.c_uint64, _i32p, _u32p]
     L.orc_redistribute.argtypes = [C.c_int64, C.c_int64, _i32p, C.c_void_p, C.c_void_p]
+    L.orc_nearly_sort.argtypes = [C.c_int64, C.c_int64, _i32p, C.c_void_p, _i32p, C.c_void_p]
     L.orc_reset_logw.argtypes = [C.c_int64]
     L.orc_reset_logw.restype = C.c_double
     L.orc_resample.argtypes = [C.c_int64, _dp, C.c_uint64, C.c_uint64, C.c_int, _i32p, _u32p, _u64p, _u64p]
@@ -199,6 +200,20 @@ def redistribute(ncopies, x: np.ndarray) -> np.ndarray:
     lib().orc_redistribute(N, row_bytes, _p(nc, C.c_int32), xa.ctypes.data_as(C.c_void_p),
                            out.ctypes.data_as(C.c_void_p))
     return out
+
+
+def nearly_sort(ncopies, x: np.ndarray):
+    """Algorithm 8 (S-NS) on the keys ncopies and the rows of x: returns
+    (ncopies_new, x_new)."""
+    nc = np.ascontiguousarray(ncopies, dtype=np.int32)
+    xa = np.ascontiguousarray(x)
+    nc_new = np.empty_like(nc)
+    out = np.empty_like(xa)
+    N = nc.size
+    row_bytes = xa.nbytes // N if N else 0
+    lib().orc_nearly_sort(N, row_bytes, _p(nc, C.c_int32), xa.ctypes.data_as(C.c_void_p), _p(nc_new, C.c_int32),
+                          out.ctypes.data_as(C.c_void_p))
+    return nc_new, out
 
 
 def reset_logw(N: int) -> float:

@@ -26,6 +26,8 @@
  *   orc_lse_ess             pinned: closed forms (equal / one-hot weights)
  *   orc_systematic          pinned: sum == N, floor bounds, exhaustive-U mean
  *   orc_redistribute        pinned: brute-force stable repeat, all compositions
+ *   orc_nearly_sort         pinned: hand-worked cases, Definition 1 (ascending Nearly-Sorted),
+ *                           stable partition over every key vector of small N
  *   orc_run (Gaussian)      pinned: closed-form posterior moments within MC error
  *   logistic logpi          pinned: b = 0 closed form (-M log 2), scipy Bernoulli log-likelihood
  *                           + normal prior, closed-form gradient by central differences,
@@ -573,6 +575,31 @@ void orc_redistribute(int64_t N, int64_t row_bytes, const int32_t* ncopies, cons
       memcpy(dst + i * row_bytes, src + j * row_bytes, (size_t)row_bytes);
       ++i;
     }
+}
+
+/* Algorithm 8 (S-NS, Sec. 4.2): a single pass in index order with two
+ * cursors; an element whose copy count is positive takes the next free slot
+ * from the right end of the output, any other element the next free slot
+ * from the left end.  The keys come out as an ascending Nearly-Sorted
+ * sequence (Definition 1: zeros first, then the positive counts); each
+ * particle row travels with its key. */
+void orc_nearly_sort(int64_t N, int64_t row_bytes, const int32_t* ncopies, const void* x,
+                     int32_t* ncopies_new, void* x_new) {
+  const char* src = x;
+  char* dst = x_new;
+  int64_t l = 0, r = N - 1;
+  for (int64_t i = 0; i < N; ++i) {
+    int64_t k;
+    if (ncopies[i] > 0) {
+      k = r;
+      --r;
+    } else {
+      k = l;
+      ++l;
+    }
+    ncopies_new[k] = ncopies[i];
+    memcpy(dst + k * row_bytes, src + i * row_bytes, (size_t)row_bytes);
+  }
 }
 
 /* Algorithm 4, line 3: all weights reset to 1/N. */
