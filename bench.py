@@ -437,11 +437,17 @@ def run_redistribute(args):
         out = torch.empty_like(x)
         wsb = torch.empty(native.smc_redistribute_ws_bytes(n), dtype=torch.uint8, device="cuda")
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        # the paper's N-R local step for comparison: S-NS (Algorithm 8), then
+        # S-R on the nearly-sorted keys and rows
+        ns_keys, ns_rows, nr_out = (torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty_like(x),
+                                    torch.empty_like(x))
+        wsn = torch.empty(native.smc_nearly_sort_ws_bytes(n), dtype=torch.uint8, device="cuda")
+        row_bytes = d * 4
         for case in args.cases.split(","):
             lw = inputs.one_hot_log_weights(n, 0) if case == "onehot" else inputs.log_weights(n, float(case[1:]), 0)
             lwd = torch.as_tensor(lw, device="cuda")
             nc = torch.empty(n, dtype=torch.int32, device="cuda")
-            res_ms, red_ms = [], []
+            res_ms, red_ms, ns_ms, nr_ms = [], [], [], []
             for it in range(args.warmup + 20):
                 flush.zero_()  # L2 flush between iterations
                 a, b, c = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -453,19 +459,33 @@ def run_redistribute(args):
                 b2.record()
                 native.smc_redistribute_raw(nc, x, out, ws=wsb)
                 c.record()
+                flush.zero_()
+                e0, e1, e2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e0.record()
+                native.smc_nearly_sort_raw(nc, x, ns_keys, ns_rows, ws=wsn)
+                e1.record()
+                native.smc_redistribute_raw(ns_keys, ns_rows, nr_out, ws=wsb)
+                e2.record()
                 torch.cuda.synchronize()
                 if it >= args.warmup:
                     res_ms.append(a.elapsed_time(b))
                     red_ms.append(b2.elapsed_time(c))
+                    ns_ms.append(e0.elapsed_time(e1))
+                    nr_ms.append(e0.elapsed_time(e2))
             nnz = int((nc > 0).sum().item())
-            red_bytes = 4 * n + 64 * nnz + 64 * n
+            red_bytes = 4 * n + row_bytes * nnz + row_bytes * n
             res_bytes = 8 * n + 8 * n + 4 * n
+            ns_bytes = 8 * n + 2 * row_bytes * n
             rm, dm = statistics.median(res_ms), statistics.median(red_ms)
+            sm_, nm = statistics.median(ns_ms), statistics.median(nr_ms)
             line = {"metric": "redistribute GB/s", "workload": f"resample+redistribute N=2^{int(np.log2(n))} {case}",
                     "n": n, "d": d, "survivors": nnz, "resample_ms": rm, "redistribute_ms": dm,
                     "redistribute_gbs": red_bytes / (dm * 1e-3) / 1e9, "resample_gbs": res_bytes / (rm * 1e-3) / 1e9,
                     "peak_gbs": peak, "peak_kind": peak_kind,
-                    "redistribute_frac": red_bytes / (dm * 1e-3) / 1e9 / peak, "timing": "median of 20, L2 flushed"}
+                    "redistribute_frac": red_bytes / (dm * 1e-3) / 1e9 / peak,
+                    "nearly_sort_ms": sm_, "nearly_sort_gbs": ns_bytes / (sm_ * 1e-3) / 1e9,
+                    "nearly_sort_frac": ns_bytes / (sm_ * 1e-3) / 1e9 / peak,
+                    "nr_ms": nm, "nr_over_gather": nm / dm, "timing": "median of 20, L2 flushed"}
             if rank == 0:
                 print(json.dumps(line), flush=True)
 

@@ -227,6 +227,25 @@ int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_de
 int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t t, int32_t mode,
                      int32_t* ncopies_dev, smc_iter_stats* stats_dev, void* ws_dev, smc_stream_t stream);
 
+/* Algorithm 8 (S-NS, Sec. 4.2), the local step of the paper's nearly-sort
+ * based redistribute (N-R, Algorithm 9), as a comparison for the gather
+ * design of smc_redistribute_raw.  Scanning i = 0..n-1, a row whose key
+ * ncopies_i is positive goes to the next free slot from the right end of the
+ * output, any other row to the next free slot from the left end:
+ *   slot(i) = n - 1 - P_i if ncopies_i > 0, else i - P_i,
+ *   P_i = #{j < i : ncopies_j > 0};
+ * ncopies_out_dev[slot(i)] = ncopies_i and out row slot(i) = in row i, so the
+ * output keys are an ascending Nearly-Sorted sequence (Definition 1: every
+ * zero before every positive key).  Any int32 keys are accepted (no device
+ * error).  ncopies_dev: n int32, 16-byte aligned; in_dev / out_dev: n rows of
+ * row_bytes (a multiple of 4; rows aligned to 16, 8 or 4 bytes as row_bytes
+ * allows); outputs must not overlap inputs.  ws_dev:
+ * smc_nearly_sort_ws_bytes(n) bytes, 256-byte aligned.  Errors: SMC_EINVAL
+ * (sizes, null or misaligned pointers), SMC_ECUDA. */
+int smc_nearly_sort_ws_bytes(int64_t n, size_t* bytes);
+int smc_nearly_sort_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
+                        int32_t* ncopies_out_dev, void* out_dev, void* ws_dev, smc_stream_t stream);
+
 /* Synchronises stream and returns (then clears) the error recorded in a
  * stateless workspace. */
 int smc_ws_status(void* ws_dev, smc_stream_t stream);

@@ -683,6 +683,37 @@ int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t 
   return SMC_OK;
 }
 
+int smc_nearly_sort_ws_bytes(int64_t n, size_t* bytes) {
+  if (n < 1 || n > 2147483647LL || !bytes) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
+  *bytes = 2 * align_up(size_t(nearly_sort_tiles(n)) * sizeof(int32_t));
+  return SMC_OK;
+}
+
+int smc_nearly_sort_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
+                        int32_t* ncopies_out_dev, void* out_dev, void* ws_dev, smc_stream_t stream) {
+  SMC_RANGE("smc_nearly_sort_raw");
+  if (n < 1 || n > 2147483647LL) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
+  if (row_bytes < 4 || row_bytes % 4) return fail(nullptr, SMC_EINVAL, "row_bytes must be a positive multiple of 4");
+  if (!ncopies_dev || !in_dev || !ncopies_out_dev || !out_dev || !ws_dev) return fail(nullptr, SMC_EINVAL, "null pointer");
+  if (!aligned(ws_dev, kAlign)) return fail(nullptr, SMC_EINVAL, "workspace must be 256-byte aligned");
+  if (!aligned(ncopies_dev, 16)) return fail(nullptr, SMC_EINVAL, "ncopies must be 16-byte aligned");
+  const size_t va = row_bytes % 16 == 0 ? 16 : (row_bytes % 8 == 0 ? 8 : 4);
+  if (!aligned(in_dev, va) || !aligned(out_dev, va)) return fail(nullptr, SMC_EINVAL, "rows misaligned");
+  NearlySortArgs a{};
+  a.n = n;
+  a.row_bytes = row_bytes;
+  a.ntiles = nearly_sort_tiles(n);
+  a.ncopies = ncopies_dev;
+  a.ncopies_out = ncopies_out_dev;
+  a.in = in_dev;
+  a.out = out_dev;
+  a.tile_count = static_cast<int32_t*>(ws_dev);
+  a.tile_base = reinterpret_cast<int32_t*>(static_cast<char*>(ws_dev) + align_up(size_t(a.ntiles) * sizeof(int32_t)));
+  cudaError_t e = launch_nearly_sort(a, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "smc_nearly_sort_raw");
+  return SMC_OK;
+}
+
 int smc_ws_status(void* ws_dev, smc_stream_t stream) {
   if (!ws_dev) return fail(nullptr, SMC_EINVAL, "null workspace");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

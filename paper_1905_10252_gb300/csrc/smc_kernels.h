@@ -104,6 +104,20 @@ struct QuantArgs {
   void* xpart;         // nblocks x d partial sums, in the particle dtype
 };
 
+// Sequential Nearly Sort (Algorithm 8) as a stable partition (k_nearly_sort.cu).
+constexpr int kNsTile = 4096;  // keys per block
+struct NearlySortArgs {
+  int64_t n;
+  int32_t row_bytes;   // multiple of 4
+  int32_t ntiles;      // ceil(n / kNsTile)
+  const int32_t* ncopies;  // 16-byte aligned
+  int32_t* ncopies_out;
+  const void* in;
+  void* out;
+  int32_t* tile_count;  // ntiles
+  int32_t* tile_base;   // ntiles, exclusive prefix of tile_count
+};
+
 struct RedistArgs {
   int64_t n;
   int32_t row_bytes;
@@ -190,6 +204,8 @@ cudaError_t launch_nc_reduce(const NcScanArgs& a, cudaStream_t s);
 cudaError_t launch_nc_finalize(const NcScanArgs& a, cudaStream_t s);
 cudaError_t launch_nc_scan(const NcScanArgs& a, cudaStream_t s);
 cudaError_t launch_redistribute(const RedistArgs& a, cudaStream_t s);
+int nearly_sort_tiles(int64_t n);
+cudaError_t launch_nearly_sort(const NearlySortArgs& a, cudaStream_t s);
 cudaError_t launch_state_init(DevState* st, int64_t n, int64_t t, int F, cudaStream_t s);
 
 }  // namespace smc

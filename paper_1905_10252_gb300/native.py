@@ -28,6 +28,7 @@ EXPORTED = [
     "smc_redistribute_raw_noalloc", "smc_batch_ws_bytes", "smc_batch_create", "smc_batch_step",
     "smc_batch_step_profile", "smc_batch_set_variant", "smc_batch_tune", "smc_batch_sync", "smc_batch_destroy", "smc_batch_last_error",
     "smc_checkpoint_bytes", "smc_checkpoint_save", "smc_checkpoint_load",
+    "smc_nearly_sort_ws_bytes", "smc_nearly_sort_raw",
 ]
 
 BATCH_MOVE_VARIANTS, BATCH_COPY_VARIANTS = 5, 3  # SMC_BATCH_MOVE_VARIANTS, SMC_BATCH_COPY_VARIANTS
@@ -117,6 +118,8 @@ def _declare(L: C.CDLL) -> None:
     L.smc_batch_destroy.argtypes = [vp]
     L.smc_batch_last_error.argtypes = [vp]
     L.smc_batch_last_error.restype = C.c_char_p
+    L.smc_nearly_sort_ws_bytes.argtypes = [i64, C.POINTER(sz)]
+    L.smc_nearly_sort_raw.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp]
     L.smc_checkpoint_bytes.argtypes = [vp, C.POINTER(sz)]
     L.smc_checkpoint_save.argtypes = [vp, vp, sz]
     L.smc_checkpoint_load.argtypes = [vp, vp, sz]
@@ -172,6 +175,33 @@ def smc_redistribute_raw(ncopies: torch.Tensor, x_in: torch.Tensor, x_out: torch
     _check(lib().smc_redistribute_raw(n, row_bytes, _ptr(ncopies), _ptr(x_in), _ptr(x_out), _ptr(ws),
                                       _stream_ptr(stream)))
     return x_out
+
+
+def smc_nearly_sort_ws_bytes(n: int) -> int:
+    out = C.c_size_t()
+    _check(lib().smc_nearly_sort_ws_bytes(int(n), C.byref(out)))
+    return out.value
+
+
+def smc_nearly_sort_raw(ncopies: torch.Tensor, x_in: torch.Tensor, ncopies_out: torch.Tensor | None = None,
+                        x_out: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """Algorithm 8 (S-NS) on the keys ncopies (int32) and the rows of x_in;
+    returns (ncopies_out, x_out)."""
+    n = ncopies.numel()
+    if x_in.shape[0] != n:
+        raise ValueError("x_in must have one row per ncopies entry")
+    if ncopies.dtype != torch.int32:
+        raise ValueError("ncopies must be int32")
+    if ncopies_out is None:
+        ncopies_out = torch.empty_like(ncopies)
+    if x_out is None:
+        x_out = torch.empty_like(x_in)
+    if ws is None:
+        ws = _alloc_ws(smc_nearly_sort_ws_bytes(n), x_in.device)
+    row_bytes = x_in[0].numel() * x_in.element_size() if n else 0
+    _check(lib().smc_nearly_sort_raw(n, row_bytes, _ptr(ncopies), _ptr(x_in), _ptr(ncopies_out), _ptr(x_out),
+                                     _ptr(ws), _stream_ptr(stream)))
+    return ncopies_out, x_out
 
 
 def smc_resample_raw(logw: torch.Tensor, seed: int, t: int, mode: int = RESAMPLE_ESS,
