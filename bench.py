@@ -275,15 +275,19 @@ def job_value(n_per_rank: int, steps: int, world_size: int, total_ms: float) -> 
     return n_per_rank * steps * world_size / (total_ms * 1e-3)
 
 
-def algorithmic_bytes(n: int, d: int, esize: int, survivors: float):
+def algorithmic_bytes(n: int, d: int, esize: int, survivors: float, est_in_move: bool = False):
     """Per-launch algorithmic bytes of each stage (see the measurement section
-    of the design notes): reads + writes the definition of the stage needs."""
+    of the design notes): reads + writes the definition of the stage needs.
+    est_in_move: the move kernel formed the sums of eq. (7) (FP32 Gaussian,
+    D <= 16, every log w equal after the previous resampling), so the
+    quantise pass reads log w only."""
     row = d * esize
     return {
         # read x, log pi, log w; write x, log pi, log w
         "move_reweight": n * (2 * row + 2 * esize + 2 * 8),
-        # read log w (quantisation) and x (the weighted mean of eq. (7))
-        "quantise_reduce_estimate": n * (8 + row),
+        # read log w (quantisation) and x (the weighted mean of eq. (7)),
+        # unless the move kernel formed the mean
+        "quantise_reduce_estimate": n * 8 if est_in_move else n * (8 + row),
         # read log w, write one run start per survivor (the ncopies information)
         "systematic_scan": n * 8 + survivors * 4,
         # read the run starts, the distinct surviving rows + log pi, write
@@ -345,7 +349,8 @@ def run_iteration(args):
     stage_ms = {k: float(np.mean(v)) for k, v in per_stage.items()}
     st = S.stats()
     survivors = float(st["survivors"])
-    byt = algorithmic_bytes(n, d, 4, survivors)
+    # every timed iteration resamples, so each one starts from equal weights
+    byt = algorithmic_bytes(n, d, 4, survivors, est_in_move=d <= 16)
     peak, peak_kind = peaks()
     dominant = max(stage_ms, key=stage_ms.get)
     traffic = measured_traffic()
@@ -564,6 +569,8 @@ def run_batch(args):
                 for j, name in enumerate(STAGES)}
     # algorithmic bytes of the stages that do not depend on the resampling decision
     mv_bytes = sum(n * (2 * 4 * d + 2 * 4 + 2 * 8) for n, d in shapes)
+    # (rows counted for every member: an upper bound, since members with
+    # D <= 16 read log w only in iterations that follow a resampling)
     q_bytes = sum(n * (8 + 4 * d) for n, d in shapes)
     peak, peak_kind = peaks()
 

@@ -499,14 +499,69 @@ __device__ __forceinline__ void stage_rows(const float* __restrict__ P, const fl
   for (int c = threadIdx.x; c < kTgtMaxD; c += blockDim.x) m[c] = mu[c];
 }
 
-template <int DPL, bool MOVE, bool REWEIGHT, typename FS>
+// eq. (7) record of one warp tile (kEstTile consecutive particles) whose
+// starting log weights all equal R: rec = {M, sum_i e^{dlt_i - Mf} x_i} with
+// M = R + Mf, dlt_i the particle's log pi difference and Mf the largest of
+// the lanes' references em (every dlt_i < Mf + 16).  Each lane's sums are
+// rescaled from its em to Mf and added over the warp by a transposing halving
+// tree (a fixed order: the record does not depend on the launch shape).
+template <int DMAX>
+__device__ __forceinline__ void warp_write_est(float em, double R, float (&v)[DMAX], int d,
+                                               double* __restrict__ rec) {
+  const int lane = threadIdx.x & 31;
+  float Mf = em;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) Mf = fmaxf(Mf, __shfl_xor_sync(0xffffffffu, Mf, o));
+  const float sc = (em == -INFINITY) ? 0.0f : __expf(em - Mf);
+#pragma unroll
+  for (int c = 0; c < DMAX; ++c) v[c] *= sc;
+  // halving: at the step with offset o, a lane keeps the upper half of its
+  // columns if (lane & o), the lower half otherwise, and adds its partner's
+  // copy of the kept half
+  int col = 0;
+#pragma unroll
+  for (int h = DMAX / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = lane & o;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float send = up ? v[k] : v[k + h];
+      const float keep = up ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    col += up ? h : 0;
+  }
+  // DMAX halvings used offsets 16 .. 32 / DMAX; the lanes that still share
+  // a column add up with the remaining offsets
+#pragma unroll
+  for (int o = 16 / DMAX; o >= 1; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  if ((lane & (32 / DMAX - 1)) == 0 && col < d) rec[1 + col] = double(v[0]);
+  // the record's reference log w, formed as the reweight forms every log w
+  if (lane == 0) rec[0] = Mf == -INFINITY ? -INFINITY : R + double(Mf);
+}
+
+template <int DPL, bool MOVE, bool REWEIGHT, typename FS, bool EST = false>
 __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const FS gp, const int blk, const int nblk) {
   constexpr int DMAX = DPL;
+  static_assert(!EST || DPL <= 16, "eq. (7) records: D <= 16");
   // the next particle's data is loaded during the current one's arithmetic
   // when the registers allow it (up to 16 coordinates per lane)
   constexpr bool PF = DPL <= 16;
   MaxTracker mt;
   mt.init();
+  // EST: eq. (7) sums of the lane's particles in the current warp tile.  They
+  // are formed only when every starting log w is the same value R (the last
+  // iteration resampled): then log w_i - log w_j = (lpi_i - lpc_i) - (lpi_j -
+  // lpc_j) up to one FP64 rounding, so the weights need only the FP32 log pi
+  // differences dlt.  The lane's sums are relative to a reference em, raised
+  // (and the sums rescaled) only when a dlt exceeds it by more than 16, so
+  // every term stays below e^16 and the rescale is rare.  Otherwise (weights
+  // not uniform) the quantise pass reads the rows.
+  const bool est_on = EST && a.st->w_uniform;
+  const double R = a.st->reset_logw;
+  float em = -INFINITY;
+  float eacc[EST ? DMAX : 1];
+#pragma unroll
+  for (int c = 0; c < (EST ? DMAX : 1); ++c) eacc[c] = 0.0f;
   const int cur = a.st->cur;
   const uint64_t t = uint64_t(a.st->t);
   float* __restrict__ x = static_cast<float*>(cur ? a.x[1] : a.x[0]);
@@ -517,50 +572,58 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
   const int nvalid = d;
   const bool vec = ((d & 3) == 0) && (nvalid >= DPL);
   const float eps = float(a.step);
-  // The loop runs over whole warps (its bound is warp-uniform); lanes past
-  // the end are predicated.
-  constexpr int kGroups = 32;
-  const int64_t warp_global = (int64_t(blk) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t step = int64_t(nblk) * (blockDim.x >> 5) * kGroups;
+  // Warp tiles of kEstTile consecutive particles (kEstChunks chunks of 32,
+  // lane l takes particle 32 r + l of chunk r), tile j to warp j mod W.  The
+  // loop bound is warp-uniform; lanes past the end are predicated.
+  constexpr int kChunks = kEstTile / 32;
+  const int64_t gw = (int64_t(blk) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t W = int64_t(nblk) * (blockDim.x >> 5);
+  const int64_t ntile = (a.n + kEstTile - 1) / kEstTile;
   const int grp = threadIdx.x & 31;
-  int64_t base = warp_global * kGroups;
+  int64_t j = gw;
+  int r = 0;
   // prologue: the first particle's data
   float xo[DPL];
   double lwc = 0.0;
   float lpc = 0.0f;
   {
-    const int64_t i = base + grp;
-    if (i < a.n && nvalid > 0) load_seg<DPL>(x + i * d + c0, vec, nvalid, xo);
+    const int64_t i = j * kEstTile + grp;
+    if (j < ntile && i < a.n && nvalid > 0) load_seg<DPL>(x + i * d + c0, vec, nvalid, xo);
     else
 #pragma unroll
       for (int c = 0; c < DPL; ++c) xo[c] = 0.0f;
-    if (REWEIGHT && i < a.n && q == 0) {
+    if (REWEIGHT && j < ntile && i < a.n && q == 0) {
       lwc = logw[i];
       lpc = lp[i];
     }
   }
-  for (; base < a.n; base += step) {
-    const int64_t i = base + grp;
+  bool first = true;
+  while (j < ntile) {
+    const int64_t i = j * kEstTile + r * 32 + grp;
     const bool valid = i < a.n;
-    if (!PF && base != warp_global * kGroups) {  // (the prologue loaded the first)
+    if (!PF && !first) {  // (the prologue loaded the first)
       if (valid && nvalid > 0) load_seg<DPL>(x + i * d + c0, vec, nvalid, xo);
       if (REWEIGHT && valid && q == 0) {
         lwc = logw[i];
         lpc = lp[i];
       }
     }
-    // prefetch the next particle
-    const int64_t inx = i + step;
+    first = false;
+    // the next particle: next chunk of this tile, or the first of the next
+    const int rn = r + 1 == kChunks ? 0 : r + 1;
+    const int64_t jn = r + 1 == kChunks ? j + W : j;
+    const int64_t inx = jn * kEstTile + rn * 32 + grp;
+    const bool vn = jn < ntile && inx < a.n;
     constexpr int kPF = PF ? DPL : 1;
     float xn[kPF];
     double lwn = 0.0;
     float lpn = 0.0f;
     if constexpr (PF) {
-      if (inx < a.n && nvalid > 0) load_seg<kPF>(x + inx * d + c0, vec, nvalid, xn);
+      if (vn && nvalid > 0) load_seg<kPF>(x + inx * d + c0, vec, nvalid, xn);
       else
 #pragma unroll
         for (int c = 0; c < kPF; ++c) xn[c] = 0.0f;
-      if (REWEIGHT && inx < a.n && q == 0) {
+      if (REWEIGHT && vn && q == 0) {
         lwn = logw[inx];
         lpn = lp[inx];
       }
@@ -604,9 +667,9 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       for (int c = 0; c < DMAX; ++c) dv[c] = xo[c] - gp.mu(c);
       float qs = 0.0f;
 #pragma unroll
-      for (int r = 0; r < DMAX; ++r) {
-        if (r < d) {
-          const float acc = gp.row(r, dv);
+      for (int rr = 0; rr < DMAX; ++rr) {
+        if (rr < d) {
+          const float acc = gp.row(rr, dv);
           qs = fmaf(acc, acc, qs);
         }
       }
@@ -617,6 +680,31 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       lp[i] = lpi;
       logw[i] = lw;
       mt.add(lw);
+      if constexpr (EST) {
+        if (est_on) {
+          const float dlt = lpi - lpc;
+          float dl = dlt - em;
+          if (dl > 16.0f) {  // the lane's reference exceeded by e^16 (always for its first particle)
+            const float sc = __expf(-dl);
+#pragma unroll
+            for (int c = 0; c < DMAX; ++c) eacc[c] *= sc;
+            em = dlt;
+            dl = 0.0f;
+          }
+          const float e = dl == dl ? __expf(dl) : 0.0f;  // NaN only with a NaN log pi (reported)
+#pragma unroll
+          for (int c = 0; c < DMAX; ++c)
+            if (c < d) eacc[c] = fmaf(e, xo[c], eacc[c]);
+        }
+      }
+    }
+    if constexpr (EST) {
+      if (est_on && r + 1 == kChunks) {  // the tile is complete: its record, then fresh sums
+        warp_write_est<DMAX>(em, R, eacc, d, a.epart + j * (1 + d));
+        em = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < DMAX; ++c) eacc[c] = 0.0f;
+      }
     }
     if constexpr (PF) {
 #pragma unroll
@@ -624,15 +712,17 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       lwc = lwn;
       lpc = lpn;
     }
+    r = rn;
+    j = jn;
   }
   if (REWEIGHT) block_write_max(mt, a.part + 2 * blk, a.st);
 }
 
 // One sampler per launch: the factor's entries are kernel parameters, read by
 // the FMAs straight from the constant bank.
-template <int DPL, bool MOVE, bool REWEIGHT>
+template <int DPL, bool MOVE, bool REWEIGHT, bool EST = false>
 __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleArgs a, const GaussParamsF32 gp) {
-  move_reweight_body<DPL, MOVE, REWEIGHT>(a, FactorParam{gp}, blockIdx.x, gridDim.x);
+  move_reweight_body<DPL, MOVE, REWEIGHT, FactorParam, EST>(a, FactorParam{gp}, blockIdx.x, gridDim.x);
 }
 
 // Batched: block b runs block map[b].y of map[b].z of sampler map[b].x; the
@@ -648,11 +738,11 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_batch(const Part
   __syncthreads();
   const FactorSmem fs{sfac, smu};
   if (a.d <= 8)
-    move_reweight_body<8, true, true>(a, fs, m.y, m.z);
+    move_reweight_body<8, true, true, FactorSmem, true>(a, fs, m.y, m.z);
   else if (a.d <= 16)
-    move_reweight_body<16, true, true>(a, fs, m.y, m.z);
-  else
-    move_reweight_body<32, true, true>(a, fs, m.y, m.z);
+    move_reweight_body<16, true, true, FactorSmem, true>(a, fs, m.y, m.z);
+  else  // (D > 16: no register room for the estimate; the quantise pass forms it)
+    move_reweight_body<32, true, true, FactorSmem, false>(a, fs, m.y, m.z);
 }
 
 // ---------------------------------------------------------------- finalise the maximum
@@ -675,6 +765,10 @@ __device__ __forceinline__ void max_finalize_body(const double* __restrict__ par
     const double M = from_ordered_key(v);
     st->m = M;
     if (!(M > -INFINITY && M < INFINITY)) record_error(st, SMC_ENONFINITE);
+    // the move kernel that just ran wrote eq. (7) records iff the weights it
+    // started from were uniform; after its reweight they are not
+    st->est_ready = st->w_uniform;
+    st->w_uniform = 0;
   }
 }
 
@@ -796,6 +890,8 @@ __device__ __forceinline__ void commit_one(DevState* st, int d, int force_flip, 
   }
   if (flip) st->cur ^= 1;
   st->lse_prev = flip ? 0.0 : st->lse;
+  // a resampled iteration leaves every log w at reset_logw
+  st->w_uniform = (flip && !st->err) ? 1 : 0;
 }
 
 __global__ void k_commit(DevState* st, int d, int force_flip, int recycle) {
@@ -880,6 +976,13 @@ static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, int thr
     case OP_MOVE: k_move_reweight_lanes<DPL, true, false><<<grid, threads, 0, s>>>(a, gp); break;
     case OP_REWEIGHT: k_move_reweight_lanes<DPL, false, true><<<grid, threads, 0, s>>>(a, gp); break;
     case OP_MOVE_REWEIGHT: k_move_reweight_lanes<DPL, true, true><<<grid, threads, 0, s>>>(a, gp); break;
+    case OP_MOVE_REWEIGHT_EST:  // D <= 16 only (register room)
+      if constexpr (DPL <= 16) {
+        k_move_reweight_lanes<DPL, true, true, true><<<grid, threads, 0, s>>>(a, gp);
+        break;
+      } else {
+        return cudaErrorInvalidValue;
+      }
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

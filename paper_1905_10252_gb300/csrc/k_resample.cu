@@ -108,6 +108,8 @@ __global__ void k_state_init(DevState* st, int64_t n, int64_t t, int F) {
   st->trace_t0 = 0;
   st->mean_out = st->fhat_out = st->cov_out = nullptr;
   st->want_cov = 0;
+  st->w_uniform = 0;
+  st->est_ready = 0;
 }
 
 // ---------------------------------------------------------------- max of log w (stateless path)
@@ -181,11 +183,41 @@ __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int 
 #pragma unroll
   for (int c = 0; c < DMAX; ++c) acc[c] = ST(0);
   const int d = a.d;
+  // eq. (7) from the move kernel's tile records when it wrote them this
+  // iteration, else from the rows
+  const bool use_rec = EST && a.est_src && st->est_ready;
   if (!st->err) {
     const double m = st->m;
     const int sh_w = 62 - st->F;
     const int64_t base = int64_t(blk) * kQTile;
     const ST* __restrict__ x = static_cast<const ST*>(st->cur ? a.x[1] : a.x[0]);
+    bool done = false;
+    if constexpr (sizeof(ST) == 4) {  // (records exist for FP32 samplers only)
+      if (use_rec) {
+        // only log w is read: every load of the thread first (more bytes in
+        // flight), then the arithmetic
+        double lv[kQItems];
+#pragma unroll
+        for (int k = 0; k < kQItems; ++k) {
+          const int64_t i = base + k * kQThreads + threadIdx.x;
+          lv[k] = i < a.n ? a.logw[i] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < kQItems; ++k) {
+          const int64_t i = base + k * kQThreads + threadIdx.x;
+          if (i < a.n) {
+            const uint64_t E = expfx_a(__dsub_rn(m, lv[k]), T);
+            const uint64_t W = E >> sh_w;
+            a.wbuf[i] = W;
+            sw += W;
+            sw2 += u128(W) * W;
+            se += E;
+          }
+        }
+        done = true;
+      }
+    }
+    if (!done)
 #pragma unroll 4
     for (int k = 0; k < kQItems; ++k) {
       const int64_t i = base + k * kQThreads + threadIdx.x;
@@ -196,7 +228,7 @@ __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int 
         sw += W;
         sw2 += u128(W) * W;
         se += E;
-        if (EST) {
+        if (EST && !use_rec) {
           ST w;
           weight_of(E, &w);
           const ST* row = x + i * d;
@@ -231,7 +263,7 @@ __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int 
     sh[wid][3] = uint64_t(se);
     sh[wid][4] = uint64_t(se >> 64);
   }
-  if (EST) {
+  if (EST && !use_rec) {
     // warp sums in the state precision (the FP64 pipe is scarce), then FP64
 #pragma unroll
     for (int c = 0; c < DMAX; ++c) {
@@ -257,10 +289,27 @@ __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int 
     q[3] = uint64_t(te);
     q[4] = uint64_t(te >> 64);
   }
-  if (EST && threadIdx.x < d) {
+  if (EST && !use_rec && threadIdx.x < d) {
     double v = 0.0;
     for (int w = 0; w < kQThreads / 32; ++w) v += shx[w][threadIdx.x];
     static_cast<ST*>(a.xpart)[int64_t(blk) * d + threadIdx.x] = ST(v);
+  }
+  if (use_rec && wid == 0) {
+    // eq. (7) partials of this block from the move kernel's tile records
+    // {M_r, sum e^{log w - M_r} x}: scaled to the units of E_i (2^62 e^{log w - m})
+    // and added over the block's tiles by a fixed shuffle tree
+    constexpr int kTiles = kQTile / kEstTile;
+    static_assert(kTiles <= 32, "one lane per tile record");
+    const int64_t ntile = (a.n + kEstTile - 1) / kEstTile;
+    const int64_t jt = int64_t(blk) * kTiles + lane;
+    const bool have = lane < kTiles && jt < ntile && !st->err;
+    const double* rec = a.epart + jt * (1 + d);
+    const double Mr = have ? rec[0] : -INFINITY;
+    const float f = Mr == -INFINITY ? 0.0f : __expf(float(Mr - st->m)) * 0x1p62f;
+    for (int c = 0; c < d; ++c) {
+      const ST v = warp_sum(ST(have ? f * float(rec[1 + c]) : 0.0f));
+      if (lane == 0) static_cast<ST*>(a.xpart)[int64_t(blk) * d + c] = v;
+    }
   }
 }
 

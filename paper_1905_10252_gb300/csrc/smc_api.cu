@@ -43,7 +43,10 @@ Layout layout_for(int64_t n, int d, int m = 0) {
   p = align_up(p + sizeof(TargetDev));
   L.part = p;
   const size_t part_blocks = size_t(std::max(kMaxPartBlocks, L.qblocks));
-  p = align_up(p + part_blocks * (2 + size_t(d < 1 ? 1 : d)) * sizeof(double));
+  p = align_up(p + part_blocks * 2 * sizeof(double));
+  // eq. (7) records of the move kernel, one per 256-particle tile: {M_r, sum e x}
+  L.epart = p;
+  p = align_up(p + size_t(div_up(n, kEstTile)) * (1 + size_t(d < 1 ? 1 : d)) * sizeof(double));
   L.qpart = p;
   p = align_up(p + size_t(L.qblocks) * 5 * sizeof(uint64_t));
   L.cbase = p;
@@ -133,6 +136,7 @@ ParticleArgs particle_args(const smc_sampler* h) {
   a.logpi[1] = h->lp[1];
   a.logw = h->logw;
   a.part = h->part;
+  a.epart = reinterpret_cast<double*>(h->ws + h->L.epart);
   a.tg = h->tg;
   a.st = h->st;
   if (h->cfg.flags & SMC_FLAG_TEST_STALL_LIKELIHOOD) a.flags |= PA_STALL_COPIES;
@@ -158,6 +162,8 @@ QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies) {
   q.dtype = h->dtype;
   q.xpart = h->xpart;
   q.tile_src = h->tile_src;
+  q.epart = reinterpret_cast<const double*>(h->ws + h->L.epart);
+  q.est_src = 0;
   q.nblocks = h->L.qblocks;
   q.ntiles = h->L.ntiles;
   q.st = h->st;
@@ -204,6 +210,12 @@ cudaError_t launch_stats(smc_sampler* h, int set_lse_prev, int nb) {
   return launch_quant_finalize(q, set_lse_prev, h->stream);
 }
 
+// FP32 Gaussian samplers with D <= 16: the fused move/reweight kernel also
+// forms the eq. (7) sums of its blocks (the particles are in its registers),
+// so the quantise pass does not read them again.  (For D > 16 the kernel has
+// no registers to spare.)
+bool est_in_move(const smc_sampler* h) { return h->have_gp && !h->lg_tc && h->d <= 16; }
+
 // Move and reweight of one iteration (Algorithm 2, line 4; eq. (5)); returns
 // the number of max records written.
 cudaError_t launch_move_reweight(smc_sampler* h, const ParticleArgs& a, int* nb) {
@@ -214,7 +226,8 @@ cudaError_t launch_move_reweight(smc_sampler* h, const ParticleArgs& a, int* nb)
     return e;
   }
   *nb = h->grid_p;
-  return launch_particles(OP_MOVE_REWEIGHT, a, h->grid_p, h->threads_p, h->stream, gauss_params(h));
+  return launch_particles(est_in_move(h) ? OP_MOVE_REWEIGHT_EST : OP_MOVE_REWEIGHT, a, h->grid_p, h->threads_p,
+                          h->stream, gauss_params(h));
 }
 
 // One iteration of Algorithm 2 (lines 3-10), all on h->stream.
@@ -224,7 +237,8 @@ cudaError_t launch_iteration(smc_sampler* h, bool with_cov) {
   cudaError_t e = launch_begin(h->st, h->stream);
   if (e == cudaSuccess) e = launch_move_reweight(h, a, &nb);
   if (e == cudaSuccess) e = launch_max_finalize(h->part, nb, h->st, h->stream);
-  const QuantArgs q = quant_args(h, 0, nullptr);
+  QuantArgs q = quant_args(h, 0, nullptr);
+  q.est_src = est_in_move(h) ? 1 : 0;
   if (e == cudaSuccess) e = launch_quant_reduce(q, h->stream);
   if (e == cudaSuccess) e = launch_quant_finalize(q, 0, h->stream);
   if (e == cudaSuccess && with_cov)
@@ -479,7 +493,8 @@ int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host,
   };
   SMC_TRY(h, launch_step_setup(h->st, nullptr, mean_dev, nullptr, nullptr, s));
   const ParticleArgs a = particle_args(h);
-  const QuantArgs q = quant_args(h, 0, nullptr);
+  QuantArgs q = quant_args(h, 0, nullptr);
+  q.est_src = est_in_move(h) ? 1 : 0;
   int nb = 0;
   SMC_TRY(h, rec(0));
   {

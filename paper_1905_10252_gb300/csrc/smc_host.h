@@ -11,7 +11,7 @@ namespace smc {
 
 // Byte offsets of the stateful sampler's workspace.
 struct Layout {
-  size_t st, tg, part, qpart, cbase, xpart, rs, wbuf, tile_src, lg_x, lg_y, lg_img, covpart, total;
+  size_t st, tg, part, epart, qpart, cbase, xpart, rs, wbuf, tile_src, lg_x, lg_y, lg_img, covpart, total;
   int qblocks, ntiles, cov_blocks;
 };
 

@@ -31,6 +31,8 @@ constexpr int kRTile = 2048;          // output rows per block of the redistribu
 constexpr int kRThreads = 256;
 constexpr int kPThreads = 256;        // particle kernels (init / move / reweight)
 constexpr int kFinThreads = 1024;     // single-block finalisers
+constexpr int kEstTile = 256;         // particles per eq. (7) record of the move kernel (one warp tile)
+static_assert(kQTile % kEstTile == 0, "a quantise block covers whole estimate tiles");
 constexpr int kFinBatchThreads = 256; // one finaliser block per sampler of a batch
 
 // Random-stream purposes (third Philox counter word = purpose << 32 | block).
@@ -46,7 +48,7 @@ struct alignas(256) DevState {
   int32_t err;          // first smc_status recorded on the device, 0 if none
   int32_t F;            // fixed-point scale of the weights
   int32_t L;            // bit length of S (ncopies division)
-  int32_t pad0;
+  int32_t w_uniform;    // 1: every log w equals reset_logw (the last iteration resampled)
   double m;             // max_i log w
   double lse;           // LSE_t
   double lse_prev;      // LSE_{t-1} (0 after a reset)
@@ -69,7 +71,7 @@ struct alignas(256) DevState {
   double* fhat_out;
   double* cov_out;
   int32_t want_cov;
-  int32_t pad1;
+  int32_t est_ready;    // 1: this iteration's move kernel wrote the eq. (7) tile records
   unsigned long long survivors;  // particles with ncopies > 0 in the current resampling
   smc_iter_stats last;  // statistics of the last finalised iteration
 };

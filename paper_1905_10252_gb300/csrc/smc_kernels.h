@@ -42,7 +42,7 @@ constexpr int kLgRows = 256;
 constexpr int kLgK = 32;
 constexpr size_t kLgTileBytes = size_t(kLgRows) * kLgK * 2 * 2;
 
-enum { OP_INIT = 0, OP_MOVE = 1, OP_REWEIGHT = 2, OP_MOVE_REWEIGHT = 3 };
+enum { OP_INIT = 0, OP_MOVE = 1, OP_REWEIGHT = 2, OP_MOVE_REWEIGHT = 3, OP_MOVE_REWEIGHT_EST = 4 };
 
 // FP32 Gaussian target passed by value as a kernel parameter (constant bank):
 // the lower triangle of L^-1 packed row by row (row r holds r + 1 entries at
@@ -74,7 +74,8 @@ struct ParticleArgs {
   void* x[2];
   void* logpi[2];
   double* logw;
-  double* part;  // per-block partials (2 + d doubles each)
+  double* part;   // per-block maximum records (2 doubles each)
+  double* epart;  // eq. (7) records {M_r, sum e x} per 256-particle tile (1 + d doubles each)
   const TargetDev* tg;
   DevState* st;
 };
@@ -102,6 +103,11 @@ struct QuantArgs {
   int32_t d;
   int32_t dtype;
   void* xpart;         // nblocks x d partial sums, in the particle dtype
+  // est_src = 1: the reduce pass forms the eq. (7) partials from the move
+  // kernel's tile records (epart) instead of reading x
+  const double* epart;
+  int32_t est_src;
+  int32_t pad2;
 };
 
 // Sequential Nearly Sort (Algorithm 8) as a stable partition (k_nearly_sort.cu).

@@ -387,3 +387,29 @@ def test_full_size_iteration_sampled(nat, orc):
     assert np.array_equal(x2g[ks], x1g[np.searchsorted(csum, ks, side="right")])
     assert np.all(host(S.logw[:: 4097]) == orc.reset_logw(N))
     S.sync()
+
+
+@pytest.mark.parametrize("D", [3, 8, 16])
+def test_fp32_mean_from_move_records_matches_rows(nat, D):
+    """After a resampling iteration every log w is the same, and the fused
+    move kernel forms the eq. (7) sums itself (per 256-particle tile, from
+    the FP32 log pi differences); the piecewise path forms them from the
+    rows in the quantise pass.  Same particles and weights, two summation
+    routes: the means agree to FP32 rounding."""
+    N = 300007
+    mu, Sigma = _gauss(D)
+    kw = dict(dtype=torch.float32, seed=9, mu=mu, sigma=Sigma, resample_mode=nat.RESAMPLE_ALWAYS, step=0.3)
+    a = nat.Sampler(N, D, **kw)
+    b = nat.Sampler(N, D, **kw)
+    for it in range(4):
+        ra = a.step(1)
+        b.move()
+        b.reweight()
+        mb, _ = b.estimate()
+        nc, _ = b.resample()
+        b.redistribute(nc)
+        a.sync()
+        b.sync()
+        assert torch.equal(a.logw, b.logw)
+        scale = 1.0 + mb.abs()
+        assert torch.all((ra["mean"] - mb).abs() <= 1e-5 * scale), (it, ra["mean"], mb)
