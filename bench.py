@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--rate", type=float, default=200.0, help="serve workload: arrivals per second")
     p.add_argument("--logistic-frac", type=float, default=0.1, help="serve workload: share of logistic jobs")
     p.add_argument("--sat-jobs", type=int, default=300, help="serve workload: jobs of the saturated run")
+    p.add_argument("--min-batch", type=int, default=16,
+                   help="serve workload: fewest ready Gaussian jobs that share a batched launch")
     p.add_argument("--count", type=int, default=256, help="batch workload: samplers")
     p.add_argument("--n", type=int, default=1 << 24)
     p.add_argument("--d", type=int, default=16)
@@ -748,10 +750,10 @@ def run_serve(args):
     out = {}
     # warm-up: a short stream through both engines (kernels, allocator, graphs)
     for batched in (True, False):
-        Scheduler(GpuEngine(batched=batched), budget_bytes=budget).run(serve_jobs(40, 400.0, args.logistic_frac, 99))
+        Scheduler(GpuEngine(batched=batched, min_batch=args.min_batch), budget_bytes=budget).run(serve_jobs(40, 400.0, args.logistic_frac, 99))
     for batched in (True, False):
         jobs = serve_jobs(args.jobs, args.rate, args.logistic_frac, seed=rank)
-        eng = GpuEngine(batched=batched)
+        eng = GpuEngine(batched=batched, min_batch=args.min_batch)
         sch = Scheduler(eng, budget_bytes=budget, round_iters=5)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -769,7 +771,7 @@ def run_serve(args):
             jobs = serve_jobs(args.sat_jobs, args.rate, frac, seed=rank + 7)
             for j in jobs:
                 j.arrival = 0.0
-            sch = Scheduler(GpuEngine(batched=batched), budget_bytes=budget, round_iters=5)
+            sch = Scheduler(GpuEngine(batched=batched, min_batch=args.min_batch), budget_bytes=budget, round_iters=5)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             done = sch.run(jobs, t0=t0)
@@ -789,7 +791,7 @@ def run_serve(args):
             "dtype": "f32 state / f64 weights", "data": "synthetic",
             "config": {"workload": f"serve Poisson {args.rate:g} jobs/s x {args.jobs}: gauss (batched workload, "
                                    f"K=50) + {args.logistic_frac:.0%} logistic (N=2^18, M in {{1024,8192}}, D=32, "
-                                   "K=100)", "budget_bytes": budget, "round_iters": 5,
+                                   "K=100)", "budget_bytes": budget, "min_batch": args.min_batch, "round_iters": 5,
                        "parallelism": f"replicas x{ws}"},
             "p50_s": b["p50_s"], "p99_s": b["p99_s"],
             "serving": out,

@@ -285,10 +285,11 @@ int smc_redistribute_raw_noalloc(int64_t n, int32_t row_bytes, const int32_t* nc
  * Members are handles from smc_init with dtype SMC_F32 and target SMC_GAUSS
  * (the FP32 move / reweight kernel), all on the current device, each listed
  * once.  A handle must not be stepped by itself, nor be a member of another
- * batch, while the batch is in use.  smc_batch_create synchronises every
- * member's stream once; afterwards the batch works on its own stream, and
- * smc_batch_sync must return before a member's own calls (smc_read_stats,
- * smc_current, ...) see the batch's results.
+ * batch, while the batch is in use.  smc_batch_create makes the batch's
+ * stream wait (on the device, no host wait) for the work already queued on
+ * every member's stream; afterwards the batch works on its own stream, and
+ * a member's own calls must be ordered after the batch's work (smc_batch_sync,
+ * or the member's stream waiting on the batch's stream) to see its results.
  *
  * ws_dev: smc_batch_ws_bytes(...) bytes of device memory, 256-byte aligned,
  * owned by the caller and alive until smc_batch_destroy.  It holds the

@@ -245,9 +245,22 @@ int smc_batch_create(smc_batch** out, smc_sampler* const* members, int32_t count
   Plan plan = make_plan(members, count, sm_count());
   const BatchLayout L = batch_layout(plan);
   if (ws_bytes < L.total) return bfail(nullptr, SMC_ENOMEM, "workspace too small");
-  for (int s = 0; s < count; ++s) {
-    const cudaError_t e = cudaStreamSynchronize(members[s]->stream);
-    if (e != cudaSuccess) return bfail(nullptr, SMC_ECUDA, std::string("member stream: ") + cudaGetErrorString(e));
+  // the batch's stream waits for the members' queued work (device-side
+  // ordering: one event, recorded on each member stream in turn)
+  {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    const cudaStream_t bs = reinterpret_cast<cudaStream_t>(stream);
+    for (int s = 0; s < count && e == cudaSuccess; ++s) {
+      if (members[s]->stream == bs) continue;
+      e = cudaEventRecord(ev, members[s]->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, ev, 0);
+    }
+    if (ev) {
+      const cudaError_t e2 = cudaEventDestroy(ev);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) return bfail(nullptr, SMC_ECUDA, std::string("member stream order: ") + cudaGetErrorString(e));
   }
   smc_batch* b = new (std::nothrow) smc_batch();
   if (!b) return bfail(nullptr, SMC_ENOMEM, "host allocation failed");

@@ -7,8 +7,11 @@ index t, the Philox key is the job's seed) resident in HBM, and advances all
 resident jobs together in rounds of a few iterations:
 
   * Gaussian FP32 jobs share one batched launch per stage (``native.Batch``,
-    one CUDA graph of the batched iteration); the batch is rebuilt whenever
-    jobs join or leave, between rounds;
+    one CUDA graph of the batched iteration) when at least ``min_batch`` of
+    them are ready together; the batch is rebuilt whenever jobs join or
+    leave, between rounds.  Fewer ready jobs (light load, or arrivals while
+    the batch runs) take one launch per job on their own streams, which
+    starts them at once instead of waiting for the batch's round;
   * logistic-regression jobs run their own iterations (tensor-core
     likelihood) on their own streams, concurrently with the batch;
   * Gaussian work runs on high-priority streams, so that its short kernels
@@ -239,13 +242,14 @@ def poisson_arrivals(count: int, rate: float, seed: int = 0) -> np.ndarray:
 class GpuEngine(Engine):
     """Jobs as libsmc samplers on one GPU (see the module docstring)."""
 
-    def __init__(self, batched: bool = True, device: str = "cuda"):
+    def __init__(self, batched: bool = True, device: str = "cuda", min_batch: int = 16):
         import torch
 
         from . import native
 
         self.torch, self.native = torch, native
         self.batched = batched
+        self.min_batch = max(1, int(min_batch))
         self.device = device
         self.samplers: dict[int, object] = {}
         self.means: dict[int, object] = {}
@@ -301,26 +305,25 @@ class GpuEngine(Engine):
         gauss = [j for j in jobs if j.kind == "gauss"]
         others = [j for j in jobs if j.kind != "gauss"]
         launched = []
-        if self.batched and gauss:
-            if self.batch_busy:
-                # the batch is still running its round: idle Gaussian jobs join
-                # the next one (no batch is split while it runs)
-                gauss = []
-            else:
-                # the batch advances every member by the same count: jobs
-                # needing fewer iterations this round (their last) step alone
-                k = min(iters[j.jid] for j in gauss)
-                full = [j for j in gauss if iters[j.jid] == k]
-                rest = [j for j in gauss if iters[j.jid] != k]
-                b = self._batch_for(full)
-                # outputs in the batch's member order
-                b.step_raw(k, means=[self.means[i] for i in self.batch_ids])
-                ev = torch.cuda.Event()
-                ev.record(self.stream)
-                self.pending.append((ev, [j.jid for j in full], True))
-                self.batch_busy = True
-                launched += [j.jid for j in full]
-                others = rest + others
+        if self.batched and gauss and not self.batch_busy and len(gauss) >= self.min_batch:
+            # the batch advances every member by the same count: jobs needing
+            # fewer iterations this round (their last) step alone
+            k = min(iters[j.jid] for j in gauss)
+            full = [j for j in gauss if iters[j.jid] == k]
+            rest = [j for j in gauss if iters[j.jid] != k]
+            b = self._batch_for(full)
+            # members may have stepped alone since the batch was built: its
+            # stream waits for their streams
+            for i in self.batch_ids:
+                self.stream.wait_stream(self.samplers[i].stream)
+            # outputs in the batch's member order
+            b.step_raw(k, means=[self.means[i] for i in self.batch_ids])
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            self.pending.append((ev, [j.jid for j in full], True))
+            self.batch_busy = True
+            launched += [j.jid for j in full]
+            others = rest + others
         elif gauss:
             others = gauss + others
         for j in others:

@@ -55,12 +55,15 @@ def alone(nat, job):
     return out
 
 
-@pytest.mark.parametrize("batched", [True, False])
-def test_served_results_equal_alone(nat, batched):
+@pytest.mark.parametrize("batched,min_batch", [(True, 1), (True, 4), (False, 1)])
+def test_served_results_equal_alone(nat, batched, min_batch):
+    """min_batch = 1: every ready Gaussian job goes into the batch; 4: the
+    engine alternates between the batch and one launch per job as the number
+    of ready jobs changes (the same samplers step both ways)."""
     from paper_1905_10252_gb300.serve import GpuEngine, Scheduler, latency_summary
 
     jobs = make_jobs()
-    eng = GpuEngine(batched=batched)
+    eng = GpuEngine(batched=batched, min_batch=min_batch)
     need = sum(eng.bytes_needed(j) for j in jobs)
     sch = Scheduler(eng, budget_bytes=need // 3, round_iters=3)
     done = sch.run(jobs)
@@ -80,7 +83,7 @@ def test_cancelled_jobs_leave_the_others_unchanged(nat):
 
     class Canceller(GpuEngine):
         def __init__(self, ids, after):
-            super().__init__(batched=True)
+            super().__init__(batched=True, min_batch=1)
             self.ids, self.after, self.calls, self.sch = ids, after, 0, None
 
         def step(self, jobs, iters):
