@@ -83,6 +83,8 @@ def _declare(L: C.CDLL) -> None:
     L.orc_quantise.argtypes = [C.c_int64, _dp, C.c_double, _u64p, _u64p]
     L.orc_decide.argtypes = [C.c_int64, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int]
     L.orc_decide.restype = C.c_int
+    L.orc_decide_nstar.argtypes = [C.c_int64, C.c_int64, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int]
+    L.orc_decide_nstar.restype = C.c_int
     L.orc_resample_u.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
     L.orc_resample_u.restype = C.c_uint64
     L.orc_systematic.argtypes = [C.c_int64, _u64p, C.c_uint64, C.c_uint64, _i32p, _u32p]
@@ -93,7 +95,7 @@ def _declare(L: C.CDLL) -> None:
     L.orc_resample.argtypes = [C.c_int64, _dp, C.c_uint64, C.c_uint64, C.c_int, _i32p, _u32p, _u64p, _u64p]
     L.orc_resample.restype = C.c_int
     L.orc_run.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_uint64, C.c_double, C.c_double, C.c_int,
-                          C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _i32p]
+                          C.c_int64, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _i32p]
     L.orc_run.restype = C.c_int
 
 
@@ -156,8 +158,10 @@ def quantise(logw, m: float):
     return W, s[0], s[1] | (s[2] << 64), s[3] | (s[4] << 64)
 
 
-def decide(N: int, S: int, sumW2: int, mode: int = RESAMPLE_ESS) -> bool:
-    return bool(lib().orc_decide(N, S, sumW2 & ((1 << 64) - 1), sumW2 >> 64, mode))
+def decide(N: int, S: int, sumW2: int, mode: int = RESAMPLE_ESS, nstar: int = 0) -> bool:
+    """Algorithm 2, line 7: resample iff N_eff = S^2 / sum W^2 < N* (nstar = 0:
+    the paper's N* = N/2)."""
+    return bool(lib().orc_decide_nstar(N, nstar, S, sumW2 & ((1 << 64) - 1), sumW2 >> 64, mode))
 
 
 def resample_u(seed: int, t: int, S: int) -> int:
@@ -323,7 +327,7 @@ def estimate(x, logw, lse: float, with_cov: bool = True):
 
 
 def run(tgt: Target, N: int, seed: int, K: int, init_scale: float = 2.0, step: float = 0.5,
-        mode: int = RESAMPLE_ESS, ubits: int = 53, ncopies_trace: bool = False):
+        mode: int = RESAMPLE_ESS, ubits: int = 53, ncopies_trace: bool = False, nstar: int = 0):
     """Algorithm 2 for K iterations; returns a dict of final state and traces."""
     D = tgt.D
     x = np.zeros((N, D))
@@ -334,7 +338,7 @@ def run(tgt: Target, N: int, seed: int, K: int, init_scale: float = 2.0, step: f
     cov = np.zeros((D, D))
     fhat = np.zeros(D)
     nct = np.zeros((K, N), dtype=np.int32) if ncopies_trace else None
-    rc = lib().orc_run(tgt.h, N, D, seed, init_scale, step, mode, ubits, K, _p(x, C.c_double),
+    rc = lib().orc_run(tgt.h, N, D, seed, init_scale, step, mode, nstar, ubits, K, _p(x, C.c_double),
                        _p(lw, C.c_double), _p(lp, C.c_double), _p(trace, C.c_double), _p(means, C.c_double),
                        _p(cov, C.c_double), _p(fhat, C.c_double),
                        _p(nct, C.c_int32) if nct is not None else None)

@@ -527,15 +527,21 @@ void orc_quantise(int64_t N, const double* logw, double m, uint64_t* W, uint64_t
   sums[4] = (uint64_t)(se >> 64);
 }
 
-/* Resampling decision, eq. (1) against N* = N/2 (Sec. 3.1), taken exactly on
- * the quantised weights: N_eff < N/2  <=>  2 S^2 < N sum W^2.
+/* Resampling decision of Algorithm 2 (line 7: resample iff N_eff < N*), with
+ * N_eff from eq. (1) on the quantised weights, N_eff = S^2 / sum W^2, taken
+ * exactly in integers: N_eff < N*  <=>  S^2 < N* sum W^2.  nstar = 0 selects
+ * the paper's N* = N/2 (Sec. 3.1) as 2 S^2 < N sum W^2, exact for odd N too.
  * mode 0: that rule; 1: always (the worst case of Sec. 5.2); 2: never. */
-int orc_decide(int64_t N, uint64_t S, uint64_t sw2_lo, uint64_t sw2_hi, int mode) {
+int orc_decide_nstar(int64_t N, int64_t nstar, uint64_t S, uint64_t sw2_lo, uint64_t sw2_hi, int mode) {
   if (mode == 1) return 1;
   if (mode == 2) return 0;
   u128 sw2 = ((u128)sw2_hi << 64) | sw2_lo;
-  u128 lhs = (u128)S * S * 2;
-  return lhs < (u128)N * sw2;
+  if (nstar == 0) return (u128)S * S * 2 < (u128)N * sw2;
+  return (u128)S * S < (u128)nstar * sw2;
+}
+
+int orc_decide(int64_t N, uint64_t S, uint64_t sw2_lo, uint64_t sw2_hi, int mode) {
+  return orc_decide_nstar(N, 0, S, sw2_lo, sw2_hi, mode);
 }
 
 /* The systematic offset U in [0, S): U = floor(r S / 2^64), r the first 64-bit
@@ -642,7 +648,7 @@ int orc_resample(int64_t N, const double* logw, uint64_t seed, uint64_t t, int m
  * resolution (53 for the FP64 state, 24 for the FP32 state).  Returns nonzero on
  * failure. */
 int orc_run(const void* tgt, int64_t N, int D, uint64_t seed, double init_scale, double step,
-            int mode, int ubits, int K, double* x, double* logw, double* logpi, double* trace,
+            int mode, int64_t nstar, int ubits, int K, double* x, double* logw, double* logpi, double* trace,
             double* means, double* cov, double* fhat, int32_t* ncopies_trace) {
   size_t nd = (size_t)N * D;
   double* xp = malloc(sizeof(double) * nd);
@@ -674,7 +680,7 @@ int orc_run(const void* tgt, int64_t N, int D, uint64_t seed, double init_scale,
     /* lines 7-9: N_eff and resampling */
     uint64_t sums[5];
     orc_quantise(N, logw, m, W, sums);
-    int did = orc_decide(N, sums[0], sums[1], sums[2], mode);
+    int did = orc_decide_nstar(N, nstar, sums[0], sums[1], sums[2], mode);
     int64_t distinct = 0;
     if (did) {
       uint64_t U = orc_resample_u(seed, (uint64_t)t, sums[0]);

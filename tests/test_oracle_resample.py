@@ -13,6 +13,8 @@ import os
 import numpy as np
 import pytest
 
+from paper_1905_10252_gb300 import inputs
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -170,3 +172,53 @@ def test_redistribute_bytes_any_dtype(orc):
         x = (g.standard_normal((N, D)) * 100).astype(dt)
         nc = np.bincount(g.integers(0, N, N), minlength=N).astype(np.int32)
         np.testing.assert_array_equal(orc.redistribute(nc, x), np.repeat(x, nc, axis=0))
+
+
+def test_decide_threshold_against_exact_rationals(orc):
+    """Algorithm 2, line 7 with a general N*: resample iff N_eff < N*, where
+    N_eff = S^2 / sum W^2 (eq. (1) on the quantised weights), compared with
+    exact rational arithmetic; nstar = 0 is the paper's N* = N/2."""
+    from fractions import Fraction
+
+    g = np.random.default_rng(11)
+    for trial in range(300):
+        N = int(g.integers(1, 40))
+        W = [int(v) for v in g.integers(0, 2 ** 20, size=N)]
+        if trial % 5 == 0:
+            W = [w if g.uniform() < 0.3 else 0 for w in W]
+        if sum(W) == 0:
+            W[0] = 1
+        S, S2 = sum(W), sum(w * w for w in W)
+        neff = Fraction(S * S, S2)
+        assert orc.decide(N, S, S2, nstar=0) == (neff < Fraction(N, 2)), (W,)
+        for nstar in range(1, N + 1):
+            assert orc.decide(N, S, S2, nstar=nstar) == (neff < nstar), (W, nstar)
+
+
+def test_decide_threshold_closed_forms(orc):
+    # equal weights: N_eff = N, never below N* <= N; one-hot: N_eff = 1
+    for N in (1, 2, 7, 1000):
+        for nstar in (1, max(1, N // 2), N):
+            assert not orc.decide(N, N * 5, N * 25, nstar=nstar)
+            assert orc.decide(N, 9, 81, nstar=nstar) == (nstar > 1)
+    # the modes override the threshold
+    assert orc.decide(10, 9, 81, mode=orc.RESAMPLE_NEVER, nstar=10) is False
+    assert orc.decide(10, 50, 250, mode=orc.RESAMPLE_ALWAYS, nstar=1) is True
+
+
+def test_run_threshold_extremes_match_the_modes(orc):
+    """N* = 1 never resamples (N_eff >= 1 always) and N* = N resamples unless
+    every weight is equal: whole runs equal the NEVER and ALWAYS runs."""
+    mu, Sigma = inputs.gaussian_target(3, seed=2)
+    tgt = orc.Target.gauss(mu, Sigma)
+    N, K = 500, 5
+    never = orc.run(tgt, N, 4, K, mode=orc.RESAMPLE_NEVER)
+    always = orc.run(tgt, N, 4, K, mode=orc.RESAMPLE_ALWAYS)
+    low = orc.run(tgt, N, 4, K, nstar=1)
+    high = orc.run(tgt, N, 4, K, nstar=N)
+    for a, b in ((low, never), (high, always)):
+        assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["logw"], b["logw"])
+        assert np.array_equal(a["trace"], b["trace"])
+    # a threshold between gives a decision sequence between the two
+    mid = orc.run(tgt, N, 4, K, nstar=N // 4)
+    assert set(mid["trace"][:, 4]) <= {0.0, 1.0}
