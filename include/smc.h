@@ -53,8 +53,9 @@ typedef enum { SMC_F32 = 1, SMC_F64 = 2 } smc_dtype;
  *  SMC_STUDENT_T  log pi = -(nu+1)/2 log(1 + (x-mu)^2/nu), D = 1 (Sec. 5.2.3, eq. (14)) */
 typedef enum { SMC_GAUSS = 1, SMC_LOGISTIC = 2, SMC_STUDENT_T = 3 } smc_target_kind;
 
-/* When to resample (Sec. 3.1): SMC_RESAMPLE_ESS resamples iff N_eff < N/2,
- * decided exactly on the quantised weights (2 S^2 < N sum W^2);
+/* When to resample (Sec. 3.1): SMC_RESAMPLE_ESS resamples iff N_eff < N*
+ * (smc_config.nstar; N/2 by default), decided exactly on the quantised
+ * weights (2 S^2 < N sum W^2 for N/2);
  * SMC_RESAMPLE_ALWAYS is the worst case of Sec. 5.2 (every iteration). */
 typedef enum { SMC_RESAMPLE_ESS = 0, SMC_RESAMPLE_ALWAYS = 1, SMC_RESAMPLE_NEVER = 2 } smc_resample_mode;
 
@@ -87,6 +88,9 @@ typedef struct {
   int32_t flags;            /* SMC_FLAG_* (0: defaults) */
   double prior_var;         /* LOGISTIC: prior N(0, prior_var I) */
   double nu;                /* STUDENT_T: degrees of freedom */
+  int64_t nstar;            /* SMC_RESAMPLE_ESS threshold N* of Algorithm 2: resample iff
+                               N_eff < N*, decided exactly as S^2 < N* sum W^2; 0..n, and
+                               0 selects the paper's N* = N/2 (2 S^2 < N sum W^2) */
 } smc_config;
 
 typedef struct smc_sampler smc_sampler;

@@ -428,7 +428,9 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
       flag = 1;
     else if (a.mode == SMC_RESAMPLE_NEVER)
       flag = 0;
-    else
+    else if (a.nstar > 0)  // N_eff < N*  <=>  S^2 < N* sum W^2 (Algorithm 2, line 7)
+      flag = u128(S) * S < u128(uint64_t(a.nstar)) * sw2;
+    else  // N* = N/2
       flag = (u128(S) * S * 2) < u128(n) * sw2;
   }
   const P4 r = stream_block(a.seed, uint64_t(st->t), kPurposeResample, 0xFFFFFFFFull, 0);

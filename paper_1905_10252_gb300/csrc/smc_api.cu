@@ -146,6 +146,7 @@ ParticleArgs particle_args(const smc_sampler* h) {
 QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies) {
   QuantArgs q{};
   q.n = h->n;
+  q.nstar = h->cfg.nstar;
   q.logw = h->logw;
   q.seed = h->cfg.seed;
   q.mode = h->cfg.resample_mode;
@@ -280,6 +281,7 @@ int check_config(const smc_config* c) {
     return fail(nullptr, SMC_EINVAL, "Gaussian target needs mu_dev and sigma_dev");
   if (c->target == SMC_STUDENT_T && !c->mu_dev) return fail(nullptr, SMC_EINVAL, "Student-t target needs mu_dev");
   if (c->resample_mode < 0 || c->resample_mode > 2) return fail(nullptr, SMC_EINVAL, "bad resample_mode");
+  if (c->nstar < 0 || c->nstar > c->n) return fail(nullptr, SMC_EINVAL, "nstar must be in [0, n]");
   if (!(c->step >= 0.0) || !(c->init_scale > 0.0)) return fail(nullptr, SMC_EINVAL, "bad step / init_scale");
   return SMC_OK;
 }

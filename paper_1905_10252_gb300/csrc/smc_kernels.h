@@ -82,6 +82,7 @@ struct ParticleArgs {
 
 struct QuantArgs {
   int64_t n;
+  int64_t nstar;       // resampling threshold N* (0: N/2)
   const double* logw;
   uint64_t seed;
   int32_t mode;        // smc_resample_mode

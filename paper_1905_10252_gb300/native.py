@@ -48,6 +48,7 @@ class smc_config(C.Structure):
         ("target", C.c_int32), ("resample_mode", C.c_int32), ("step", C.c_double), ("init_scale", C.c_double),
         ("mu_dev", C.c_void_p), ("sigma_dev", C.c_void_p), ("X_dev", C.c_void_p), ("y_dev", C.c_void_p),
         ("m", C.c_int32), ("flags", C.c_int32), ("prior_var", C.c_double), ("nu", C.c_double),
+        ("nstar", C.c_int64),
     ]
 
 
@@ -254,13 +255,14 @@ class Sampler:
 
     target='gauss' needs mu [D] and sigma [D, D]; target='student_t' needs mu
     (scalar) and nu; target='logistic' needs X [M, D], y [M] and prior_var.
-    dtype is torch.float32 or torch.float64 (particle state).
+    dtype is torch.float32 or torch.float64 (particle state).  nstar is the
+    resampling threshold N* of Algorithm 2 (0: N/2).
     """
 
     def __init__(self, n: int, d: int, *, dtype=torch.float32, seed: int = 0, target: str = "gauss",
                  mu=None, sigma=None, nu: float = 0.0, step: float = 0.5, init_scale: float = 2.0,
                  resample_mode: int = RESAMPLE_ESS, device="cuda", stream: torch.cuda.Stream | None = None,
-                 X=None, y=None, prior_var: float = 4.0, flags: int = 0):
+                 X=None, y=None, prior_var: float = 4.0, flags: int = 0, nstar: int = 0):
         L = lib()
         self.n, self.d, self.dtype = int(n), int(d), dtype
         self.device = torch.device(device)
@@ -273,6 +275,7 @@ class Sampler:
         cfg.seed, cfg.target, cfg.resample_mode = int(seed), kind, int(resample_mode)
         cfg.step, cfg.init_scale, cfg.nu = float(step), float(init_scale), float(nu)
         cfg.flags = int(flags)
+        cfg.nstar = int(nstar)  # resampling threshold N* (0: N/2)
         self.mu = self.sigma = self.X = self.y = None
         if target == "logistic":
             self.X = torch.as_tensor(X, dtype=torch.float32).reshape(-1, d).contiguous().to(self.device)

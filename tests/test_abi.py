@@ -101,7 +101,8 @@ def test_init_rejects_bad_arguments_host_only(built):
            dict(resample_mode=3), dict(step=-1.0), dict(init_scale=0.0), dict(mu_dev=None),
            dict(target=native.SMC_STUDENT_T, d=2, nu=5.0), dict(target=native.SMC_STUDENT_T, nu=0.0, d=1),
            dict(target=native.SMC_LOGISTIC, X_dev=None, y_dev=A, m=10, prior_var=1.0),
-           dict(target=native.SMC_LOGISTIC, X_dev=A, y_dev=A, m=10, prior_var=0.0)]
+           dict(target=native.SMC_LOGISTIC, X_dev=A, y_dev=A, m=10, prior_var=0.0),
+           dict(nstar=-1), dict(nstar=1025)]
     for kw in bad:
         c = cfg(**kw)
         assert L.smc_workspace_bytes(ctypes.byref(c), ctypes.byref(ctypes.c_size_t())) == native.SMC_EINVAL, kw
@@ -114,3 +115,34 @@ def test_init_rejects_bad_arguments_host_only(built):
     L.smc_workspace_bytes(ctypes.byref(c), ctypes.byref(need))
     assert init(c, ws_bytes=need.value - 1) == native.SMC_ENOMEM
     assert b"workspace too small" in L.smc_last_error(None)
+
+
+def test_struct_layouts_match_the_header(built, tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets that
+    a C compiler gives the header's structs (gcc, host only)."""
+    import shutil
+    import subprocess
+
+    from paper_1905_10252_gb300 import native
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"smc_config": native.smc_config, "smc_iter_stats": native.smc_iter_stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "smc.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
+

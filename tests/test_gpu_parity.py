@@ -413,3 +413,35 @@ def test_fp32_mean_from_move_records_matches_rows(nat, D):
         assert torch.equal(a.logw, b.logw)
         scale = 1.0 + mb.abs()
         assert torch.all((ra["mean"] - mb).abs() <= 1e-5 * scale), (it, ra["mean"], mb)
+
+
+@pytest.mark.parametrize("frac", [0.25, 0.75, 1.0])
+def test_fp64_run_with_threshold_nstar(nat, orc, frac):
+    """Algorithm 2 with its threshold input N* (resample iff N_eff < N*):
+    a whole FP64 run against the oracle's with the same N*, decisions and
+    particles bit for bit; N* = N/4 resamples less and 3N/4 more often than
+    the default N/2."""
+    N, D, K = 1024, 4, 12
+    nstar = int(frac * N)
+    mu, Sigma = _gauss(D, seed=0)
+    tgt = orc.Target.gauss(mu, Sigma)
+    ref = orc.run(tgt, N, 3, K, init_scale=2.0, step=0.5, nstar=nstar)
+    S = nat.Sampler(N, D, dtype=torch.float64, seed=3, mu=mu, sigma=Sigma, step=0.5, init_scale=2.0, nstar=nstar)
+    out = S.step(K, trace=True)
+    S.sync()
+    tr = nat.trace_dicts(out["trace"])
+    assert [t["resampled"] for t in tr] == [int(v) for v in ref["trace"][:, 4]]
+    x, lp = S.current()
+    assert np.array_equal(host(x), ref["x"])
+    assert np.array_equal(host(S.logw), ref["logw"])
+    # the decision is N_eff < N* on the quantised weights
+    for t in tr:
+        assert t["resampled"] == int(t["ess"] < nstar) or abs(t["ess"] - nstar) < 1e-9 * nstar
+    S.close()
+
+
+def test_fp32_threshold_rejects_out_of_range(nat):
+    mu, Sigma = _gauss(2)
+    with pytest.raises(nat.SmcError) as e:
+        nat.Sampler(100, 2, dtype=torch.float32, mu=mu, sigma=Sigma, nstar=101)
+    assert e.value.code == nat.SMC_EINVAL
