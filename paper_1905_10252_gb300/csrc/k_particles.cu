@@ -4,12 +4,15 @@
 //   * random-walk move and importance reweighting (Algorithm 2, line 4; eq. (5)),
 //     fused in one pass over the particle rows,
 //   * the per-block maxima of log w (integer-ordered compares, no FP64 pipe),
-//     combined by a single-block finaliser (the weighted mean of eq. (7) is
-//     formed in the quantisation pass, from the fixed-point weights),
+//     combined by a single-block finaliser,
+//   * the sums of eq. (7) for FP32 Gaussian samplers whose iteration starts
+//     from equal weights, one record per 256-particle warp tile (otherwise
+//     the quantisation pass forms them from the fixed-point weights),
 //   * the weighted covariance (diagnostic),
 //   * the iteration bookkeeping kernels (begin / commit, eq. (6) recycling).
 //
-// One thread owns one particle row at a time (grid-stride over N); rows are
+// One thread owns one particle row at a time (grid-stride over N; the FP32
+// Gaussian kernel strides over warp tiles of 256 consecutive rows); rows are
 // read and written with the widest aligned vector the row allows.  The FP64
 // path uses explicitly rounded operations only, in the same order as the
 // paper's definitions, so its results are reproducible bit for bit.

@@ -1,8 +1,10 @@
 // k_resample.cu -- resampling and redistribute on sm_103a.
 //
 //  * Quantisation of the weights to 64-bit fixed point, W_i = E(log w_i - m)
-//    >> (62 - F), with exact 128-bit sums S, sum W^2, sum E (reduce pass), the
-//    N_eff decision 2 S^2 < N sum W^2 (eq. (1) against N* = N/2), LSE_t and
+//    >> (62 - F), with exact 128-bit sums S, sum W^2, sum E (reduce pass; the
+//    partial sums of eq. (7) from the rows, or from the move kernel's tile
+//    records), the N_eff decision S^2 < N* sum W^2 (eq. (1) against the
+//    threshold N* of Algorithm 2; 2 S^2 < N sum W^2 for N* = N/2), LSE_t and
 //    log c_t (eqs. (2), (8)) in a single-block finaliser.
 //  * Systematic resampling (MVR, Algorithm 4 line 1) on the integer CDF:
 //    off_i = floor((N C_{i-1} + U)/S) is the exclusive cumulative sum of
@@ -11,7 +13,7 @@
 //  * Redistribute (Algorithm 5 as the definition of the output): output-tile
 //    parallel gather.  The scan pass writes runstart[off_i] = i for every
 //    survivor (a run of ncopies_i output rows starts at off_i) and the source
-//    row of each tile's first output row; a tile of 4096 output rows loads its
+//    row of each tile's first output row; a tile of 2048 output rows loads its
 //    slice of runstart (resetting it to -1 for the next iteration), a block
 //    max-scan turns it into src(k), and the rows are copied with 16-byte
 //    vector loads/stores.  Every tile does the same bounded work whatever the

@@ -287,7 +287,7 @@ int smc_batch_create(smc_batch** out, smc_sampler* const* members, int32_t count
     const smc_sampler* h = members[s];
     pa[s] = particle_args(h);
     qa[s] = quant_args(h, 0, nullptr);
-    qa[s].est_src = h->d <= 16 ? 1 : 0;  // the batched move kernel writes the eq. (7) block records
+    qa[s].est_src = h->d <= 16 ? 1 : 0;  // the batched move kernel writes the eq. (7) tile records
     ra[s] = redist_args(h, 0);
     gp[s] = h->gp;
     // the copy autotuner's input: an in-place identity copy of buffer 0

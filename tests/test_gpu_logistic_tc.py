@@ -103,3 +103,30 @@ def test_tc_timeout_is_reported_and_the_context_survives(nat):
     r = T.step(2)
     T.sync()
     assert np.all(np.isfinite(host(r["mean"])))
+
+
+def test_tc_full_size_sampled(nat, orc):
+    """The logistic workload at full size, as the benchmark launches it:
+    N = 2^18 particles, M = 8192 rows, D = 32, q_0 = N(0, 4I), step 0.5,
+    iterations replayed from the CUDA graph.  The log-targets of 512 sampled
+    particles (after the moves and resampling) against the oracle's, each
+    computed one by one; the log-weights follow eq. (5) or the reset."""
+    N, D, M, K = 1 << 18, 32, 8192, 3
+    X, y, _ = inputs.logistic_data(M, D, seed=0)
+    tgt = orc.Target.logistic(X.astype(np.float64), y.astype(np.float64), 4.0)
+    S = nat.Sampler(N, D, dtype=torch.float32, seed=11, target="logistic", X=X, y=y, prior_var=4.0, step=0.5,
+                    init_scale=2.0)
+    r = S.step(K, trace=True)
+    S.sync()
+    x, lp = [host(t) for t in S.current()]
+    idx = np.random.default_rng(3).choice(N, size=512, replace=False)
+    ref = tgt.logpi(x[idx].astype(np.float64))
+    err = np.abs(lp[idx] - ref)
+    assert np.all(err <= 2e-5 * (1 + np.abs(ref))), err.max()
+    tr = nat.trace_dicts(r["trace"])
+    assert [t["t"] for t in tr] == [1, 2, 3]
+    lw = host(S.logw)
+    if tr[-1]["resampled"]:
+        assert np.all(lw == lw[0]) and abs(lw[0] + np.log(N)) < 1e-12 * np.log(N)
+    assert np.all(np.isfinite(lw))
+    print(f"full size: max |d log pi| over 512 particles = {err.max():.3e} (|log pi| up to {np.abs(ref).max():.0f})")
