@@ -774,6 +774,30 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute(RedistArgs a) {
   redistribute_body<V, CPR>(a, blockIdx.x, sm);
 }
 
+// ---------------------------------------------------------------- one-block samplers
+// A sampler whose N fits one quantise block (N <= 4096) runs the reduce,
+// finalise and scan passes as one kernel of one block, with the same bodies in
+// the same order (the results are those of the three launches); one whose N
+// fits one copy tile (N <= 2048) runs redistribute and commit as one kernel.
+// For such samplers the launches, not the work, set the iteration's time.
+template <typename ST, int DMAX, bool EST>
+__global__ void __launch_bounds__(kQThreads) k_quant_small(QuantArgs a) {
+  __shared__ QuantReduceSmem sm;
+  quant_reduce_body<ST, DMAX, EST>(a, 0, sm);
+  __syncthreads();  // the block's sums, W and estimate partials are written
+  quant_finalize_body(a, 0);
+  __syncthreads();  // S, U, the decision and the block base are written
+  quant_scan_body(a, 0);
+}
+
+template <typename V, int CPR>
+__global__ void __launch_bounds__(kRThreads) k_redistribute_commit(RedistArgs a, int d, int force_flip, int recycle) {
+  __shared__ RedistSmem sm;
+  redistribute_body<V, CPR>(a, 0, sm);
+  __syncthreads();
+  if (threadIdx.x == 0) commit_one(a.st, d, force_flip, recycle);
+}
+
 // ---------------------------------------------------------------- batched launches
 // One launch per stage for many samplers: block b of the launch runs block
 // map[b].y of sampler map[b].x with that sampler's own arguments, so every
@@ -947,6 +971,44 @@ cudaError_t launch_redistribute(const RedistArgs& a, cudaStream_t s) {
       k_redistribute<uint32_t, 1><<<grid, kRThreads, 0, s>>>(a);
     else
       k_redistribute<uint32_t, 0><<<grid, kRThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename ST>
+static cudaError_t quant_small_t(const QuantArgs& a, cudaStream_t s) {
+  if (!a.x[0] || a.d < 1)
+    k_quant_small<ST, 1, false><<<1, kQThreads, 0, s>>>(a);
+  else if (a.d <= 4)
+    k_quant_small<ST, 4, true><<<1, kQThreads, 0, s>>>(a);
+  else if (a.d <= 8)
+    k_quant_small<ST, 8, true><<<1, kQThreads, 0, s>>>(a);
+  else if (a.d <= 16)
+    k_quant_small<ST, 16, true><<<1, kQThreads, 0, s>>>(a);
+  else
+    k_quant_small<ST, 32, true><<<1, kQThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant_small(const QuantArgs& a, cudaStream_t s) {
+  if (qblocks(a.n) != 1) return cudaErrorInvalidValue;
+  return a.dtype == SMC_F64 ? quant_small_t<double>(a, s) : quant_small_t<float>(a, s);
+}
+
+cudaError_t launch_redistribute_commit(const RedistArgs& a, int d, int force_flip, int recycle, cudaStream_t s) {
+  if (a.n > kRTile) return cudaErrorInvalidValue;
+  const int rb = a.row_bytes;
+  if (rb % 16 == 0) {
+    switch (rb / 16) {
+      case 1: k_redistribute_commit<uint4, 1><<<1, kRThreads, 0, s>>>(a, d, force_flip, recycle); break;
+      case 2: k_redistribute_commit<uint4, 2><<<1, kRThreads, 0, s>>>(a, d, force_flip, recycle); break;
+      case 4: k_redistribute_commit<uint4, 4><<<1, kRThreads, 0, s>>>(a, d, force_flip, recycle); break;
+      default: k_redistribute_commit<uint4, 0><<<1, kRThreads, 0, s>>>(a, d, force_flip, recycle); break;
+    }
+  } else if (rb % 8 == 0) {
+    k_redistribute_commit<uint2, 0><<<1, kRThreads, 0, s>>>(a, d, force_flip, recycle);
+  } else {
+    k_redistribute_commit<uint32_t, 0><<<1, kRThreads, 0, s>>>(a, d, force_flip, recycle);
   }
   return cudaGetLastError();
 }

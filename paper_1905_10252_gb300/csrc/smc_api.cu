@@ -240,13 +240,24 @@ cudaError_t launch_iteration(smc_sampler* h, bool with_cov) {
   if (e == cudaSuccess) e = launch_max_finalize(h->part, nb, h->st, h->stream);
   QuantArgs q = quant_args(h, 0, nullptr);
   q.est_src = est_in_move(h) ? 1 : 0;
-  if (e == cudaSuccess) e = launch_quant_reduce(q, h->stream);
-  if (e == cudaSuccess) e = launch_quant_finalize(q, 0, h->stream);
+  // (a sampler of one quantise block / one copy tile: the same bodies fused
+  // into fewer launches; the covariance reads nothing the scan writes)
+  const bool one_q = h->L.qblocks == 1, one_r = h->L.ntiles == 1;
+  if (one_q) {
+    if (e == cudaSuccess) e = launch_quant_small(q, h->stream);
+  } else {
+    if (e == cudaSuccess) e = launch_quant_reduce(q, h->stream);
+    if (e == cudaSuccess) e = launch_quant_finalize(q, 0, h->stream);
+  }
   if (e == cudaSuccess && with_cov)
     e = launch_cov(a, nullptr, reinterpret_cast<double*>(h->ws + h->L.covpart), h->L.cov_blocks, h->stream);
-  if (e == cudaSuccess) e = launch_quant_scan(q, h->stream);
-  if (e == cudaSuccess) e = launch_redistribute(redist_args(h, 0), h->stream);
-  if (e == cudaSuccess) e = launch_commit(h->st, h->d, 0, 1, h->stream);
+  if (!one_q && e == cudaSuccess) e = launch_quant_scan(q, h->stream);
+  if (one_r) {
+    if (e == cudaSuccess) e = launch_redistribute_commit(redist_args(h, 0), h->d, 0, 1, h->stream);
+  } else {
+    if (e == cudaSuccess) e = launch_redistribute(redist_args(h, 0), h->stream);
+    if (e == cudaSuccess) e = launch_commit(h->st, h->d, 0, 1, h->stream);
+  }
   return e;
 }
 

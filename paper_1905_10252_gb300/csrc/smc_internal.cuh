@@ -390,4 +390,34 @@ __device__ __forceinline__ long long warp_max_ll(long long v) {
 }
 
 
+// ---------------------------------------------------------------- end of an iteration
+// Ends iteration t: swap buffers if resampled (or if forced by an explicit
+// redistribute), LSE_{t} becomes the next LSE_{t-1} (0 after a reset), and
+// the recycling sums of eq. (6) take f_t with weight c_t.
+__device__ __forceinline__ void commit_one(DevState* st, int d, int force_flip, int recycle) {
+  const bool flip = force_flip || (st->flag && !st->err);
+  if (recycle && !st->err) {
+    const double lc = st->logc;
+    const double M = fmax(st->rc_max, lc);
+    const double sc = (st->rc_max == -INFINITY) ? 0.0 : exp(st->rc_max - M);
+    const double e = exp(lc - M);
+    st->rc_den = st->rc_den * sc + e;
+    for (int c = 0; c < d; ++c) st->rc_num[c] = st->rc_num[c] * sc + e * st->mean[c];
+    st->rc_max = M;
+    if (st->fhat_out)
+      for (int c = 0; c < d; ++c) st->fhat_out[c] = st->rc_num[c] / st->rc_den;
+  }
+  if (st->flag && !st->err) {
+    st->last.survivors = (int64_t)st->survivors;
+    if (st->trace) {
+      const int64_t idx = st->t - st->trace_t0 - 1;
+      if (idx >= 0) st->trace[idx].survivors = (int64_t)st->survivors;
+    }
+  }
+  if (flip) st->cur ^= 1;
+  st->lse_prev = flip ? 0.0 : st->lse;
+  // a resampled iteration leaves every log w at reset_logw
+  st->w_uniform = (flip && !st->err) ? 1 : 0;
+}
+
 }  // namespace smc

@@ -211,6 +211,10 @@ cudaError_t launch_nc_reduce(const NcScanArgs& a, cudaStream_t s);
 cudaError_t launch_nc_finalize(const NcScanArgs& a, cudaStream_t s);
 cudaError_t launch_nc_scan(const NcScanArgs& a, cudaStream_t s);
 cudaError_t launch_redistribute(const RedistArgs& a, cudaStream_t s);
+// one-block samplers: quantise reduce + finalise + scan (N <= 4096), and
+// redistribute + commit (N <= 2048), each as one launch
+cudaError_t launch_quant_small(const QuantArgs& a, cudaStream_t s);
+cudaError_t launch_redistribute_commit(const RedistArgs& a, int d, int force_flip, int recycle, cudaStream_t s);
 int nearly_sort_tiles(int64_t n);
 cudaError_t launch_nearly_sort(const NearlySortArgs& a, cudaStream_t s);
 cudaError_t launch_state_init(DevState* st, int64_t n, int64_t t, int F, cudaStream_t s);
