@@ -449,56 +449,75 @@ __device__ __forceinline__ void load_seg(const float* __restrict__ row, bool vec
 // launches).  row(r, dv) = sum_{c <= r} P[r][c] dv[c], accumulated with one
 // FMA per term in the order c = 0, 1, ..., r in both cases, so both give the
 // same bits.
+// Packed two-lane FP32 arithmetic (sm_100 family): each lane of fma.rn.f32x2
+// is an IEEE fused multiply-add rounded to nearest, bit for bit the fmaf of
+// that lane, so pairing changes no result, only the instruction count.
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return make_float2(a, b);
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 struct FactorParam {
   const GaussParamsF32& g;
   __device__ __forceinline__ float mu(int c) const { return g.mu[c]; }
+  // rows r and r + 1 (r even) at once, from the interleaved copy: the same
+  // FMAs in the same order per row (row r's extra term at c = r + 1 has a
+  // zero coefficient and adds +0)
   template <int DMAX>
-  __device__ __forceinline__ float row(int r, const float (&dv)[DMAX]) const {
-    float acc = 0.0f;
+  __device__ __forceinline__ float2 row2(int r, const uint64_t (&dd)[DMAX]) const {
+    uint64_t acc = 0;
 #pragma unroll
     for (int c = 0; c < DMAX; ++c)
-      if (c <= r) acc = fmaf(g.P[r * (r + 1) / 2 + c], dv[c], acc);
-    return acc;
+      if (c <= r + 1) acc = ffma2(*reinterpret_cast<const uint64_t*>(&g.P2[(r / 2) * kTgtMaxD + c]), dd[c], acc);
+    return unpack2(acc);
   }
 };
 
-// Shared-memory layout of the factor: row r starts at float offset
-// padded_row_start(r) (a multiple of 4) and is zero-padded to a multiple of 4
-// entries, so that it is read with 16-byte loads.
-__host__ __device__ constexpr int padded_row_start(int r) {
-  int o = 0;
-  for (int k = 0; k < r; ++k) o += (k + 4) / 4 * 4;
-  return o;
-}
-constexpr int kPaddedFactor = padded_row_start(kTgtMaxD);
+
+// Shared-memory layout of the factor for batched launches: the interleaved
+// row pairs of GaussParamsF32::P2, pair p (rows 2p, 2p + 1) holding columns
+// 0 .. 2p + 1 from float2 offset p (p + 1), read with 16-byte loads.
+constexpr int kPairedFactor = (kTgtMaxD / 2) * (kTgtMaxD / 2 + 1);  // float2 entries
 
 struct FactorSmem {
-  const float4* p;
+  static constexpr bool kPaired = true;
+  const float4* p;  // the pairs, two columns per 16-byte load
   const float* m;
   __device__ __forceinline__ float mu(int c) const { return m[c]; }
   template <int DMAX>
-  __device__ __forceinline__ float row(int r, const float (&dv)[DMAX]) const {
-    float acc = 0.0f;
-    const float4* rp = p + padded_row_start(r) / 4;
+  __device__ __forceinline__ float2 row2(int r, const uint64_t (&dd)[DMAX]) const {
+    const int pr = r / 2;
+    const float4* rp = p + pr * (pr + 1) / 2;
+    uint64_t acc = 0;
 #pragma unroll
-    for (int j = 0; j < (DMAX + 3) / 4; ++j) {
-      if (4 * j <= r) {
+    for (int j = 0; j < DMAX / 2; ++j) {
+      if (j <= pr) {
         const float4 v = rp[j];
-        const float e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (4 * j + u <= r && 4 * j + u < DMAX) acc = fmaf(e[u], dv[4 * j + u], acc);
+        acc = ffma2(pack2(v.x, v.y), dd[2 * j], acc);
+        acc = ffma2(pack2(v.z, v.w), dd[2 * j + 1], acc);
       }
     }
-    return acc;
+    return unpack2(acc);
   }
 };
 
-// Stages rows < d into the padded row layout of FactorSmem.
-__device__ __forceinline__ void stage_rows(const float* __restrict__ P, const float* __restrict__ mu, int d,
-                                           float* pr, float* m) {
-  for (int r = threadIdx.x; r < d; r += blockDim.x)
-    for (int c = 0; c <= r; ++c) pr[padded_row_start(r) + c] = P[r * (r + 1) / 2 + c];
+// Stages the row pairs of rows < d into the layout of FactorSmem.
+__device__ __forceinline__ void stage_pairs(const float2* __restrict__ P2, const float* __restrict__ mu, int d,
+                                            float2* pr, float* m) {
+  const int np = (d + 1) / 2;
+  for (int q = threadIdx.x; q < np; q += blockDim.x)
+    for (int c = 0; c <= 2 * q + 1; ++c) pr[q * (q + 1) + c] = P2[q * kTgtMaxD + c];
   for (int c = threadIdx.x; c < kTgtMaxD; c += blockDim.x) m[c] = mu[c];
 }
 
@@ -668,12 +687,18 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       float dv[DMAX];
 #pragma unroll
       for (int c = 0; c < DMAX; ++c) dv[c] = xo[c] - gp.mu(c);
+      // rows 2p and 2p + 1 advance together in packed two-lane FMAs, each
+      // row's terms in column order (as a scalar loop would add them)
       float qs = 0.0f;
+      uint64_t dd[DMAX];
 #pragma unroll
-      for (int rr = 0; rr < DMAX; ++rr) {
+      for (int c = 0; c < DMAX; ++c) dd[c] = pack2(dv[c], dv[c]);
+#pragma unroll
+      for (int rr = 0; rr < DMAX; rr += 2) {
         if (rr < d) {
-          const float acc = gp.row(rr, dv);
-          qs = fmaf(acc, acc, qs);
+          const float2 acc = gp.row2(rr, dd);
+          qs = fmaf(acc.x, acc.x, qs);
+          if (rr + 1 < d) qs = fmaf(acc.y, acc.y, qs);
         }
       }
       // eq. (5): the log-target difference in FP32 (exact when the two
@@ -735,9 +760,9 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_batch(const Part
                                                                      const int4* __restrict__ map) {
   const int4 m = map[blockIdx.x];
   const ParticleArgs a = pa[m.x];
-  __shared__ float4 sfac[kPaddedFactor / 4];
+  __shared__ float4 sfac[kPairedFactor / 2];
   __shared__ float smu[kTgtMaxD];
-  stage_rows(gps[m.x].P, gps[m.x].mu, a.d, reinterpret_cast<float*>(sfac), smu);
+  stage_pairs(gps[m.x].P2, gps[m.x].mu, a.d, reinterpret_cast<float2*>(sfac), smu);
   __syncthreads();
   const FactorSmem fs{sfac, smu};
   if (a.d <= 8)

@@ -396,9 +396,11 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
     if (e == cudaSuccess) e = cudaMemcpyAsync(muf, h->tg->muf, sizeof muf, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) {
-      for (int r = 0; r < kTgtMaxD; ++r)
-        for (int c = 0; c <= r; ++c) h->gp.P[r * (r + 1) / 2 + c] = Pf[r * kTgtMaxD + c];
       for (int c = 0; c < kTgtMaxD; ++c) h->gp.mu[c] = muf[c];
+      for (int p = 0; p < kTgtMaxD / 2; ++p)
+        for (int c = 0; c < kTgtMaxD; ++c)
+          h->gp.P2[p * kTgtMaxD + c] = make_float2(c <= 2 * p ? Pf[2 * p * kTgtMaxD + c] : 0.0f,
+                                                   c <= 2 * p + 1 ? Pf[(2 * p + 1) * kTgtMaxD + c] : 0.0f);
       h->have_gp = true;
     }
   }

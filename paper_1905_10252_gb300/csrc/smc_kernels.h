@@ -47,9 +47,13 @@ enum { OP_INIT = 0, OP_MOVE = 1, OP_REWEIGHT = 2, OP_MOVE_REWEIGHT = 3, OP_MOVE_
 // FP32 Gaussian target passed by value as a kernel parameter (constant bank):
 // the lower triangle of L^-1 packed row by row (row r holds r + 1 entries at
 // r (r + 1) / 2) and mu.
+// The FP32 Gaussian target of the move / reweight kernels: mu and the
+// inverse Cholesky factor P = L^-1 with rows 2p and 2p + 1 interleaved,
+// P2[p][c] = {P[2p][c], P[2p+1][c]} (zero above the diagonal), so that one
+// packed two-lane FMA advances both rows.
 struct GaussParamsF32 {
-  float P[kTgtMaxD * (kTgtMaxD + 1) / 2];
   float mu[kTgtMaxD];
+  float2 P2[kTgtMaxD / 2 * kTgtMaxD];
 };
 
 // Lanes that share one particle in the move / reweight kernels: one in every
