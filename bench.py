@@ -499,7 +499,7 @@ def run_redistribute(args):
             lw = inputs.one_hot_log_weights(n, 0) if case == "onehot" else inputs.log_weights(n, float(case[1:]), 0)
             lwd = torch.as_tensor(lw, device="cuda")
             nc = torch.empty(n, dtype=torch.int32, device="cuda")
-            res_ms, red_ms, ns_ms, nr_ms = [], [], [], []
+            res_ms, red_ms, ns_ms, nr_ms, copy_ms = [], [], [], [], []
             for it in range(args.warmup + 20):
                 flush.zero_()  # L2 flush between iterations
                 a, b, c = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -508,8 +508,9 @@ def run_redistribute(args):
                 b.record()
                 flush.zero_()
                 b2 = torch.cuda.Event(enable_timing=True)
+                evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
                 b2.record()
-                native.smc_redistribute_raw(nc, x, out, ws=wsb)
+                native.smc_redistribute_raw_profile(nc, x, out, wsb, evs)
                 c.record()
                 flush.zero_()
                 e0, e1, e2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -522,6 +523,7 @@ def run_redistribute(args):
                 if it >= args.warmup:
                     res_ms.append(a.elapsed_time(b))
                     red_ms.append(b2.elapsed_time(c))
+                    copy_ms.append(evs[1].elapsed_time(evs[2]))
                     ns_ms.append(e0.elapsed_time(e1))
                     nr_ms.append(e0.elapsed_time(e2))
             nnz = int((nc > 0).sum().item())
@@ -530,11 +532,16 @@ def run_redistribute(args):
             ns_bytes = 8 * n + 2 * row_bytes * n
             rm, dm = statistics.median(res_ms), statistics.median(red_ms)
             sm_, nm = statistics.median(ns_ms), statistics.median(nr_ms)
+            cm = statistics.median(copy_ms)
+            # the copy kernel alone: run starts 4 B per row, distinct source rows, N rows written
+            copy_bytes = 4 * n + row_bytes * nnz + row_bytes * n
             line = {"metric": "redistribute GB/s", "workload": f"resample+redistribute N=2^{int(np.log2(n))} {case}",
                     "n": n, "d": d, "survivors": nnz, "resample_ms": rm, "redistribute_ms": dm,
                     "redistribute_gbs": red_bytes / (dm * 1e-3) / 1e9, "resample_gbs": res_bytes / (rm * 1e-3) / 1e9,
                     "peak_gbs": peak, "peak_kind": peak_kind,
                     "redistribute_frac": red_bytes / (dm * 1e-3) / 1e9 / peak,
+                    "copy_kernel_ms": cm, "copy_kernel_gbs": copy_bytes / (cm * 1e-3) / 1e9,
+                    "copy_kernel_frac": copy_bytes / (cm * 1e-3) / 1e9 / peak,
                     "nearly_sort_ms": sm_, "nearly_sort_gbs": ns_bytes / (sm_ * 1e-3) / 1e9,
                     "nearly_sort_frac": ns_bytes / (sm_ * 1e-3) / 1e9 / peak,
                     "nr_ms": nm, "nr_over_gather": nm / dm, "timing": "median of 20, L2 flushed"}

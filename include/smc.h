@@ -223,6 +223,13 @@ const char* smc_last_error(const smc_sampler* h);
 int smc_redistribute_ws_bytes(int64_t n, size_t* bytes);
 int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
                          void* out_dev, void* ws_dev, smc_stream_t stream);
+/* The same call with caller events (cudaEvent_t, n_events = 3, or 0 for
+ * none) recorded on stream before it, after the exclusive scan of ncopies
+ * (run starts and tile starts written), and after the row copy: the copy
+ * kernel's own time is the interval between events 1 and 2. */
+int smc_redistribute_raw_profile(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
+                                 void* out_dev, void* ws_dev, smc_stream_t stream, void* const* events_host,
+                                 int32_t n_events);
 
 /* Stateless resampling (Algorithm 4, line 1) of logw_dev[n] with Philox
  * (seed, t): writes ncopies_dev[n] and, when stats_dev is not NULL, one

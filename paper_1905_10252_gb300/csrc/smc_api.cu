@@ -626,18 +626,26 @@ int smc_redistribute_ws_bytes(int64_t n, size_t* bytes) {
   return SMC_OK;
 }
 
-int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
-                         void* out_dev, void* ws_dev, smc_stream_t stream) {
-  SMC_RANGE("smc_redistribute_raw");
+namespace {
+
+// Algorithm 5 on raw rows; with n_events = 3, caller events are recorded
+// before the call, after the ncopies scan, and after the copy.
+int redistribute_raw_impl(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
+                          void* out_dev, void* ws_dev, smc_stream_t stream, void* const* events_host,
+                          int32_t n_events) {
   if (n < 1 || n > 2147483647LL) return fail(nullptr, SMC_EINVAL, "n must be in [1, 2^31)");
   if (row_bytes < 4 || row_bytes % 4) return fail(nullptr, SMC_EINVAL, "row_bytes must be a positive multiple of 4");
   if (!ncopies_dev || !in_dev || !out_dev || !ws_dev) return fail(nullptr, SMC_EINVAL, "null pointer");
   if (!aligned(ws_dev, kAlign)) return fail(nullptr, SMC_EINVAL, "workspace must be 256-byte aligned");
+  if (n_events != 0 && (n_events != 3 || !events_host)) return fail(nullptr, SMC_EINVAL, "n_events must be 0 or 3");
   const size_t va = row_bytes % 16 == 0 ? 16 : (row_bytes % 8 == 0 ? 8 : 4);
   if (!aligned(in_dev, va) || !aligned(out_dev, va)) return fail(nullptr, SMC_EINVAL, "rows misaligned");
   const RawLayout L = raw_layout(n);
   char* ws = static_cast<char*>(ws_dev);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto rec = [&](int j) -> cudaError_t {
+    return n_events ? cudaEventRecord(static_cast<cudaEvent_t>(events_host[j]), s) : cudaSuccess;
+  };
   DevState* st = reinterpret_cast<DevState*>(ws + L.st);
   NcScanArgs a{};
   a.n = n;
@@ -662,14 +670,32 @@ int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_de
   r.logw = nullptr;
   r.st = st;
   r.stateful = 0;
-  cudaError_t e = cudaMemsetAsync(&st->err, 0, sizeof(int32_t), s);
+  cudaError_t e = rec(0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&st->err, 0, sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.runstart, 0xFF, size_t(n) * sizeof(int32_t), s);
   if (e == cudaSuccess) e = launch_nc_reduce(a, s);
   if (e == cudaSuccess) e = launch_nc_finalize(a, s);
   if (e == cudaSuccess) e = launch_nc_scan(a, s);
+  if (e == cudaSuccess) e = rec(1);
   if (e == cudaSuccess) e = launch_redistribute(r, s);
+  if (e == cudaSuccess) e = rec(2);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "smc_redistribute_raw");
   return SMC_OK;
+}
+
+}  // namespace
+
+int smc_redistribute_raw(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
+                         void* out_dev, void* ws_dev, smc_stream_t stream) {
+  SMC_RANGE("smc_redistribute_raw");
+  return redistribute_raw_impl(n, row_bytes, ncopies_dev, in_dev, out_dev, ws_dev, stream, nullptr, 0);
+}
+
+int smc_redistribute_raw_profile(int64_t n, int32_t row_bytes, const int32_t* ncopies_dev, const void* in_dev,
+                                 void* out_dev, void* ws_dev, smc_stream_t stream, void* const* events_host,
+                                 int32_t n_events) {
+  SMC_RANGE("smc_redistribute_raw_profile");
+  return redistribute_raw_impl(n, row_bytes, ncopies_dev, in_dev, out_dev, ws_dev, stream, events_host, n_events);
 }
 
 int smc_resample_raw(int64_t n, const double* logw_dev, uint64_t seed, uint64_t t, int32_t mode,

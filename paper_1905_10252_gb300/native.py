@@ -28,7 +28,7 @@ EXPORTED = [
     "smc_redistribute_raw_noalloc", "smc_batch_ws_bytes", "smc_batch_create", "smc_batch_step",
     "smc_batch_step_profile", "smc_batch_set_variant", "smc_batch_tune", "smc_batch_sync", "smc_batch_destroy", "smc_batch_last_error",
     "smc_checkpoint_bytes", "smc_checkpoint_save", "smc_checkpoint_load",
-    "smc_nearly_sort_ws_bytes", "smc_nearly_sort_raw",
+    "smc_nearly_sort_ws_bytes", "smc_nearly_sort_raw", "smc_redistribute_raw_profile",
 ]
 
 BATCH_MOVE_VARIANTS, BATCH_COPY_VARIANTS = 5, 3  # SMC_BATCH_MOVE_VARIANTS, SMC_BATCH_COPY_VARIANTS
@@ -119,6 +119,7 @@ def _declare(L: C.CDLL) -> None:
     L.smc_batch_destroy.argtypes = [vp]
     L.smc_batch_last_error.argtypes = [vp]
     L.smc_batch_last_error.restype = C.c_char_p
+    L.smc_redistribute_raw_profile.argtypes = [i64, i32, vp, vp, vp, vp, vp, C.POINTER(vp), i32]
     L.smc_nearly_sort_ws_bytes.argtypes = [i64, C.POINTER(sz)]
     L.smc_nearly_sort_raw.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp]
     L.smc_checkpoint_bytes.argtypes = [vp, C.POINTER(sz)]
@@ -149,6 +150,13 @@ def _stream_ptr(stream) -> int | None:
     if stream is None:
         stream = torch.cuda.current_stream()
     return stream.cuda_stream or None
+
+
+def _event_handle(e: torch.cuda.Event) -> int:
+    """The cudaEvent_t of a torch event (torch creates it at its first record)."""
+    if not e.cuda_event:
+        e.record(torch.cuda.current_stream())
+    return e.cuda_event
 
 
 def _alloc_ws(nbytes: int, device) -> torch.Tensor:
@@ -203,6 +211,18 @@ def smc_nearly_sort_raw(ncopies: torch.Tensor, x_in: torch.Tensor, ncopies_out: 
     _check(lib().smc_nearly_sort_raw(n, row_bytes, _ptr(ncopies), _ptr(x_in), _ptr(ncopies_out), _ptr(x_out),
                                      _ptr(ws), _stream_ptr(stream)))
     return ncopies_out, x_out
+
+
+def smc_redistribute_raw_profile(ncopies: torch.Tensor, x_in: torch.Tensor, x_out: torch.Tensor, ws: torch.Tensor,
+                                 events, stream=None) -> torch.Tensor:
+    """smc_redistribute_raw with three caller events: before, after the
+    ncopies scan, after the row copy."""
+    n = ncopies.numel()
+    row_bytes = x_in[0].numel() * x_in.element_size() if n else 0
+    arr = (C.c_void_p * 3)(*[_event_handle(e) for e in events])
+    _check(lib().smc_redistribute_raw_profile(n, row_bytes, _ptr(ncopies), _ptr(x_in), _ptr(x_out), _ptr(ws),
+                                              _stream_ptr(stream), arr, 3))
+    return x_out
 
 
 def smc_resample_raw(logw: torch.Tensor, seed: int, t: int, mode: int = RESAMPLE_ESS,
@@ -351,7 +371,7 @@ class Sampler:
     def step_profile(self, events=None, mean: torch.Tensor | None = None):
         """One iteration with 8 caller-created CUDA events recorded around its stages."""
         if events is not None:
-            arr = (C.c_void_p * 8)(*[e.cuda_event for e in events])
+            arr = (C.c_void_p * 8)(*[_event_handle(e) for e in events])
             n = 8
         else:
             arr, n = None, 0
@@ -462,7 +482,7 @@ class Batch:
     def step_profile(self, events=None):
         """One batched iteration with 8 caller-created CUDA events around its stages."""
         if events is not None:
-            arr, n = (C.c_void_p * 8)(*[e.cuda_event for e in events]), 8
+            arr, n = (C.c_void_p * 8)(*[_event_handle(e) for e in events]), 8
         else:
             arr, n = None, 0
         self._enter()

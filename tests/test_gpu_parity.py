@@ -445,3 +445,20 @@ def test_fp32_threshold_rejects_out_of_range(nat):
     with pytest.raises(nat.SmcError) as e:
         nat.Sampler(100, 2, dtype=torch.float32, mu=mu, sigma=Sigma, nstar=101)
     assert e.value.code == nat.SMC_EINVAL
+
+
+def test_redistribute_raw_profile_same_output(nat, orc):
+    """The profiled stateless call writes the same rows as the plain one and
+    records its three events in order (scan before copy)."""
+    N = 100003
+    nc = inputs.composition(N, seed=21)
+    x = np.random.default_rng(22).standard_normal((N, 16)).astype(np.float32)
+    ncd, xd = torch.as_tensor(nc, device="cuda"), torch.as_tensor(x, device="cuda")
+    ws = torch.empty(nat.smc_redistribute_ws_bytes(N), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(xd)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    nat.smc_redistribute_raw_profile(ncd, xd, out, ws, evs)
+    torch.cuda.synchronize()
+    assert nat.smc_ws_status(ws) == nat.SMC_OK
+    assert np.array_equal(out.cpu().numpy(), orc.redistribute(nc, x))
+    assert evs[0].elapsed_time(evs[1]) >= 0 and evs[1].elapsed_time(evs[2]) > 0
