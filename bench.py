@@ -78,6 +78,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sizes", default="16,20,24", help="redistribute workload: log2 N values")
     p.add_argument("--cases", default="s0.5,s2,s8,onehot", help="redistribute workload: weight cases")
+    p.add_argument("--seeds", default="0,1,2,3,4", help="redistribute workload: input seeds")
     return p.parse_args()
 
 
@@ -495,56 +496,64 @@ def run_redistribute(args):
                                     torch.empty_like(x))
         wsn = torch.empty(native.smc_nearly_sort_ws_bytes(n), dtype=torch.uint8, device="cuda")
         row_bytes = d * 4
+        seeds = [int(v) for v in args.seeds.split(",")]
         for case in args.cases.split(","):
-            lw = inputs.one_hot_log_weights(n, 0) if case == "onehot" else inputs.log_weights(n, float(case[1:]), 0)
-            lwd = torch.as_tensor(lw, device="cuda")
             nc = torch.empty(n, dtype=torch.int32, device="cuda")
-            res_ms, red_ms, ns_ms, nr_ms, copy_ms = [], [], [], [], []
-            for it in range(args.warmup + 20):
-                flush.zero_()  # L2 flush between iterations
-                a, b, c = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                a.record()
-                native.smc_resample_raw(lwd, 0, it + 1, native.RESAMPLE_ALWAYS, ncopies=nc, ws=wsb)
-                b.record()
-                flush.zero_()
-                b2 = torch.cuda.Event(enable_timing=True)
-                evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                b2.record()
-                native.smc_redistribute_raw_profile(nc, x, out, wsb, evs)
-                c.record()
-                flush.zero_()
-                e0, e1, e2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                e0.record()
-                native.smc_nearly_sort_raw(nc, x, ns_keys, ns_rows, ws=wsn)
-                e1.record()
-                native.smc_redistribute_raw(ns_keys, ns_rows, nr_out, ws=wsb)
-                e2.record()
-                torch.cuda.synchronize()
-                if it >= args.warmup:
-                    res_ms.append(a.elapsed_time(b))
-                    red_ms.append(b2.elapsed_time(c))
-                    copy_ms.append(evs[1].elapsed_time(evs[2]))
-                    ns_ms.append(e0.elapsed_time(e1))
-                    nr_ms.append(e0.elapsed_time(e2))
-            nnz = int((nc > 0).sum().item())
-            red_bytes = 4 * n + row_bytes * nnz + row_bytes * n
-            res_bytes = 8 * n + 8 * n + 4 * n
-            ns_bytes = 8 * n + 2 * row_bytes * n
-            rm, dm = statistics.median(res_ms), statistics.median(red_ms)
-            sm_, nm = statistics.median(ns_ms), statistics.median(nr_ms)
-            cm = statistics.median(copy_ms)
-            # the copy kernel alone: run starts 4 B per row, distinct source rows, N rows written
-            copy_bytes = 4 * n + row_bytes * nnz + row_bytes * n
+            # per timed iteration: (ms, algorithmic bytes) of each measured part
+            res, red, cop, nsr, nr = [], [], [], [], []
+            survivors = []
+            for seed in seeds:
+                lw = (inputs.one_hot_log_weights(n, seed) if case == "onehot"
+                      else inputs.log_weights(n, float(case[1:]), seed))
+                lwd = torch.as_tensor(lw, device="cuda")
+                for it in range(args.warmup + 20):
+                    flush.zero_()  # L2 flush between iterations
+                    a, b, c = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    a.record()
+                    native.smc_resample_raw(lwd, seed, it + 1, native.RESAMPLE_ALWAYS, ncopies=nc, ws=wsb)
+                    b.record()
+                    flush.zero_()
+                    b2 = torch.cuda.Event(enable_timing=True)
+                    evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    b2.record()
+                    native.smc_redistribute_raw_profile(nc, x, out, wsb, evs)
+                    c.record()
+                    flush.zero_()
+                    e0, e1, e2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    e0.record()
+                    native.smc_nearly_sort_raw(nc, x, ns_keys, ns_rows, ws=wsn)
+                    e1.record()
+                    native.smc_redistribute_raw(ns_keys, ns_rows, nr_out, ws=wsb)
+                    e2.record()
+                    torch.cuda.synchronize()
+                    if it >= args.warmup:
+                        nnz = int((nc > 0).sum().item())
+                        survivors.append(nnz)
+                        res.append((a.elapsed_time(b), 8 * n + 8 * n + 4 * n))
+                        red.append((b2.elapsed_time(c), 4 * n + row_bytes * nnz + row_bytes * n))
+                        # the copy kernel alone: run starts 4 B per row, distinct source rows, N rows written
+                        cop.append((evs[1].elapsed_time(evs[2]), 4 * n + row_bytes * nnz + row_bytes * n))
+                        nsr.append((e0.elapsed_time(e1), 8 * n + 2 * row_bytes * n))
+                        nr.append((e0.elapsed_time(e2), 0))
+
+            def med_ms(v):
+                return statistics.median(t for t, _ in v)
+
+            def med_gbs(v):
+                return statistics.median(byt / (t * 1e-3) / 1e9 for t, byt in v)
+
+            rm, dm, cm, sm_, nm = med_ms(res), med_ms(red), med_ms(cop), med_ms(nsr), med_ms(nr)
             line = {"metric": "redistribute GB/s", "workload": f"resample+redistribute N=2^{int(np.log2(n))} {case}",
-                    "n": n, "d": d, "survivors": nnz, "resample_ms": rm, "redistribute_ms": dm,
-                    "redistribute_gbs": red_bytes / (dm * 1e-3) / 1e9, "resample_gbs": res_bytes / (rm * 1e-3) / 1e9,
+                    "n": n, "d": d, "seeds": seeds, "survivors_median": int(statistics.median(survivors)),
+                    "resample_ms": rm, "redistribute_ms": dm,
+                    "redistribute_gbs": med_gbs(red), "resample_gbs": med_gbs(res),
                     "peak_gbs": peak, "peak_kind": peak_kind,
-                    "redistribute_frac": red_bytes / (dm * 1e-3) / 1e9 / peak,
-                    "copy_kernel_ms": cm, "copy_kernel_gbs": copy_bytes / (cm * 1e-3) / 1e9,
-                    "copy_kernel_frac": copy_bytes / (cm * 1e-3) / 1e9 / peak,
-                    "nearly_sort_ms": sm_, "nearly_sort_gbs": ns_bytes / (sm_ * 1e-3) / 1e9,
-                    "nearly_sort_frac": ns_bytes / (sm_ * 1e-3) / 1e9 / peak,
-                    "nr_ms": nm, "nr_over_gather": nm / dm, "timing": "median of 20, L2 flushed"}
+                    "redistribute_frac": med_gbs(red) / peak,
+                    "copy_kernel_ms": cm, "copy_kernel_gbs": med_gbs(cop), "copy_kernel_frac": med_gbs(cop) / peak,
+                    "nearly_sort_ms": sm_, "nearly_sort_gbs": med_gbs(nsr), "nearly_sort_frac": med_gbs(nsr) / peak,
+                    "nr_ms": nm, "nr_over_gather": nm / dm,
+                    "timing": f"medians over {len(seeds)} seeds x 20 iterations (after {args.warmup} warm-up "
+                              "iterations per seed), L2 flushed"}
             if rank == 0:
                 print(json.dumps(line), flush=True)
 
