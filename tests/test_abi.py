@@ -146,3 +146,26 @@ def test_struct_layouts_match_the_header(built, tmp_path):
         for field, _ in cls._fields_:
             assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
 
+
+
+def test_stateless_calls_reject_bad_arguments_host_only(built):
+    """The stateless entry points check sizes, pointers, alignment and the
+    event count before any CUDA call."""
+    from paper_1905_10252_gb300 import native
+
+    L = native.load_library()
+    A = 1 << 24  # fake, aligned device addresses (never dereferenced)
+    EINVAL = native.SMC_EINVAL
+    assert L.smc_redistribute_raw(0, 16, A, A, A, A, None) == EINVAL        # n = 0
+    assert L.smc_redistribute_raw(2 ** 31, 16, A, A, A, A, None) == EINVAL  # n too large
+    assert L.smc_redistribute_raw(100, 6, A, A, A, A, None) == EINVAL       # row bytes
+    assert L.smc_redistribute_raw(100, 16, A, A, A, A + 8, None) == EINVAL  # workspace alignment
+    assert L.smc_redistribute_raw(100, 16, A, A + 4, A, A, None) == EINVAL  # rows misaligned
+    ev = (ctypes.c_void_p * 3)(A, A, A)
+    assert L.smc_redistribute_raw_profile(100, 16, A, A, A, A, None, ev, 2) == EINVAL  # event count
+    assert L.smc_redistribute_raw_profile(100, 16, A, A, A, A, None, None, 3) == EINVAL  # null events
+    assert L.smc_nearly_sort_raw(100, 16, A + 4, A, A, A, A, None) == EINVAL  # keys misaligned
+    assert L.smc_resample_raw(100, A, 0, 0, 3, A, None, A, None) == EINVAL    # mode
+    out = ctypes.c_size_t()
+    assert L.smc_nearly_sort_ws_bytes(0, ctypes.byref(out)) == EINVAL
+    assert L.smc_nearly_sort_ws_bytes(5000, ctypes.byref(out)) == 0 and out.value >= 2 * 4 * 2
