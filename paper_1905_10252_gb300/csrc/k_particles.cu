@@ -894,7 +894,7 @@ __global__ void k_begin(DevState* st) {
 }
 
 __global__ void k_commit(DevState* st, int d, int force_flip, int recycle) {
-  if (threadIdx.x == 0) commit_one(st, d, force_flip, recycle);
+  if (threadIdx.x < 32) commit_warp(st, d, force_flip, recycle);
 }
 
 // Batched bookkeeping: thread s handles sampler s.
@@ -903,9 +903,10 @@ __global__ void k_begin_batch(const ParticleArgs* __restrict__ pa, int count) {
   if (s < count) pa[s].st->t += 1;
 }
 
+// Batched: one warp (block) per sampler.
 __global__ void k_commit_batch(const ParticleArgs* __restrict__ pa, int count) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < count) commit_one(pa[s].st, pa[s].d, 0, 1);
+  const int s = blockIdx.x;
+  if (s < count) commit_warp(pa[s].st, pa[s].d, 0, 1);
 }
 
 // Points every sampler's step outputs; outs holds three arrays of count
@@ -1053,7 +1054,7 @@ cudaError_t launch_take_errors_batch(const ParticleArgs* pa, int32_t* errs, int 
   return cudaGetLastError();
 }
 cudaError_t launch_commit_batch(const ParticleArgs* pa, int count, cudaStream_t s) {
-  k_commit_batch<<<(count + 127) / 128, 128, 0, s>>>(pa, count);
+  k_commit_batch<<<count, 32, 0, s>>>(pa, count);
   return cudaGetLastError();
 }
 

@@ -415,6 +415,17 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
     }
     __syncthreads();
   }
+  // eq. (7): the weighted mean, one column per thread
+  {
+    u128 se_all = 0;
+    for (int w = 0; w < nw; ++w) se_all += (u128(sheh[w]) << 64) | shel[w];
+    const double se_all_d = u128_to_double(se_all);
+    if (est && !st->err && se_all_d > 0.0 && int(threadIdx.x) < a.d) {
+      const double mc = sxsum[threadIdx.x] / se_all_d;
+      st->mean[threadIdx.x] = mc;
+      if (st->mean_out) st->mean_out[threadIdx.x] = mc;
+    }
+  }
   if (threadIdx.x != 0) return;
   uint64_t S = 0;
   u128 sw2 = 0, se = 0;
@@ -445,13 +456,6 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
   const double se_d = u128_to_double(se);
   const double lse = m + log(se_d * 0x1p-62);
   st->est_s = se_d * 0x1p-62;
-  if (est && !st->err && se_d > 0.0) {
-    for (int c = 0; c < a.d; ++c) {
-      const double mc = sxsum[c] / se_d;
-      st->mean[c] = mc;
-      if (st->mean_out) st->mean_out[c] = mc;
-    }
-  }
   const double Sd = double(S);
   const double ess = (S && sw2) ? Sd * Sd / u128_to_double(sw2) : 0.0;
   st->S = S;
@@ -795,7 +799,7 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute_commit(RedistArgs a,
   __shared__ RedistSmem sm;
   redistribute_body<V, CPR>(a, 0, sm);
   __syncthreads();
-  if (threadIdx.x == 0) commit_one(a.st, d, force_flip, recycle);
+  if (threadIdx.x < 32) commit_warp(a.st, d, force_flip, recycle);
 }
 
 // ---------------------------------------------------------------- batched launches

@@ -391,23 +391,35 @@ __device__ __forceinline__ long long warp_max_ll(long long v) {
 
 
 // ---------------------------------------------------------------- end of an iteration
-// Ends iteration t: swap buffers if resampled (or if forced by an explicit
-// redistribute), LSE_{t} becomes the next LSE_{t-1} (0 after a reset), and
-// the recycling sums of eq. (6) take f_t with weight c_t.
-__device__ __forceinline__ void commit_one(DevState* st, int d, int force_flip, int recycle) {
-  const bool flip = force_flip || (st->flag && !st->err);
-  if (recycle && !st->err) {
-    const double lc = st->logc;
-    const double M = fmax(st->rc_max, lc);
-    const double sc = (st->rc_max == -INFINITY) ? 0.0 : exp(st->rc_max - M);
-    const double e = exp(lc - M);
-    st->rc_den = st->rc_den * sc + e;
-    for (int c = 0; c < d; ++c) st->rc_num[c] = st->rc_num[c] * sc + e * st->mean[c];
-    st->rc_max = M;
-    if (st->fhat_out)
-      for (int c = 0; c < d; ++c) st->fhat_out[c] = st->rc_num[c] / st->rc_den;
+// Ends iteration t, executed by one full warp: swap buffers if resampled (or
+// if forced by an explicit redistribute), LSE_t becomes the next LSE_{t-1}
+// (0 after a reset), and the recycling sums of eq. (6) take f_t with weight
+// c_t -- one column per lane, each with explicitly rounded FP64 operations
+// (the same bits whichever kernel runs it).
+__device__ __forceinline__ void commit_warp(DevState* st, int d, int force_flip, int recycle) {
+  const int lane = threadIdx.x & 31;
+  const int err = st->err, flag = st->flag;
+  const bool flip = force_flip || (flag && !err);
+  if (recycle && !err) {
+    const double lc = st->logc, rmax = st->rc_max;
+    const double M = fmax(rmax, lc);
+    const double sc = (rmax == -INFINITY) ? 0.0 : exp(__dsub_rn(rmax, M));
+    const double e = exp(__dsub_rn(lc, M));
+    const double den = __fma_rn(st->rc_den, sc, e);
+    double* fh = st->fhat_out;
+    for (int c = lane; c < d; c += 32) {
+      const double num = __fma_rn(st->rc_num[c], sc, __dmul_rn(e, st->mean[c]));
+      st->rc_num[c] = num;
+      if (fh) fh[c] = __ddiv_rn(num, den);
+    }
+    __syncwarp();  // every lane has read rc_max and rc_den
+    if (lane == 0) {
+      st->rc_den = den;
+      st->rc_max = M;
+    }
   }
-  if (st->flag && !st->err) {
+  if (lane != 0) return;
+  if (flag && !err) {
     st->last.survivors = (int64_t)st->survivors;
     if (st->trace) {
       const int64_t idx = st->t - st->trace_t0 - 1;
@@ -417,7 +429,7 @@ __device__ __forceinline__ void commit_one(DevState* st, int d, int force_flip, 
   if (flip) st->cur ^= 1;
   st->lse_prev = flip ? 0.0 : st->lse;
   // a resampled iteration leaves every log w at reset_logw
-  st->w_uniform = (flip && !st->err) ? 1 : 0;
+  st->w_uniform = (flip && !err) ? 1 : 0;
 }
 
 }  // namespace smc
