@@ -462,3 +462,25 @@ def test_redistribute_raw_profile_same_output(nat, orc):
     assert nat.smc_ws_status(ws) == nat.SMC_OK
     assert np.array_equal(out.cpu().numpy(), orc.redistribute(nc, x))
     assert evs[0].elapsed_time(evs[1]) >= 0 and evs[1].elapsed_time(evs[2]) > 0
+
+
+@pytest.mark.parametrize("D", [2, 16, 32])
+def test_fp32_covariance_against_oracle(nat, orc, D):
+    """The weighted covariance of eq. (7)'s estimate (the diagnostic output)
+    for FP32 state against the oracle's on the same particles and weights."""
+    N = 40000
+    mu, Sigma = _gauss(D, seed=3)
+    S = nat.Sampler(N, D, dtype=torch.float32, seed=5, mu=mu, sigma=Sigma, resample_mode=nat.RESAMPLE_NEVER)
+    S.move()
+    S.reweight()
+    mean, cov = S.estimate(cov=True)
+    S.sync()
+    x = host(S.current()[0]).astype(np.float64)
+    lw = host(S.logw)
+    _, lse, _ = orc.lse_ess(lw)
+    mref, cref = orc.estimate(x, lw, lse, with_cov=True)
+    scale = 1.0 + np.abs(cref).max()
+    np.testing.assert_allclose(host(cov), cref, rtol=0, atol=5e-5 * scale)
+    np.testing.assert_allclose(host(mean), mref, rtol=0, atol=2e-5 * (1 + np.abs(mref).max()))
+    c = host(cov)
+    assert np.array_equal(c, c.T)

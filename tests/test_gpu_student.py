@@ -67,3 +67,19 @@ def test_student_posterior_moments(nat, dtype):
         v = np.asarray(vals)
         se = v.std(ddof=1) / np.sqrt(R)
         assert abs(v.mean() - target) <= 4.5 * se + 1e-12, (v.mean(), target, se)
+
+
+def test_student_fp32_logpi_against_oracle(nat, orc):
+    """FP32 Student-t log pi (eq. (14)) of the initial and moved particles
+    against the oracle's FP64 values, within the reduced-precision bound."""
+    N, mu, nu = 50001, -0.3, 4.0
+    tgt = orc.Target.student_t(mu, nu)
+    S = nat.Sampler(N, 1, dtype=torch.float32, seed=12, target="student_t", mu=[mu], nu=nu, step=0.7,
+                    init_scale=2.0, resample_mode=nat.RESAMPLE_NEVER)
+    for _ in range(2):
+        x, lp = [t.cpu().numpy().copy() for t in S.current()]
+        ref = tgt.logpi(x.astype(np.float64))
+        assert np.all(np.abs(lp - ref) <= 2e-5 * (1 + np.abs(ref))), np.abs(lp - ref).max()
+        S.move()
+        S.reweight()
+    S.sync()
