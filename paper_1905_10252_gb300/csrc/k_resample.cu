@@ -583,22 +583,43 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
 __global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) { quant_scan_body(a, blockIdx.x); }
 
 // ---------------------------------------------------------------- standalone ncopies scan
+// Thread t of a block owns the 16 consecutive entries [base + 16 t, +16) of
+// the caller's ncopies, read with 16-byte loads when the vector is 16-byte
+// aligned and the group is complete (scalar loads otherwise).
+__device__ __forceinline__ void load_counts(const int32_t* __restrict__ nc, int64_t n, int64_t first, int32_t c[16]) {
+  const bool vec = ((reinterpret_cast<uintptr_t>(nc) & 15) == 0) && first + 16 <= n;
+  if (vec) {
+    const int4* p = reinterpret_cast<const int4*>(nc + first);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int4 v = __ldg(p + q);
+      c[4 * q] = v.x;
+      c[4 * q + 1] = v.y;
+      c[4 * q + 2] = v.z;
+      c[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) c[q] = first + q < n ? nc[first + q] : 0;
+  }
+}
+
 __global__ void __launch_bounds__(kQThreads) k_nc_reduce(NcScanArgs a) {
   __shared__ uint64_t sh[kQThreads / 32];
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
+  const int64_t first = int64_t(blockIdx.x) * kQTile + int64_t(threadIdx.x) * kQItems;
+  int32_t c[kQItems];
+  load_counts(a.ncopies, a.n, first, c);
   uint64_t s = 0;
-  const int64_t base = int64_t(blockIdx.x) * kQTile;
-#pragma unroll 4
-  for (int k = 0; k < kQItems; ++k) {
-    const int64_t i = base + k * kQThreads + threadIdx.x;
-    if (i < a.n) {
-      const int32_t c = a.ncopies[i];
-      if (c < 0) bad = 1;
-      s += uint64_t(uint32_t(max(c, 0)));
-    }
+  bool neg = false;
+#pragma unroll
+  for (int q = 0; q < kQItems; ++q) {
+    neg |= c[q] < 0;
+    s += uint64_t(uint32_t(max(c[q], 0)));
   }
+  if (neg) bad = 1;
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -626,38 +647,51 @@ __global__ void __launch_bounds__(kFinThreads) k_nc_finalize(NcScanArgs a) {
   if (threadIdx.x == 0 && total != uint64_t(a.n)) record_error(a.st, SMC_EINVAL);
 }
 
+// Run starts of the block's items: the block's outputs form the window
+// [cbase, cbase + total); when it fits in shared memory it is assembled
+// there (-1, then the run starts) and written out with coalesced stores,
+// otherwise the run starts are stored one by one into the already cleared
+// array.
+constexpr int kNcWin = 8192;
+
 __global__ void __launch_bounds__(kQThreads) k_nc_scan(NcScanArgs a) {
   if (a.st->err) return;
-  __shared__ uint32_t buf[kQThreads * 17];
+  __shared__ int32_t win[kNcWin];
   __shared__ uint64_t scratch[33];
   const int64_t n = a.n;
   const int64_t base = int64_t(blockIdx.x) * kQTile;
-#pragma unroll 4
-  for (int k = 0; k < kQItems; ++k) {
-    const int idx = k * kQThreads + threadIdx.x;
-    const int64_t i = base + idx;
-    buf[pad_idx(idx)] = i < n ? uint32_t(a.ncopies[i]) : 0u;
-  }
-  __syncthreads();
-  uint32_t c[kQItems];
+  const int64_t i0 = base + int64_t(threadIdx.x) * kQItems;
+  int32_t c[kQItems];
+  load_counts(a.ncopies, n, i0, c);
   uint64_t tsum = 0;
 #pragma unroll
-  for (int q = 0; q < kQItems; ++q) {
-    c[q] = buf[threadIdx.x * 17 + q];
-    tsum += c[q];
-  }
+  for (int q = 0; q < kQItems; ++q) tsum += uint32_t(c[q]);
   uint64_t btot;
-  uint64_t o = a.cbase[blockIdx.x] + block_excl_scan_u64(tsum, scratch, &btot);
-  const int64_t i0 = base + int64_t(threadIdx.x) * kQItems;
+  const uint64_t w0 = a.cbase[blockIdx.x];
+  const uint64_t o0 = w0 + block_excl_scan_u64(tsum, scratch, &btot);
+  const bool staged = btot <= uint64_t(kNcWin);
+  if (staged) {
+    for (int k = threadIdx.x; k < int(btot); k += blockDim.x) win[k] = -1;
+    __syncthreads();
+  }
+  uint64_t o = o0;
 #pragma unroll
   for (int q = 0; q < kQItems; ++q) {
     const int64_t i = i0 + q;
     if (c[q] > 0 && i < n && o < uint64_t(n)) {
-      a.runstart[o] = int32_t(i);
-      for (uint64_t kb = ((o + kRTile - 1) / kRTile) * kRTile; kb < o + c[q] && kb < uint64_t(n); kb += kRTile)
+      if (staged)
+        win[o - w0] = int32_t(i);
+      else
+        a.runstart[o] = int32_t(i);
+      for (uint64_t kb = ((o + kRTile - 1) / kRTile) * kRTile; kb < o + uint32_t(c[q]) && kb < uint64_t(n); kb += kRTile)
         a.tile_src[kb / kRTile] = int32_t(i);
     }
-    o += c[q];
+    o += uint32_t(c[q]);
+  }
+  if (staged) {
+    __syncthreads();
+    int32_t* __restrict__ rs = a.runstart + w0;
+    for (int k = threadIdx.x; k < int(btot); k += blockDim.x) rs[k] = win[k];
   }
 }
 

@@ -484,3 +484,20 @@ def test_fp32_covariance_against_oracle(nat, orc, D):
     np.testing.assert_allclose(host(mean), mref, rtol=0, atol=2e-5 * (1 + np.abs(mref).max()))
     c = host(cov)
     assert np.array_equal(c, c.T)
+
+
+@pytest.mark.parametrize("N", [4097, 100003])
+def test_redistribute_raw_misaligned_ncopies(nat, orc, N):
+    """A copy-count vector that does not start on a 16-byte boundary (a
+    slice of a larger tensor) takes the scalar-load path: same rows."""
+    nc = inputs.composition(N, seed=N + 5)
+    x = np.random.default_rng(N).standard_normal((N, 16)).astype(np.float32)
+    big = torch.zeros(N + 3, dtype=torch.int32, device="cuda")
+    big[1:N + 1] = torch.as_tensor(nc, device="cuda")
+    ncd = big[1:N + 1]
+    assert ncd.data_ptr() % 16 != 0
+    ws = torch.empty(nat.smc_redistribute_ws_bytes(N), dtype=torch.uint8, device="cuda")
+    out = nat.smc_redistribute_raw(ncd, torch.as_tensor(x, device="cuda"), ws=ws)
+    torch.cuda.synchronize()
+    assert nat.smc_ws_status(ws) == nat.SMC_OK
+    assert np.array_equal(out.cpu().numpy(), orc.redistribute(nc, x))
