@@ -401,30 +401,43 @@ __global__ void __launch_bounds__(kPThreads) k_move_reweight(ParticleArgs a) {
 
 // ---------------------------------------------------------------- move + reweight, FP32 fast path
 // The FP32 path gives each lane one particle of up to DPL coordinates (DPL/4
-// Philox blocks: four 32-bit words, two Box-Muller pairs per block).  Box-Muller uses the multi-function unit: r^2 = -2 ln(1-a)
-// by __logf, or by its series when a < 1/16 (where __logf's absolute error
-// would dominate), and __sincosf on 2 pi (b - 1/2) in [-pi, pi); the normals
-// differ from the exactly rounded ones by a few 1e-6 at most, and since the
-// random-walk proposal stays symmetric the weights of eq. (5) are unaffected.
+// Philox blocks: four 32-bit words, two Box-Muller pairs per block).
+// Box-Muller uses the multi-function unit: (eps r)^2 = -2 eps^2 ln(1-a) from
+// log2 (ln y = ln 2 log2 y), or from its series when a < 1/16 (where the
+// approximate log2's absolute error would dominate), and __sincosf on
+// 2 pi (b - 1/2) in [-pi, pi).  The step eps is folded into the constants, so
+// a pair costs one multiply for each of a, the radius and the angle, and the
+// move itself is two FMAs; the moved coordinates differ from the exactly
+// rounded x + eps z by a few 1e-6 at most, and since the random-walk proposal
+// stays symmetric the weights of eq. (5) are unaffected.
 // Up to 16 coordinates, the next particle's row, log pi and log w are loaded
 // while the current one is computed.
-__device__ __forceinline__ void bm_pair_fast(uint32_t h0, uint32_t h1, float& z0, float& z1) {
+struct BmStep {
+  float s4, s3, s2, s1, s0;  // eps^2 (2/5, 1/2, 2/3, 1, 2): -2 eps^2 ln(1-a) / a as a series in a
+  float slog;                // -2 eps^2 ln 2
+};
+__device__ __forceinline__ BmStep bm_step(float eps) {
+  const float e2 = eps * eps;
+  return BmStep{0.4f * e2, 0.5f * e2, (2.0f / 3.0f) * e2, e2, 2.0f * e2, -1.38629436111989061883f * e2};
+}
+// x0 += eps z0, x1 += eps z1 for the normal pair (z0, z1) of the words h0, h1.
+__device__ __forceinline__ void bm_pair_step(uint32_t h0, uint32_t h1, const BmStep& k, float& x0, float& x1) {
   const float a = float(h0 >> 8) * 0x1p-24f;  // u1 = 1 - a
   // -ln(1 - a) = a (1 + a/2 + a^2/3 + a^3/4 + a^4/5 + ...): for a < 1/16 the
   // truncation error is below 1.7e-7 relative (about 1.4 FP32 ulp)
-  float p = fmaf(a, 0.2f, 0.25f);
-  p = fmaf(a, p, 1.0f / 3.0f);
-  p = fmaf(a, p, 0.5f);
-  p = fmaf(a, p, 1.0f);
-  const float r2s = 2.0f * a * p;                 // -2 ln(1-a), |a| < 1/16
-  const float r2l = -2.0f * __logf(1.0f - a);
+  float p = fmaf(a, k.s4, k.s3);
+  p = fmaf(a, p, k.s2);
+  p = fmaf(a, p, k.s1);
+  p = fmaf(a, p, k.s0);
+  const float r2s = a * p;  // (eps r)^2, a < 1/16
+  const float r2l = __log2f(1.0f - a) * k.slog;
   const float r2 = a < 0.0625f ? r2s : r2l;
-  const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+  const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;  // eps r
   const float th = float(int(h1 >> 8) - (1 << 23)) * (0x1p-24f * 6.28318530717958647692f);
   float sn, cs;
   __sincosf(th, &sn, &cs);  // (sin, cos)(2 pi b - pi) = -(sin, cos)(2 pi b)
-  z0 = -r * cs;
-  z1 = -r * sn;
+  x0 = fmaf(-r, cs, x0);
+  x1 = fmaf(-r, sn, x1);
 }
 
 template <int DPL>
@@ -593,7 +606,7 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
   constexpr int q = 0, c0 = 0;  // one lane per particle: it owns coordinates [0, d)
   const int nvalid = d;
   const bool vec = ((d & 3) == 0) && (nvalid >= DPL);
-  const float eps = float(a.step);
+  const BmStep bs = bm_step(float(a.step));
   // Warp tiles of kEstTile consecutive particles (kEstChunks chunks of 32,
   // lane l takes particle 32 r + l of chunk r), tile j to warp j mod W.  The
   // loop bound is warp-uniform; lanes past the end are predicated.
@@ -664,10 +677,7 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             if (DPL == 8 && 4 * b4 + 2 * h >= nvalid) continue;  // this pair's normals are not used
-            float z0, z1;
-            bm_pair_fast(w[b4].v[2 * h], w[b4].v[2 * h + 1], z0, z1);
-            xo[4 * b4 + 2 * h] = fmaf(eps, z0, xo[4 * b4 + 2 * h]);
-            xo[4 * b4 + 2 * h + 1] = fmaf(eps, z1, xo[4 * b4 + 2 * h + 1]);
+            bm_pair_step(w[b4].v[2 * h], w[b4].v[2 * h + 1], bs, xo[4 * b4 + 2 * h], xo[4 * b4 + 2 * h + 1]);
           }
         }
       }
