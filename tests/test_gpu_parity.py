@@ -300,6 +300,26 @@ def test_fp32_stages(nat, orc, N, D):
     S.sync()
 
 
+@pytest.mark.parametrize("step", [0.05, 0.3, 1.7])
+@pytest.mark.parametrize("N,D", [(4099, 16), (1025, 5)])
+def test_fp32_move_step_sizes(nat, orc, N, D, step):
+    """The FP32 move folds the step into its Box-Muller constants (eps^2 in
+    the radius, -eps r in the two FMAs); steps whose square is not a power of
+    two round there, on the vector (D = 16) and scalar (D = 5) row paths.
+    The bound scales with the step: the normals' own error is a few 1e-6."""
+    mu, Sigma = _gauss(D, seed=D)
+    seed = 33
+    S = nat.Sampler(N, D, dtype=torch.float32, seed=seed, mu=mu, sigma=Sigma, step=step,
+                    resample_mode=nat.RESAMPLE_ALWAYS)
+    x0g = host(S.current()[0]).copy()
+    S.move()
+    x1g = host(S.current()[0]).copy()
+    x1 = orc.move(x0g.astype(np.float64), seed, 1, step, ubits=24)
+    tol = 4e-6 * max(1.0, 2.0 * step) * (1 + np.abs(x1))
+    assert np.all(np.abs(x1g - x1) <= tol)
+    S.sync()
+
+
 def test_fp32_step_equals_piecewise(nat):
     N, D = 70001, 16
     mu, Sigma = _gauss(D)
