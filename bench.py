@@ -278,13 +278,25 @@ def job_value(n_per_rank: int, steps: int, world_size: int, total_ms: float) -> 
     return n_per_rank * steps * world_size / (total_ms * 1e-3)
 
 
-def algorithmic_bytes(n: int, d: int, esize: int, survivors: float, est_in_move: bool = False):
+def algorithmic_bytes(n: int, d: int, esize: int, survivors: float, est_in_move: bool = False,
+                      gather: bool = False):
     """Per-launch algorithmic bytes of each stage (see the measurement section
     of the design notes): reads + writes the definition of the stage needs.
     est_in_move: the move kernel formed the sums of eq. (7) (FP32 Gaussian,
     D <= 16, every log w equal after the previous resampling), so the
-    quantise pass reads log w only."""
+    quantise pass reads log w only.  gather: the previous iteration's
+    redistribution is done by this move (the rows of the survivors read once
+    through the run starts, every log w equal to -log N), and there is no
+    copy stage."""
     row = d * esize
+    if gather:
+        return {
+            # read the run starts, the distinct surviving rows + log pi; write
+            # x, log pi, log w
+            "move_reweight": n * 4 + survivors * (row + esize) + n * (row + esize + 8),
+            "quantise_reduce_estimate": n * 8,
+            "systematic_scan": n * 8 + survivors * 4,
+        }
     return {
         # read x, log pi, log w; write x, log pi, log w
         "move_reweight": n * (2 * row + 2 * esize + 2 * 8),
@@ -314,8 +326,12 @@ def run_iteration(args):
 
     n, d = args.n, args.d
     mu, Sigma = inputs.gaussian_target(d, seed=16)
+    # (D <= 16: each resampling's copy is gathered by the next iteration's
+    # move; the particles and weights are those of the copying iteration)
+    gather = d <= 16
     S = native.Sampler(n, d, dtype=torch.float32, seed=rank, mu=mu, sigma=Sigma, step=0.5, init_scale=2.0,
-                       resample_mode=native.RESAMPLE_ALWAYS)
+                       resample_mode=native.RESAMPLE_ALWAYS,
+                       flags=native.FLAG_DEFER_REDISTRIBUTE if gather else 0)
     stream = S.stream
     K, W = args.steps, args.warmup
     for _ in range(W):
@@ -353,7 +369,7 @@ def run_iteration(args):
     st = S.stats()
     survivors = float(st["survivors"])
     # every timed iteration resamples, so each one starts from equal weights
-    byt = algorithmic_bytes(n, d, 4, survivors, est_in_move=d <= 16)
+    byt = algorithmic_bytes(n, d, 4, survivors, est_in_move=d <= 16, gather=gather)
     peak, peak_kind = peaks()
     dominant = max(stage_ms, key=stage_ms.get)
     traffic = measured_traffic()
@@ -374,6 +390,12 @@ def run_iteration(args):
         x_h = S.current()[0].cpu().pin_memory()
         lp_h = S.current()[1].cpu().pin_memory()
         lw_h = S.logw.cpu().pin_memory()
+        # (samplers that copy at the end of each iteration: every step here
+        # replaces the whole state from the host buffers)
+        S.close()
+        S = native.Sampler(n, d, dtype=torch.float32, seed=rank, mu=mu, sigma=Sigma, step=0.5, init_scale=2.0,
+                           resample_mode=native.RESAMPLE_ALWAYS)
+        stream = S.stream
         mean_d = torch.empty(d, dtype=torch.float64, device="cuda")
         mean_h = torch.empty(d, dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
@@ -444,7 +466,9 @@ def run_iteration(args):
                "serial": serial}
     S.sync()
     value = job_value(n, K, ws, total_ms)
-    launches_per_step = 8
+    # step set-up, begin, move + reweight, max, quantise reduce / finalise,
+    # scan, (redistribute,) commit
+    launches_per_step = 8 if gather else 9
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K, "warmup": W,
@@ -452,7 +476,9 @@ def run_iteration(args):
             "dtype": "f32 state / f64 weights / u64 fixed-point CDF", "data": "synthetic",
             "config": {"workload": f"smc-iteration gauss N=2^{int(np.log2(n))} D={d} fp32 resample-every-iteration",
                        "n": n, "d": d, "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (particle state %.2f GB per buffer)" % (n * d * 4 / 1e9)},
+                       "l2": "inputs larger than L2 (particle state %.2f GB per buffer)" % (n * d * 4 / 1e9),
+                       "redistribute": ("gathered by the next iteration's move (SMC_FLAG_DEFER_REDISTRIBUTE)"
+                                        if gather else "copy kernel at the end of the iteration")},
             "roofline": roof(dominant) if dominant in byt else roof("move_reweight"),
             "dominant_kernel": dominant,
             "redistribute": roof("redistribute"),

@@ -69,6 +69,16 @@ typedef enum { SMC_RESAMPLE_ESS = 0, SMC_RESAMPLE_ALWAYS = 1, SMC_RESAMPLE_NEVER
  * the kernel then drains, frees its tensor memory and returns, and the next
  * smc_sync reports SMC_ETIMEOUT.  The GPU context stays usable. */
 #define SMC_FLAG_TEST_STALL_LIKELIHOOD 2
+/* SMC_FLAG_DEFER_REDISTRIBUTE: in smc_step and smc_step_profile, an iteration
+ * that resamples does not copy the rows (Algorithm 5) itself; the next
+ * iteration's move reads each particle's row from its source (the copy fused
+ * into the move kernel, which saves one write and one read of every row), so
+ * the rows, log pi and log w in the caller's buffers are the sampler's state
+ * only after smc_materialize, smc_current or any other call on the sampler.
+ * The particles, weights, estimates and statistics are bit-identical to those
+ * without the flag.  Honoured by FP32 Gaussian samplers with D <= 16 and
+ * N > 4096 (whose move kernel forms the eq. (7) sums); ignored otherwise. */
+#define SMC_FLAG_DEFER_REDISTRIBUTE 4
 
 typedef struct {
   int64_t n;              /* N particles */
@@ -176,8 +186,15 @@ int smc_sync(smc_sampler* h);
 int smc_read_stats(smc_sampler* h, smc_iter_stats* out_host);
 
 /* 0 if x_dev / logpi_dev hold the current particles, 1 if the _alt buffers do
- * (synchronising). */
+ * (synchronising; completes a deferred redistribution first). */
 int smc_current(smc_sampler* h, int32_t* which_host);
+
+/* Completes the redistribution (Algorithm 5 and the log w reset) that a
+ * sampler created with SMC_FLAG_DEFER_REDISTRIBUTE left pending, on the
+ * sampler's stream; a no-op otherwise.  smc_move, smc_reweight, smc_estimate,
+ * smc_resample, smc_redistribute, smc_current, the checkpoint calls and
+ * smc_batch_create do it themselves. */
+int smc_materialize(smc_sampler* h);
 
 /* Frees the handle (host memory only). */
 int smc_destroy(smc_sampler* h);

@@ -574,10 +574,50 @@ __device__ __forceinline__ void warp_write_est(float em, double R, float (&v)[DM
   if (lane == 0) rec[0] = Mf == -INFINITY ? -INFINITY : R + double(Mf);
 }
 
-template <int DPL, bool MOVE, bool REWEIGHT, typename FS, bool EST = false>
+// Algorithm 5 as a gather, for the 256 particles of move tile jt: row k of
+// the resampled set is row src(k) = the last run start at or before k
+// (rs[off_i] = i for every survivor i, -1 elsewhere).  tile_src holds src at
+// the first row of each 2048-row copy tile; run starts between that row and
+// the move tile's first row are found by a backward search 32 rows at a time
+// (in all but heavily duplicated regions the 32 rows just before hold one).
+// The warp writes the tile's 256 sources to out[] (clamped into [0, n), as
+// the copy kernel clamps them); every lane of the warp takes part.
+__device__ __forceinline__ void tile_sources(const int32_t* __restrict__ rs, const int32_t* __restrict__ tile_src,
+                                             int64_t n, int64_t jt, int32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k0 = jt * kEstTile;
+  const int64_t t0 = (k0 / kRTile) * kRTile;
+  int carry = tile_src[k0 / kRTile];
+  for (int64_t q = k0 - 32; q >= t0; q -= 32) {
+    int m = rs[q + lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (m >= 0) {
+      carry = max(carry, m);
+      break;
+    }
+  }
+  int v[kEstTile / 32];
+#pragma unroll
+  for (int r = 0; r < kEstTile / 32; ++r) {
+    const int64_t k = k0 + r * 32 + lane;
+    v[r] = k < n ? rs[k] : -1;
+  }
+  const int last = int(n - 1);
+#pragma unroll
+  for (int r = 0; r < kEstTile / 32; ++r) {
+    const int sk = min(max(max(warp_incl_max_i32(v[r]), carry), 0), last);
+    out[r * 32 + lane] = sk;
+    carry = __shfl_sync(0xffffffffu, sk, 31);
+  }
+  __syncwarp();
+}
+
+template <int DPL, bool MOVE, bool REWEIGHT, typename FS, bool EST = false, bool GATHER = false>
 __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const FS gp, const int blk, const int nblk) {
   constexpr int DMAX = DPL;
   static_assert(!EST || DPL <= 16, "eq. (7) records: D <= 16");
+  static_assert(!GATHER || EST, "the gathering move is the records kernel's");
   // the next particle's data is loaded during the current one's arithmetic
   // when the registers allow it (up to 16 coordinates per lane)
   constexpr bool PF = DPL <= 16;
@@ -602,6 +642,14 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
   float* __restrict__ x = static_cast<float*>(cur ? a.x[1] : a.x[0]);
   float* __restrict__ lp = static_cast<float*>(cur ? a.logpi[1] : a.logpi[0]);
   double* __restrict__ logw = a.logw;
+  // GATHER with a pending resampling (Algorithm 5 fused into this move):
+  // particle k starts from row src(k) of buffer cur with log w = reset_logw,
+  // and is written to row k of the other buffer.  Otherwise in place.
+  const bool gat = GATHER && a.st->pending;
+  float* xd = gat ? static_cast<float*>(cur ? a.x[0] : a.x[1]) : x;
+  float* lpd = gat ? static_cast<float*>(cur ? a.logpi[0] : a.logpi[1]) : lp;
+  __shared__ int32_t s_src[GATHER ? kPThreads / 32 : 1][GATHER ? kEstTile : 1];
+  int32_t* const wsrc = s_src[GATHER ? (threadIdx.x >> 5) : 0];
   const int d = a.d;
   constexpr int q = 0, c0 = 0;  // one lane per particle: it owns coordinates [0, d)
   const int nvalid = d;
@@ -623,13 +671,20 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
   float lpc = 0.0f;
   {
     const int64_t i = j * kEstTile + grp;
-    if (j < ntile && i < a.n && nvalid > 0) load_seg<DPL>(x + i * d + c0, vec, nvalid, xo);
+    int64_t si = i;
+    if constexpr (GATHER) {
+      if (gat && j < ntile) {
+        tile_sources(a.rs, a.tile_src, a.n, j, wsrc);
+        si = wsrc[grp];
+      }
+    }
+    if (j < ntile && i < a.n && nvalid > 0) load_seg<DPL>(x + si * d + c0, vec, nvalid, xo);
     else
 #pragma unroll
       for (int c = 0; c < DPL; ++c) xo[c] = 0.0f;
     if (REWEIGHT && j < ntile && i < a.n && q == 0) {
-      lwc = logw[i];
-      lpc = lp[i];
+      lwc = gat ? R : logw[i];
+      lpc = lp[si];
     }
   }
   bool first = true;
@@ -654,13 +709,22 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
     double lwn = 0.0;
     float lpn = 0.0f;
     if constexpr (PF) {
-      if (vn && nvalid > 0) load_seg<kPF>(x + inx * d + c0, vec, nvalid, xn);
+      int64_t sn = inx;
+      if constexpr (GATHER) {
+        if (gat && jn < ntile) {
+          // the current tile's sources are no longer needed once its last
+          // chunk is loaded: the next tile's replace them
+          if (rn == 0) tile_sources(a.rs, a.tile_src, a.n, jn, wsrc);
+          sn = wsrc[rn * 32 + grp];
+        }
+      }
+      if (vn && nvalid > 0) load_seg<kPF>(x + sn * d + c0, vec, nvalid, xn);
       else
 #pragma unroll
         for (int c = 0; c < kPF; ++c) xn[c] = 0.0f;
       if (REWEIGHT && vn && q == 0) {
-        lwn = logw[inx];
-        lpn = lp[inx];
+        lwn = gat ? R : logw[inx];
+        lpn = lp[sn];
       }
     }
     if (MOVE && valid && nvalid > 0) {
@@ -681,7 +745,7 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
           }
         }
       }
-      float* row = x + i * d + c0;
+      float* row = xd + i * d + c0;
       if (vec) {
 #pragma unroll
         for (int v = 0; v < DPL / 4; ++v)
@@ -715,7 +779,7 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       // values are within a factor of two), one FP64 addition
       const float lpi = -0.5f * qs;
       const double lw = lwc + double(lpi - lpc);
-      lp[i] = lpi;
+      lpd[i] = lpi;
       logw[i] = lw;
       mt.add(lw);
       if constexpr (EST) {
@@ -758,9 +822,9 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
 
 // One sampler per launch: the factor's entries are kernel parameters, read by
 // the FMAs straight from the constant bank.
-template <int DPL, bool MOVE, bool REWEIGHT, bool EST = false>
+template <int DPL, bool MOVE, bool REWEIGHT, bool EST = false, bool GATHER = false>
 __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleArgs a, const GaussParamsF32 gp) {
-  move_reweight_body<DPL, MOVE, REWEIGHT, FactorParam, EST>(a, FactorParam{gp}, blockIdx.x, gridDim.x);
+  move_reweight_body<DPL, MOVE, REWEIGHT, FactorParam, EST, GATHER>(a, FactorParam{gp}, blockIdx.x, gridDim.x);
 }
 
 // Batched: block b runs block map[b].y of map[b].z of sampler map[b].x; the
@@ -807,6 +871,14 @@ __device__ __forceinline__ void max_finalize_body(const double* __restrict__ par
     // started from were uniform; after its reweight they are not
     st->est_ready = st->w_uniform;
     st->w_uniform = 0;
+    // a move that gathered a deferred resampling's rows wrote them to the
+    // other buffer, which is now current; the run starts it read are cleared
+    // by the quantise pass that follows
+    if (st->pending) {
+      st->cur ^= 1;
+      st->pending = 0;
+      st->rs_dirty = 1;
+    }
   }
 }
 
@@ -903,8 +975,15 @@ __global__ void k_begin(DevState* st) {
   if (threadIdx.x == 0) st->t += 1;
 }
 
-__global__ void k_commit(DevState* st, int d, int force_flip, int recycle) {
-  if (threadIdx.x < 32) commit_warp(st, d, force_flip, recycle);
+__global__ void k_commit(DevState* st, int d, int force_flip, int recycle, int defer) {
+  if (threadIdx.x < 32) commit_warp(st, d, force_flip, recycle, defer);
+}
+
+__global__ void k_settle(DevState* st) {
+  if (threadIdx.x == 0 && st->pending) {
+    if (!st->err) st->cur ^= 1;
+    st->pending = 0;
+  }
 }
 
 // Batched bookkeeping: thread s handles sampler s.
@@ -993,6 +1072,13 @@ static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, int thr
       } else {
         return cudaErrorInvalidValue;
       }
+    case OP_MOVE_REWEIGHT_GATHER:  // (the same, and gathers a pending resampling's rows)
+      if constexpr (DPL <= 16) {
+        k_move_reweight_lanes<DPL, true, true, true, true><<<grid, threads, 0, s>>>(a, gp);
+        break;
+      } else {
+        return cudaErrorInvalidValue;
+      }
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1073,8 +1159,13 @@ cudaError_t launch_begin(DevState* st, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_commit(DevState* st, int d, int force_flip, int recycle, cudaStream_t s) {
-  k_commit<<<1, 32, 0, s>>>(st, d, force_flip, recycle);
+cudaError_t launch_commit(DevState* st, int d, int force_flip, int recycle, cudaStream_t s, int defer) {
+  k_commit<<<1, 32, 0, s>>>(st, d, force_flip, recycle, defer);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_settle(DevState* st, cudaStream_t s) {
+  k_settle<<<1, 32, 0, s>>>(st);
   return cudaGetLastError();
 }
 

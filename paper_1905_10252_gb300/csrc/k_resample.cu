@@ -112,6 +112,8 @@ __global__ void k_state_init(DevState* st, int64_t n, int64_t t, int F) {
   st->want_cov = 0;
   st->w_uniform = 0;
   st->est_ready = 0;
+  st->pending = 0;
+  st->rs_dirty = 0;
 }
 
 // ---------------------------------------------------------------- max of log w (stateless path)
@@ -188,6 +190,16 @@ __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int 
   // eq. (7) from the move kernel's tile records when it wrote them this
   // iteration, else from the rows
   const bool use_rec = EST && a.est_src && st->est_ready;
+  if (st->rs_dirty) {
+    // the run starts a gathering move consumed (this block's rows), cleared
+    // before the scan writes the next ones
+    const int64_t base = int64_t(blk) * kQTile;
+#pragma unroll 4
+    for (int k = 0; k < kQItems; ++k) {
+      const int64_t i = base + k * kQThreads + threadIdx.x;
+      if (i < a.n && a.runstart[i] >= 0) a.runstart[i] = -1;
+    }
+  }
   if (!st->err) {
     const double m = st->m;
     const int sh_w = 62 - st->F;
@@ -481,6 +493,7 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
   rec.survivors = 0;
   st->survivors = 0;
   st->last = rec;
+  st->rs_dirty = 0;  // (the reduce pass has cleared the consumed run starts)
   if (st->trace) {
     const int64_t idx = st->t - st->trace_t0 - 1;
     if (idx >= 0) st->trace[idx] = rec;
@@ -707,7 +720,7 @@ template <typename V, int CPR, int KU = 8>
 __device__ __forceinline__ void redistribute_body(const RedistArgs& a, const int blk, RedistSmem& sm) {
   int cur = 0;
   if (a.stateful) {
-    if (!(a.force || a.st->flag)) return;
+    if (a.use_pending ? !a.st->pending : !(a.force || a.st->flag)) return;
     cur = a.st->cur;
   }
   // after an error nothing is copied, but the runstart slice is still reset

@@ -139,6 +139,8 @@ ParticleArgs particle_args(const smc_sampler* h) {
   a.epart = reinterpret_cast<double*>(h->ws + h->L.epart);
   a.tg = h->tg;
   a.st = h->st;
+  a.rs = h->rs;
+  a.tile_src = h->tile_src;
   if (h->cfg.flags & SMC_FLAG_TEST_STALL_LIKELIHOOD) a.flags |= PA_STALL_COPIES;
   return a;
 }
@@ -170,6 +172,17 @@ QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies) {
   q.st = h->st;
   q.stats_out = nullptr;
   return q;
+}
+
+// A deferred resampling's rows copied (Algorithm 5, the log w reset) and
+// their buffer made current; both kernels do nothing unless one is pending.
+cudaError_t materialize(smc_sampler* h) {
+  if (!h->defer) return cudaSuccess;
+  RedistArgs r = redist_args(h, 0);
+  r.use_pending = 1;
+  cudaError_t e = launch_redistribute(r, h->stream);
+  if (e == cudaSuccess) e = launch_settle(h->st, h->stream);
+  return e;
 }
 
 RedistArgs redist_args(const smc_sampler* h, int force) {
@@ -227,8 +240,8 @@ cudaError_t launch_move_reweight(smc_sampler* h, const ParticleArgs& a, int* nb)
     return e;
   }
   *nb = h->grid_p;
-  return launch_particles(est_in_move(h) ? OP_MOVE_REWEIGHT_EST : OP_MOVE_REWEIGHT, a, h->grid_p, h->threads_p,
-                          h->stream, gauss_params(h));
+  const int op = h->defer ? OP_MOVE_REWEIGHT_GATHER : (est_in_move(h) ? OP_MOVE_REWEIGHT_EST : OP_MOVE_REWEIGHT);
+  return launch_particles(op, a, h->grid_p, h->threads_p, h->stream, gauss_params(h));
 }
 
 // One iteration of Algorithm 2 (lines 3-10), all on h->stream.
@@ -252,7 +265,9 @@ cudaError_t launch_iteration(smc_sampler* h, bool with_cov) {
   if (e == cudaSuccess && with_cov)
     e = launch_cov(a, nullptr, reinterpret_cast<double*>(h->ws + h->L.covpart), h->L.cov_blocks, h->stream);
   if (!one_q && e == cudaSuccess) e = launch_quant_scan(q, h->stream);
-  if (one_r) {
+  if (h->defer) {  // the next move gathers the rows (smc_materialize, if none follows)
+    if (e == cudaSuccess) e = launch_commit(h->st, h->d, 0, 1, h->stream, 1);
+  } else if (one_r) {
     if (e == cudaSuccess) e = launch_redistribute_commit(redist_args(h, 0), h->d, 0, 1, h->stream);
   } else {
     if (e == cudaSuccess) e = launch_redistribute(redist_args(h, 0), h->stream);
@@ -404,6 +419,9 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
       h->have_gp = true;
     }
   }
+  // deferred redistribution: the gathering move is the records kernel's, and
+  // the quantise and copy passes span several blocks
+  h->defer = (cfg->flags & SMC_FLAG_DEFER_REDISTRIBUTE) && est_in_move(h) && h->L.qblocks > 1 && h->L.ntiles > 1;
   if (e != cudaSuccess) {
     int r = cuda_fail(nullptr, e, "smc_init launch");
     delete h;
@@ -416,6 +434,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
 int smc_move(smc_sampler* h) {
   SMC_RANGE("smc_move");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, materialize(h));
   SMC_TRY(h, launch_begin(h->st, h->stream));
   SMC_TRY(h, launch_particles(OP_MOVE, particle_args(h), h->grid_p, h->threads_p, h->stream, gauss_params(h)));
   return SMC_OK;
@@ -424,6 +443,7 @@ int smc_move(smc_sampler* h) {
 int smc_reweight(smc_sampler* h) {
   SMC_RANGE("smc_reweight");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, materialize(h));
   if (h->lg_tc) {
     SMC_TRY(h, launch_logistic_tc(particle_args(h), h->grid_lg, h->stream));
     SMC_TRY(h, launch_stats(h, 0, h->grid_lg));
@@ -437,6 +457,7 @@ int smc_reweight(smc_sampler* h) {
 int smc_estimate(smc_sampler* h, double* mean_dev, double* cov_dev) {
   SMC_RANGE("smc_estimate");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, materialize(h));
   if (mean_dev) SMC_TRY(h, launch_copy_mean(h->st, mean_dev, h->d, h->stream));
   if (cov_dev)
     SMC_TRY(h, launch_cov(particle_args(h), cov_dev, reinterpret_cast<double*>(h->ws + h->L.covpart),
@@ -447,6 +468,7 @@ int smc_estimate(smc_sampler* h, double* mean_dev, double* cov_dev) {
 int smc_resample(smc_sampler* h, int32_t* ncopies_dev, int32_t* did_resample_dev) {
   SMC_RANGE("smc_resample");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, materialize(h));
   if (ncopies_dev) SMC_TRY(h, launch_quant_scan(quant_args(h, 1, ncopies_dev), h->stream));
   if (did_resample_dev)
     SMC_TRY(h, cudaMemcpyAsync(did_resample_dev, &h->st->flag, sizeof(int32_t), cudaMemcpyDeviceToDevice,
@@ -458,6 +480,7 @@ int smc_redistribute(smc_sampler* h, const int32_t* ncopies_dev) {
   SMC_RANGE("smc_redistribute");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   if (!ncopies_dev) return fail(h, SMC_EINVAL, "null ncopies");
+  SMC_TRY(h, materialize(h));
   NcScanArgs s{};
   s.n = h->n;
   s.ncopies = ncopies_dev;
@@ -538,14 +561,14 @@ int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host,
     SMC_TRY(h, launch_quant_scan(q, s));
   }
   SMC_TRY(h, rec(5));
-  {
+  if (!h->defer) {  // (deferred: the next iteration's move gathers the rows)
     SMC_RANGE("redistribute");
     SMC_TRY(h, launch_redistribute(redist_args(h, 0), s));
   }
   SMC_TRY(h, rec(6));
   {
     SMC_RANGE("commit");
-    SMC_TRY(h, launch_commit(h->st, h->d, 0, 1, s));
+    SMC_TRY(h, launch_commit(h->st, h->d, 0, 1, s, h->defer ? 1 : 0));
   }
   SMC_TRY(h, rec(7));
   return SMC_OK;
@@ -575,8 +598,16 @@ int smc_read_stats(smc_sampler* h, smc_iter_stats* out_host) {
 
 int smc_current(smc_sampler* h, int32_t* which_host) {
   if (!h || !which_host) return fail(h, SMC_EINVAL, "null argument");
+  SMC_TRY(h, materialize(h));
   SMC_TRY(h, cudaStreamSynchronize(h->stream));
   SMC_TRY(h, cudaMemcpy(which_host, &h->st->cur, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return SMC_OK;
+}
+
+int smc_materialize(smc_sampler* h) {
+  SMC_RANGE("smc_materialize");
+  if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, materialize(h));
   return SMC_OK;
 }
 

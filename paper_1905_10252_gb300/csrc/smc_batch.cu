@@ -246,10 +246,13 @@ int smc_batch_create(smc_batch** out, smc_sampler* const* members, int32_t count
   const BatchLayout L = batch_layout(plan);
   if (ws_bytes < L.total) return bfail(nullptr, SMC_ENOMEM, "workspace too small");
   // the batch's stream waits for the members' queued work (device-side
-  // ordering: one event, recorded on each member stream in turn)
+  // ordering: one event, recorded on each member stream in turn), after any
+  // redistribution a member left pending is completed on its stream
   {
     cudaEvent_t ev = nullptr;
-    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < count && e == cudaSuccess; ++s) e = materialize(members[s]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     const cudaStream_t bs = reinterpret_cast<cudaStream_t>(stream);
     for (int s = 0; s < count && e == cudaSuccess; ++s) {
       if (members[s]->stream == bs) continue;

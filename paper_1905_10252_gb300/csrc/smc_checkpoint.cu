@@ -72,7 +72,8 @@ int smc_checkpoint_save(smc_sampler* h, void* host_dst, size_t bytes) {
   // the state block first (it says which buffer holds the particles); all
   // copies are ordered after the work already queued on the sampler's stream
   DevState* st = reinterpret_cast<DevState*>(p);
-  cudaError_t e = cudaMemcpyAsync(st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = materialize(h);  // (a deferred redistribution completed first)
+  if (e == cudaSuccess) e = cudaMemcpyAsync(st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return ck_fail(h, SMC_ECUDA, cudaGetErrorString(e));
   if (st->err != SMC_OK) return ck_fail(h, st->err, "the sampler holds an unreported error: nothing saved");
@@ -107,6 +108,8 @@ int smc_checkpoint_load(smc_sampler* h, const void* host_src, size_t bytes) {
   p += sizeof st;
   st.cur = 0;
   st.err = 0;
+  st.pending = 0;
+  st.rs_dirty = 0;
   st.trace = nullptr;
   st.mean_out = nullptr;
   st.fhat_out = nullptr;
@@ -114,7 +117,10 @@ int smc_checkpoint_load(smc_sampler* h, const void* host_src, size_t bytes) {
   const size_t xb = size_t(h->n) * h->esize * h->d, lb = size_t(h->n) * h->esize;
   // stream-ordered copies, complete before the call returns (the host buffer
   // may be released afterwards)
-  cudaError_t e = cudaMemcpyAsync(h->st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream);
+  // (a redistribution this sampler left pending is completed first, which
+  // also clears its run starts)
+  cudaError_t e = materialize(h);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->x[0], p, xb, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->lp[0], p + xb, lb, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)

@@ -49,6 +49,8 @@ struct smc_sampler {
   // FP32 Gaussian factor for the move / reweight kernel's parameters
   smc::GaussParamsF32 gp;
   bool have_gp;
+  // SMC_FLAG_DEFER_REDISTRIBUTE honoured: resampled rows are gathered by the next move
+  bool defer;
   // CUDA graph of one iteration (with and without the covariance stage)
   cudaGraphExec_t g_iter[2];
   std::string err;
@@ -59,6 +61,8 @@ namespace smc {
 ParticleArgs particle_args(const smc_sampler* h);
 QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies);
 RedistArgs redist_args(const smc_sampler* h, int force);
+// Completes a deferred redistribution on h's stream (no-op without the flag).
+cudaError_t materialize(smc_sampler* h);
 int sm_count();
 
 }  // namespace smc

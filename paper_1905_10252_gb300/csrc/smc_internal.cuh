@@ -49,6 +49,14 @@ struct alignas(256) DevState {
   int32_t F;            // fixed-point scale of the weights
   int32_t L;            // bit length of S (ncopies division)
   int32_t w_uniform;    // 1: every log w equals reset_logw (the last iteration resampled)
+  // deferred redistribution (samplers created with SMC_FLAG_DEFER_REDISTRIBUTE):
+  // pending = 1: iteration t resampled but its rows still sit in buffer cur, to
+  // be gathered through the run starts rs / tile_src by the next move (or by
+  // smc_materialize); log w is then reset_logw for every particle whatever
+  // the array holds.  rs_dirty = 1: a gathering move consumed the run starts,
+  // which the next quantise pass clears before the scan writes new ones.
+  int32_t pending;
+  int32_t rs_dirty;
   double m;             // max_i log w
   double lse;           // LSE_t
   double lse_prev;      // LSE_{t-1} (0 after a reset)
@@ -396,10 +404,13 @@ __device__ __forceinline__ long long warp_max_ll(long long v) {
 // (0 after a reset), and the recycling sums of eq. (6) take f_t with weight
 // c_t -- one column per lane, each with explicitly rounded FP64 operations
 // (the same bits whichever kernel runs it).
-__device__ __forceinline__ void commit_warp(DevState* st, int d, int force_flip, int recycle) {
+// defer: a resampled iteration leaves its rows in place and marks them
+// pending instead of swapping (the next move gathers them).
+__device__ __forceinline__ void commit_warp(DevState* st, int d, int force_flip, int recycle, int defer = 0) {
   const int lane = threadIdx.x & 31;
   const int err = st->err, flag = st->flag;
-  const bool flip = force_flip || (flag && !err);
+  const bool pend = defer && flag && !err;
+  const bool flip = force_flip || (flag && !err && !defer);
   if (recycle && !err) {
     const double lc = st->logc, rmax = st->rc_max;
     const double M = fmax(rmax, lc);
@@ -427,9 +438,10 @@ __device__ __forceinline__ void commit_warp(DevState* st, int d, int force_flip,
     }
   }
   if (flip) st->cur ^= 1;
-  st->lse_prev = flip ? 0.0 : st->lse;
+  st->pending = pend ? 1 : 0;
+  st->lse_prev = (flip || pend) ? 0.0 : st->lse;
   // a resampled iteration leaves every log w at reset_logw
-  st->w_uniform = (flip && !err) ? 1 : 0;
+  st->w_uniform = ((flip || pend) && !err) ? 1 : 0;
 }
 
 }  // namespace smc

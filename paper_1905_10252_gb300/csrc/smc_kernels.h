@@ -42,7 +42,8 @@ constexpr int kLgRows = 256;
 constexpr int kLgK = 32;
 constexpr size_t kLgTileBytes = size_t(kLgRows) * kLgK * 2 * 2;
 
-enum { OP_INIT = 0, OP_MOVE = 1, OP_REWEIGHT = 2, OP_MOVE_REWEIGHT = 3, OP_MOVE_REWEIGHT_EST = 4 };
+enum { OP_INIT = 0, OP_MOVE = 1, OP_REWEIGHT = 2, OP_MOVE_REWEIGHT = 3, OP_MOVE_REWEIGHT_EST = 4,
+       OP_MOVE_REWEIGHT_GATHER = 5 };  // (5: OP_MOVE_REWEIGHT_EST that also gathers a pending resampling's rows)
 
 // FP32 Gaussian target passed by value as a kernel parameter (constant bank):
 // the lower triangle of L^-1 packed row by row (row r holds r + 1 entries at
@@ -82,6 +83,9 @@ struct ParticleArgs {
   double* epart;  // eq. (7) records {M_r, sum e x} per 256-particle tile (1 + d doubles each)
   const TargetDev* tg;
   DevState* st;
+  // a pending resampling's run starts and copy-tile sources (gathering move)
+  const int32_t* rs;
+  const int32_t* tile_src;
 };
 
 struct QuantArgs {
@@ -145,7 +149,7 @@ struct RedistArgs {
   double reset_logw;
   DevState* st;
   int32_t stateful;      // 1: choose buffers by st->cur, honour st->flag / st->err
-  int32_t pad;
+  int32_t use_pending;   // stateful: copy iff st->pending (a deferred resampling), not st->flag
 };
 
 struct NcScanArgs {
@@ -179,7 +183,10 @@ cudaError_t launch_max_finalize(const double* part, int nb, DevState* st, cudaSt
 // eq. (7) covariance: grid blocks write covpart[grid][D(D+1)/2], then a fixed-order sum
 cudaError_t launch_cov(const ParticleArgs& a, double* cov, double* covpart, int grid, cudaStream_t s);
 cudaError_t launch_begin(DevState* st, cudaStream_t s);
-cudaError_t launch_commit(DevState* st, int d, int force_flip, int recycle, cudaStream_t s);
+cudaError_t launch_commit(DevState* st, int d, int force_flip, int recycle, cudaStream_t s, int defer = 0);
+// Ends a pending (deferred) redistribution after its copy: the copied rows'
+// buffer becomes current.
+cudaError_t launch_settle(DevState* st, cudaStream_t s);
 cudaError_t launch_copy_mean(const DevState* st, double* out, int d, cudaStream_t s);
 cudaError_t launch_step_setup(DevState* st, smc_iter_stats* trace, double* mean_out, double* fhat_out,
                               double* cov_out, cudaStream_t s);

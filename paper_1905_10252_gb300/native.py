@@ -20,10 +20,12 @@ SMC_GAUSS, SMC_LOGISTIC, SMC_STUDENT_T = 1, 2, 3
 RESAMPLE_ESS, RESAMPLE_ALWAYS, RESAMPLE_NEVER = 0, 1, 2
 FLAG_LOGISTIC_CUDA_CORES = 1  # SMC_FLAG_LOGISTIC_CUDA_CORES
 FLAG_TEST_STALL_LIKELIHOOD = 2  # SMC_FLAG_TEST_STALL_LIKELIHOOD
+FLAG_DEFER_REDISTRIBUTE = 4  # SMC_FLAG_DEFER_REDISTRIBUTE
 
 EXPORTED = [
     "smc_workspace_bytes", "smc_init", "smc_move", "smc_reweight", "smc_estimate", "smc_resample",
-    "smc_redistribute", "smc_step", "smc_step_profile", "smc_sync", "smc_read_stats", "smc_current", "smc_destroy",
+    "smc_redistribute", "smc_step", "smc_step_profile", "smc_sync", "smc_read_stats", "smc_current", "smc_materialize",
+    "smc_destroy",
     "smc_last_error", "smc_redistribute_ws_bytes", "smc_redistribute_raw", "smc_resample_raw", "smc_ws_status",
     "smc_redistribute_raw_noalloc", "smc_batch_ws_bytes", "smc_batch_create", "smc_batch_step",
     "smc_batch_step_profile", "smc_batch_set_variant", "smc_batch_tune", "smc_batch_sync", "smc_batch_destroy", "smc_batch_last_error",
@@ -93,7 +95,7 @@ def _declare(L: C.CDLL) -> None:
     vp, i32, i64, u64, dbl, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_size_t
     L.smc_workspace_bytes.argtypes = [C.POINTER(smc_config), C.POINTER(sz)]
     L.smc_init.argtypes = [C.POINTER(vp), C.POINTER(smc_config), vp, vp, vp, vp, vp, vp, sz, vp]
-    for name in ("smc_move", "smc_reweight", "smc_sync", "smc_destroy"):
+    for name in ("smc_move", "smc_reweight", "smc_sync", "smc_materialize", "smc_destroy"):
         getattr(L, name).argtypes = [vp]
     L.smc_estimate.argtypes = [vp, vp, vp]
     L.smc_resample.argtypes = [vp, vp, vp]
@@ -379,6 +381,11 @@ class Sampler:
 
     def sync(self) -> None:
         _check(lib().smc_sync(self.h), self.h)
+
+    def materialize(self) -> None:
+        """Completes a redistribution deferred by FLAG_DEFER_REDISTRIBUTE (the
+        rows, log pi and log w in self's buffers are then the state)."""
+        self._call(lib().smc_materialize)
 
     def stats(self) -> dict:
         s = smc_iter_stats()
