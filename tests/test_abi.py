@@ -169,3 +169,23 @@ def test_stateless_calls_reject_bad_arguments_host_only(built):
     out = ctypes.c_size_t()
     assert L.smc_nearly_sort_ws_bytes(0, ctypes.byref(out)) == EINVAL
     assert L.smc_nearly_sort_ws_bytes(5000, ctypes.byref(out)) == 0 and out.value >= 2 * 4 * 2
+
+
+def test_binding_constants_match_header():
+    """Status codes, dtypes, targets, resampling modes and flags: the values
+    the binding passes are the header's (enumerators and #defines)."""
+    from paper_1905_10252_gb300 import native
+
+    src = re.sub(r"/\*.*?\*/", "", (ROOT / "include" / "smc.h").read_text(), flags=re.S)
+    values = {k: int(v) for k, v in re.findall(r"\b(SMC_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    values.update({k: int(v) for k, v in re.findall(r"^#define\s+(SMC_[A-Z0-9_]+)\s+(\d+)\s*$", src, flags=re.M)})
+    checked = 0
+    for name, v in values.items():
+        py = name[len("SMC_"):] if name.startswith(("SMC_FLAG_", "SMC_RESAMPLE_")) else name
+        if hasattr(native, py):
+            assert getattr(native, py) == v, (name, getattr(native, py), v)
+            checked += 1
+    for required in ("SMC_OK", "SMC_ENONFINITE", "SMC_F32", "SMC_GAUSS", "SMC_RESAMPLE_ALWAYS",
+                     "SMC_FLAG_DEFER_REDISTRIBUTE"):
+        assert required in values
+    assert checked >= 16
