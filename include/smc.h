@@ -74,8 +74,12 @@ typedef enum { SMC_RESAMPLE_ESS = 0, SMC_RESAMPLE_ALWAYS = 1, SMC_RESAMPLE_NEVER
  * iteration's move reads each particle's row from its source (the copy fused
  * into the move kernel, which saves one write and one read of every row), so
  * the rows, log pi and log w in the caller's buffers are the sampler's state
- * only after smc_materialize, smc_current or any other call on the sampler.
- * The particles, weights, estimates and statistics are bit-identical to those
+ * only after one of the calls that complete a pending copy: smc_materialize,
+ * smc_current, smc_move, smc_reweight, smc_estimate, smc_resample,
+ * smc_redistribute, smc_checkpoint_save, smc_checkpoint_load or
+ * smc_batch_create.  smc_step, smc_step_profile, smc_sync and smc_read_stats
+ * leave it pending (a caller reading x / log w after smc_sync alone sees the
+ * rows before the copy and log w before the reset).  The particles, weights, estimates and statistics are bit-identical to those
  * without the flag.  Honoured by FP32 Gaussian samplers with D <= 16 and
  * N > 4096 (whose move kernel forms the eq. (7) sums); ignored otherwise. */
 #define SMC_FLAG_DEFER_REDISTRIBUTE 4
@@ -84,7 +88,7 @@ typedef struct {
   int64_t n;              /* N particles */
   int32_t d;              /* D state dimension */
   int32_t dtype;          /* smc_dtype of particles and log pi */
-  uint64_t seed;          /* Philox4x64-10 key word 0 */
+  uint64_t seed;          /* Philox4x32-10 key: (seed low 32 bits, seed high 32 bits) */
   int32_t target;         /* smc_target_kind */
   int32_t resample_mode;  /* smc_resample_mode */
   double step;            /* random-walk proposal std eps: x_t = x_{t-1} + eps z (Sec. 5.2.3) */

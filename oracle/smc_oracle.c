@@ -21,6 +21,8 @@
  *   orc_philox4x32_10       pinned: cuRAND host generator PHILOX4_32_10 (independent library)
  *   orc_log, orc_sincos2pi  pinned: libm / mpmath within 2 ulp
  *   orc_normals             pinned: moments over 2^16 draws; Box-Muller identity
+ *   orc_move                pinned: each coordinate the correctly rounded x + eps z (exact
+ *                           rationals); increment std = eps (a variance reading fails)
  *   orc_expfx               pinned: Decimal exp within 2^-54 relative; tables vs exact roots
  *   orc_cholesky, logpi     pinned: numpy.linalg inverse quadratic form
  *   orc_lse_ess             pinned: closed forms (equal / one-hot weights)

@@ -3,7 +3,7 @@
 // Shared by the kernel translation units of the library only.  Contents:
 //  * DevState: the sampler's device-resident control block (iteration t,
 //    current ping-pong buffer, resampling decision, error word, statistics).
-//  * Philox4x64-10 (Salmon et al., SC'11) for counter-based normals keyed by
+//  * Philox4x32-10 (Salmon et al., SC'11) for counter-based normals keyed by
 //    (seed, iteration, particle).
 //  * IEEE-exact log and sincos(2 pi a) for the FP64 Box-Muller transform: only
 //    correctly rounded basic operations, each written with an explicit
