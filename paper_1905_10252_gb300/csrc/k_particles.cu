@@ -580,37 +580,85 @@ __device__ __forceinline__ void warp_write_est(float em, double R, float (&v)[DM
 // the first row of each 2048-row copy tile; run starts between that row and
 // the move tile's first row are found by a backward search 32 rows at a time
 // (in all but heavily duplicated regions the 32 rows just before hold one).
-// The warp writes the tile's 256 sources to out[] (clamped into [0, n), as
-// the copy kernel clamps them); every lane of the warp takes part.
-__device__ __forceinline__ void tile_sources(const int32_t* __restrict__ rs, const int32_t* __restrict__ tile_src,
-                                             int64_t n, int64_t jt, int32_t* __restrict__ out) {
+//
+// The tile's run starts are staged into shared memory one tile ahead of use
+// with asynchronous copies (cp.async), so that resolving a tile's sources
+// does not wait on memory:
+//   stage[0, 256)   rs[k0 .. k0 + 256)    (entries at or beyond n: masked)
+//   stage[256, 288) rs[k0 - 32 .. k0)     (the first step of the backward search)
+//   stage[288]      tile_src[k0 / 2048]
+// tile_sources_issue starts the copies; tile_sources_finish waits for them
+// and writes the tile's 256 sources to out[] (clamped into [0, n), as the copy
+// kernel clamps them).  Every lane of the warp takes part in both.
+constexpr int kStage = kEstTile + 32 + 4;
+
+__device__ __forceinline__ void cp_async16(int32_t* smem, const int32_t* gmem, int src_bytes) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(int32_t* smem, const int32_t* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void tile_sources_issue(const int32_t* __restrict__ rs,
+                                                   const int32_t* __restrict__ tile_src, int64_t n, int64_t jt,
+                                                   int32_t* __restrict__ stage) {
   const int lane = threadIdx.x & 31;
   const int64_t k0 = jt * kEstTile;
   const int64_t t0 = (k0 / kRTile) * kRTile;
-  int carry = tile_src[k0 / kRTile];
-  for (int64_t q = k0 - 32; q >= t0; q -= 32) {
-    int m = rs[q + lane];
+  // lane l: entries [8l, 8l + 8) as two 16-byte pieces.  rs is 256-byte
+  // aligned and padded to a multiple of 256 bytes, so a piece that starts
+  // below n stays inside the array; pieces at or beyond n copy nothing
+  // (zero-filled, masked when the sources are resolved).
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t k = k0 + 8 * lane + 4 * h;
+    const bool in = k < n;
+    cp_async16(stage + 8 * lane + 4 * h, rs + (in ? k : 0), in ? 16 : 0);
+  }
+  if (k0 > t0) cp_async4(stage + kEstTile + lane, rs + (k0 - 32 + lane));
+  if (lane == 0) cp_async4(stage + kEstTile + 32, tile_src + k0 / kRTile);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile_sources_finish(const int32_t* __restrict__ rs, int64_t n, int64_t jt,
+                                                    const int32_t* __restrict__ stage, int32_t* __restrict__ out) {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncwarp();  // every lane's copies have landed
+  const int lane = threadIdx.x & 31;
+  const int64_t k0 = jt * kEstTile;
+  const int64_t t0 = (k0 / kRTile) * kRTile;
+  int carry = stage[kEstTile + 32];
+  if (k0 > t0) {
+    int m = stage[kEstTile + lane];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (m >= 0) {
       carry = max(carry, m);
-      break;
-    }
-  }
-  int v[kEstTile / 32];
+    } else {
+      // a long run of copies: continue the search from global memory
+      for (int64_t q = k0 - 64; q >= t0; q -= 32) {
+        int mm = rs[q + lane];
 #pragma unroll
-  for (int r = 0; r < kEstTile / 32; ++r) {
-    const int64_t k = k0 + r * 32 + lane;
-    v[r] = k < n ? rs[k] : -1;
+        for (int o = 16; o > 0; o >>= 1) mm = max(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+        if (mm >= 0) {
+          carry = max(carry, mm);
+          break;
+        }
+      }
+    }
   }
   const int last = int(n - 1);
 #pragma unroll
   for (int r = 0; r < kEstTile / 32; ++r) {
-    const int sk = min(max(max(warp_incl_max_i32(v[r]), carry), 0), last);
+    const int64_t k = k0 + r * 32 + lane;
+    const int v = k < n ? stage[r * 32 + lane] : -1;
+    const int sk = min(max(max(warp_incl_max_i32(v), carry), 0), last);
     out[r * 32 + lane] = sk;
     carry = __shfl_sync(0xffffffffu, sk, 31);
   }
-  __syncwarp();
+  __syncwarp();  // out[] written, stage[] read: the next issue may overwrite it
 }
 
 template <int DPL, bool MOVE, bool REWEIGHT, typename FS, bool EST = false, bool GATHER = false>
@@ -649,7 +697,19 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
   float* xd = gat ? static_cast<float*>(cur ? a.x[0] : a.x[1]) : x;
   float* lpd = gat ? static_cast<float*>(cur ? a.logpi[0] : a.logpi[1]) : lp;
   __shared__ int32_t s_src[GATHER ? kPThreads / 32 : 1][GATHER ? kEstTile : 1];
+  __shared__ __align__(16) int32_t s_stage[GATHER ? kPThreads / 32 : 1][GATHER ? kStage : 4];
   int32_t* const wsrc = s_src[GATHER ? (threadIdx.x >> 5) : 0];
+  int32_t* const wstage = s_stage[GATHER ? (threadIdx.x >> 5) : 0];
+  // the run starts this move reads, and the other array (reset to -1 here
+  // when a previous gather left it dirty; see DevState)
+  const int32_t* rs_rd = nullptr;
+  int32_t* rs_clr = nullptr;
+  if constexpr (GATHER) {
+    if (gat) {
+      rs_rd = rs_now(a.rs, a.rs_alt, a.st);
+      if (a.rs_alt && a.st->rs_dirty) rs_clr = a.st->rs_w ? a.rs : a.rs_alt;
+    }
+  }
   const int d = a.d;
   constexpr int q = 0, c0 = 0;  // one lane per particle: it owns coordinates [0, d)
   const int nvalid = d;
@@ -674,8 +734,11 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
     int64_t si = i;
     if constexpr (GATHER) {
       if (gat && j < ntile) {
-        tile_sources(a.rs, a.tile_src, a.n, j, wsrc);
+        tile_sources_issue(rs_rd, a.tile_src, a.n, j, wstage);
+        tile_sources_finish(rs_rd, a.n, j, wstage, wsrc);
         si = wsrc[grp];
+        // the warp's next tile, staged while this one is processed
+        if (j + W < ntile) tile_sources_issue(rs_rd, a.tile_src, a.n, j + W, wstage);
       }
     }
     if (j < ntile && i < a.n && nvalid > 0) load_seg<DPL>(x + si * d + c0, vec, nvalid, xo);
@@ -713,8 +776,12 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       if constexpr (GATHER) {
         if (gat && jn < ntile) {
           // the current tile's sources are no longer needed once its last
-          // chunk is loaded: the next tile's replace them
-          if (rn == 0) tile_sources(a.rs, a.tile_src, a.n, jn, wsrc);
+          // chunk is loaded: the next tile's (staged since this tile began)
+          // replace them, and the tile after that is staged
+          if (rn == 0) {
+            tile_sources_finish(rs_rd, a.n, jn, wstage, wsrc);
+            if (jn + W < ntile) tile_sources_issue(rs_rd, a.tile_src, a.n, jn + W, wstage);
+          }
           sn = wsrc[rn * 32 + grp];
         }
       }
@@ -781,6 +848,9 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       const double lw = lwc + double(lpi - lpc);
       lpd[i] = lpi;
       logw[i] = lw;
+      if constexpr (GATHER) {
+        if (rs_clr) rs_clr[i] = -1;
+      }
       mt.add(lw);
       if constexpr (EST) {
         if (est_on) {
@@ -872,11 +942,13 @@ __device__ __forceinline__ void max_finalize_body(const double* __restrict__ par
     st->est_ready = st->w_uniform;
     st->w_uniform = 0;
     // a move that gathered a deferred resampling's rows wrote them to the
-    // other buffer, which is now current; the run starts it read are cleared
-    // by the quantise pass that follows
+    // other buffer, which is now current; the run starts it read stay set,
+    // so the next scan writes the other array (which that move reset if it
+    // was dirty) and this one is marked dirty
     if (st->pending) {
       st->cur ^= 1;
       st->pending = 0;
+      st->rs_w ^= 1;
       st->rs_dirty = 1;
     }
   }

@@ -114,6 +114,7 @@ __global__ void k_state_init(DevState* st, int64_t n, int64_t t, int F) {
   st->est_ready = 0;
   st->pending = 0;
   st->rs_dirty = 0;
+  st->rs_w = 0;
 }
 
 // ---------------------------------------------------------------- max of log w (stateless path)
@@ -190,16 +191,6 @@ __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int 
   // eq. (7) from the move kernel's tile records when it wrote them this
   // iteration, else from the rows
   const bool use_rec = EST && a.est_src && st->est_ready;
-  if (st->rs_dirty) {
-    // the run starts a gathering move consumed (this block's rows), cleared
-    // before the scan writes the next ones
-    const int64_t base = int64_t(blk) * kQTile;
-#pragma unroll 4
-    for (int k = 0; k < kQItems; ++k) {
-      const int64_t i = base + k * kQThreads + threadIdx.x;
-      if (i < a.n && a.runstart[i] >= 0) a.runstart[i] = -1;
-    }
-  }
   if (!st->err) {
     const double m = st->m;
     const int sh_w = 62 - st->F;
@@ -493,7 +484,6 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
   rec.survivors = 0;
   st->survivors = 0;
   st->last = rec;
-  st->rs_dirty = 0;  // (the reduce pass has cleared the consumed run starts)
   if (st->trace) {
     const int64_t idx = st->t - st->trace_t0 - 1;
     if (idx >= 0) st->trace[idx] = rec;
@@ -567,7 +557,7 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
     const int64_t i = i0 + q;
     if (hi > lo && i < n) {
       ++nsurv;
-      if (a.write_rs) a.runstart[lo] = int32_t(i);
+      if (a.write_rs) rs_now(a.runstart, a.runstart_alt, st)[lo] = int32_t(i);
       // every redistribute tile whose first output row lies in [lo, hi)
       for (uint64_t kb = ((lo + kRTile - 1) / kRTile) * kRTile; kb < hi && kb < uint64_t(n); kb += kRTile)
         a.tile_src[kb / kRTile] = int32_t(i);
@@ -593,7 +583,7 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
   }
 }
 
-__global__ void __launch_bounds__(kQThreads) k_quant_scan(QuantArgs a) { quant_scan_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(kQThreads, 3) k_quant_scan(QuantArgs a) { quant_scan_body(a, blockIdx.x); }
 
 // ---------------------------------------------------------------- standalone ncopies scan
 // Thread t of a block owns the 16 consecutive entries [base + 16 t, +16) of
@@ -687,6 +677,7 @@ __global__ void __launch_bounds__(kQThreads) k_nc_scan(NcScanArgs a) {
     for (int k = threadIdx.x; k < int(btot); k += blockDim.x) win[k] = -1;
     __syncthreads();
   }
+  int32_t* __restrict__ rsa = rs_now(a.runstart, a.runstart_alt, a.st);
   uint64_t o = o0;
 #pragma unroll
   for (int q = 0; q < kQItems; ++q) {
@@ -695,7 +686,7 @@ __global__ void __launch_bounds__(kQThreads) k_nc_scan(NcScanArgs a) {
       if (staged)
         win[o - w0] = int32_t(i);
       else
-        a.runstart[o] = int32_t(i);
+        rsa[o] = int32_t(i);
       for (uint64_t kb = ((o + kRTile - 1) / kRTile) * kRTile; kb < o + uint32_t(c[q]) && kb < uint64_t(n); kb += kRTile)
         a.tile_src[kb / kRTile] = int32_t(i);
     }
@@ -703,7 +694,7 @@ __global__ void __launch_bounds__(kQThreads) k_nc_scan(NcScanArgs a) {
   }
   if (staged) {
     __syncthreads();
-    int32_t* __restrict__ rs = a.runstart + w0;
+    int32_t* __restrict__ rs = rsa + w0;
     for (int k = threadIdx.x; k < int(btot); k += blockDim.x) rs[k] = win[k];
   }
 }
@@ -732,7 +723,7 @@ __device__ __forceinline__ void redistribute_body(const RedistArgs& a, const int
   const int len = int(n - k0 < kRTile ? n - k0 : int64_t(kRTile));
   // this tile's slice of runstart (survivor runs starting here), reset to -1
   // for the next resampling
-  int32_t* __restrict__ rs = a.runstart + k0;
+  int32_t* __restrict__ rs = rs_now(a.runstart, a.runstart_alt, a.st) + k0;
   {
     constexpr int kItems = kRTile / kRThreads;
     int32_t v[kItems];
@@ -912,7 +903,8 @@ __global__ void __launch_bounds__(kRThreads) k_identity_runs_batch(const RedistA
   const RedistArgs a = ra[m.x];
   const int64_t k0 = int64_t(m.y) * kRTile;
   const int len = int(a.n - k0 < kRTile ? a.n - k0 : int64_t(kRTile));
-  for (int k = threadIdx.x; k < len; k += kRThreads) a.runstart[k0 + k] = int32_t(k0 + k);
+  int32_t* __restrict__ rs = rs_now(a.runstart, a.runstart_alt, a.st);
+  for (int k = threadIdx.x; k < len; k += kRThreads) rs[k0 + k] = int32_t(k0 + k);
   if (threadIdx.x == 0) const_cast<int32_t*>(a.tile_src)[m.y] = int32_t(k0);
 }
 

@@ -32,7 +32,8 @@ int quant_shift(int64_t n) {
   return F > 62 ? 62 : F;
 }
 
-Layout layout_for(int64_t n, int d, int m = 0) {
+// two_rs: a second run-start array (SMC_FLAG_DEFER_REDISTRIBUTE samplers)
+Layout layout_for(int64_t n, int d, int m = 0, bool two_rs = false) {
   Layout L{};
   L.qblocks = int(div_up(n, kQTile));
   L.ntiles = int(div_up(n, kRTile));
@@ -55,6 +56,11 @@ Layout layout_for(int64_t n, int d, int m = 0) {
   p = align_up(p + size_t(L.qblocks) * size_t(d < 1 ? 1 : d) * sizeof(double));
   L.rs = p;
   p = align_up(p + size_t(n) * sizeof(int32_t));
+  L.rs_alt = 0;
+  if (two_rs) {
+    L.rs_alt = p;
+    p = align_up(p + size_t(n) * sizeof(int32_t));
+  }
   L.wbuf = p;
   p = align_up(p + size_t(n) * sizeof(uint64_t));
   L.tile_src = p;
@@ -76,6 +82,8 @@ Layout layout_for(int64_t n, int d, int m = 0) {
 }
 
 int logistic_rows(const smc_config* c) { return c->target == SMC_LOGISTIC ? c->m : 0; }
+
+bool wants_two_rs(const smc_config* c) { return (c->flags & SMC_FLAG_DEFER_REDISTRIBUTE) != 0; }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -140,6 +148,7 @@ ParticleArgs particle_args(const smc_sampler* h) {
   a.tg = h->tg;
   a.st = h->st;
   a.rs = h->rs;
+  a.rs_alt = h->rs_alt;
   a.tile_src = h->tile_src;
   if (h->cfg.flags & SMC_FLAG_TEST_STALL_LIKELIHOOD) a.flags |= PA_STALL_COPIES;
   return a;
@@ -156,6 +165,7 @@ QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies) {
   q.qpart = h->qpart;
   q.cbase = h->cbase;
   q.runstart = h->rs;
+  q.runstart_alt = h->rs_alt;
   q.write_rs = force ? 0 : 1;  // the fused step feeds redistribute; smc_resample does not
   q.wbuf = h->wbuf;
   q.ncopies = ncopies;
@@ -191,6 +201,7 @@ RedistArgs redist_args(const smc_sampler* h, int force) {
   r.row_bytes = int32_t(h->esize * h->d);
   r.lp_bytes = int32_t(h->esize);
   r.runstart = h->rs;
+  r.runstart_alt = h->rs_alt;
   r.tile_src = h->tile_src;
   r.ntiles = h->L.ntiles;
   r.force = force;
@@ -320,7 +331,7 @@ int smc_workspace_bytes(const smc_config* cfg, size_t* bytes) {
   int rc = check_config(cfg);
   if (rc) return rc;
   if (!bytes) return fail(nullptr, SMC_EINVAL, "null bytes");
-  *bytes = layout_for(cfg->n, cfg->d, logistic_rows(cfg)).total;
+  *bytes = layout_for(cfg->n, cfg->d, logistic_rows(cfg), wants_two_rs(cfg)).total;
   return SMC_OK;
 }
 
@@ -339,7 +350,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   if (!aligned(x_dev, 16) || !aligned(x_alt_dev, 16) || !aligned(logw_dev, 8) || !aligned(logpi_dev, es) ||
       !aligned(logpi_alt_dev, es))
     return fail(nullptr, SMC_EINVAL, "particle buffers must be 16-byte aligned");
-  const Layout L = layout_for(cfg->n, cfg->d, logistic_rows(cfg));
+  const Layout L = layout_for(cfg->n, cfg->d, logistic_rows(cfg), wants_two_rs(cfg));
   if (workspace_bytes < L.total) return fail(nullptr, SMC_ENOMEM, "workspace too small");
   cudaError_t e = upload_expfx_table();
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "upload_expfx_table");
@@ -366,6 +377,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   h->cbase = reinterpret_cast<uint64_t*>(h->ws + L.cbase);
   h->xpart = h->ws + L.xpart;
   h->rs = reinterpret_cast<int32_t*>(h->ws + L.rs);
+  h->rs_alt = L.rs_alt ? reinterpret_cast<int32_t*>(h->ws + L.rs_alt) : nullptr;
   h->wbuf = reinterpret_cast<uint64_t*>(h->ws + L.wbuf);
   h->tile_src = reinterpret_cast<int32_t*>(h->ws + L.tile_src);
   // particle kernels: 256-thread blocks, at most 8 per SM (grid-stride);
@@ -387,6 +399,8 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   // Algorithm 2, line 1, then the statistics of w_0 (LSE_0 becomes LSE_{t-1})
   e = cudaMemsetAsync(h->tg, 0, sizeof(TargetDev), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->rs, 0xFF, size_t(h->n) * sizeof(int32_t), h->stream);
+  if (e == cudaSuccess && h->rs_alt)
+    e = cudaMemsetAsync(h->rs_alt, 0xFF, size_t(h->n) * sizeof(int32_t), h->stream);
   if (e == cudaSuccess) e = launch_state_init(h->st, h->n, 0, quant_shift(h->n), h->stream);
   if (e == cudaSuccess) {
     if (cfg->target == SMC_LOGISTIC)
@@ -487,6 +501,7 @@ int smc_redistribute(smc_sampler* h, const int32_t* ncopies_dev) {
   s.part = h->qpart;
   s.cbase = h->cbase;
   s.runstart = h->rs;
+  s.runstart_alt = h->rs_alt;
   s.tile_src = h->tile_src;
   s.nblocks = h->L.qblocks;
   s.ntiles = h->L.ntiles;

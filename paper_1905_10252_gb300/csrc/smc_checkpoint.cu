@@ -109,7 +109,10 @@ int smc_checkpoint_load(smc_sampler* h, const void* host_src, size_t bytes) {
   st.cur = 0;
   st.err = 0;
   st.pending = 0;
+  // the run-start arrays of this sampler are reset below (both clean, the
+  // first in use), whatever the saving sampler's were
   st.rs_dirty = 0;
+  st.rs_w = 0;
   st.trace = nullptr;
   st.mean_out = nullptr;
   st.fhat_out = nullptr;
@@ -120,6 +123,9 @@ int smc_checkpoint_load(smc_sampler* h, const void* host_src, size_t bytes) {
   // (a redistribution this sampler left pending is completed first, which
   // also clears its run starts)
   cudaError_t e = materialize(h);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->rs, 0xFF, size_t(h->n) * sizeof(int32_t), h->stream);
+  if (e == cudaSuccess && h->rs_alt)
+    e = cudaMemsetAsync(h->rs_alt, 0xFF, size_t(h->n) * sizeof(int32_t), h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->x[0], p, xb, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->lp[0], p + xb, lb, cudaMemcpyHostToDevice, h->stream);

@@ -11,7 +11,7 @@ namespace smc {
 
 // Byte offsets of the stateful sampler's workspace.
 struct Layout {
-  size_t st, tg, part, epart, qpart, cbase, xpart, rs, wbuf, tile_src, lg_x, lg_y, lg_img, covpart, total;
+  size_t st, tg, part, epart, qpart, cbase, xpart, rs, rs_alt, wbuf, tile_src, lg_x, lg_y, lg_img, covpart, total;
   int qblocks, ntiles, cov_blocks;
 };
 
@@ -39,6 +39,7 @@ struct smc_sampler {
   uint64_t* cbase;
   void* xpart;
   int32_t* rs;
+  int32_t* rs_alt;  // second run-start array (samplers created with SMC_FLAG_DEFER_REDISTRIBUTE), else NULL
   uint64_t* wbuf;
   int32_t* tile_src;
   int grid_p;

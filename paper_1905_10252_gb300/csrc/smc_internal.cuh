@@ -53,10 +53,19 @@ struct alignas(256) DevState {
   // pending = 1: iteration t resampled but its rows still sit in buffer cur, to
   // be gathered through the run starts rs / tile_src by the next move (or by
   // smc_materialize); log w is then reset_logw for every particle whatever
-  // the array holds.  rs_dirty = 1: a gathering move consumed the run starts,
-  // which the next quantise pass clears before the scan writes new ones.
+  // the array holds.
+  // Such samplers keep two run-start arrays.  rs_w names the one the next
+  // scan writes and the next copy reads; it holds -1 everywhere between
+  // resamplings.  A gathering move reads rs_w's array without resetting it
+  // (other warps of the same launch still search it), so the array it
+  // consumed is left dirty: the move resets the OTHER array when rs_dirty
+  // says that one is dirty, and the max pass that follows makes the other
+  // array current (rs_w ^= 1) and marks the consumed one dirty.  A copy
+  // kernel resets the entries it consumed, so rs_w's array stays clean.
   int32_t pending;
   int32_t rs_dirty;
+  int32_t rs_w;
+  int32_t rs_pad;
   double m;             // max_i log w
   double lse;           // LSE_t
   double lse_prev;      // LSE_{t-1} (0 after a reset)
@@ -83,6 +92,12 @@ struct alignas(256) DevState {
   unsigned long long survivors;  // particles with ncopies > 0 in the current resampling
   smc_iter_stats last;  // statistics of the last finalised iteration
 };
+
+// The run-start array in use: rs1 (the second array of a sampler that has
+// one) when st->rs_w says so, else rs0.
+__device__ __forceinline__ int32_t* rs_now(int32_t* rs0, int32_t* rs1, const DevState* st) {
+  return (rs1 && st->rs_w) ? rs1 : rs0;
+}
 
 __device__ __forceinline__ void record_error(DevState* st, int code) {
   atomicCAS(&st->err, 0, code);

@@ -83,8 +83,10 @@ struct ParticleArgs {
   double* epart;  // eq. (7) records {M_r, sum e x} per 256-particle tile (1 + d doubles each)
   const TargetDev* tg;
   DevState* st;
-  // a pending resampling's run starts and copy-tile sources (gathering move)
-  const int32_t* rs;
+  // a pending resampling's run starts and copy-tile sources (gathering move);
+  // rs_alt: the second run-start array (NULL when the sampler has one)
+  int32_t* rs;
+  int32_t* rs_alt;
   const int32_t* tile_src;
 };
 
@@ -98,6 +100,7 @@ struct QuantArgs {
   uint64_t* qpart;     // per-block {sumW, sw2 lo, sw2 hi, sumE lo, sumE hi}
   uint64_t* cbase;     // exclusive prefix of the block sums of W
   int32_t* runstart;   // runstart[off_i] = i for every survivor (when write_rs)
+  int32_t* runstart_alt;  // second run-start array (NULL: one array); st->rs_w picks
   int32_t write_rs;
   int32_t pad;
   uint64_t* wbuf;      // W_i written by the reduce pass, read by the scan (N words)
@@ -138,6 +141,7 @@ struct RedistArgs {
   int32_t row_bytes;
   int32_t lp_bytes;      // 0: no log pi payload
   int32_t* runstart;     // consumed and reset to -1 by the tile that reads it
+  int32_t* runstart_alt; // second run-start array (NULL: one array); st->rs_w picks
   const int32_t* tile_src;
   int32_t ntiles;
   int32_t force;         // copy even if the decision is "no resample"
@@ -158,6 +162,7 @@ struct NcScanArgs {
   uint64_t* part;       // per-block sums
   uint64_t* cbase;      // exclusive block prefixes
   int32_t* runstart;    // must hold -1 everywhere on entry
+  int32_t* runstart_alt;  // second run-start array (NULL: one array); st->rs_w picks
   int32_t* tile_src;
   int32_t nblocks;
   int32_t ntiles;
