@@ -4,10 +4,15 @@ Default workload (one JSON line): one SMC iteration per step -- move, reweight,
 LSE/N_eff, estimate, systematic resampling and redistribute (Algorithm 2,
 lines 3-10) -- at the resample+redistribute microbenchmark's largest size:
 N = 2^24 particles of D = 16 FP32 coordinates, Gaussian target, resampling at
-every iteration (the worst case of Sec. 5.2).  value = particle-iterations/s.
-The line also carries the redistribute stage's GB/s against the measured HBM
-peak, the roofline of the dominant kernel, an end-to-end figure through the
-C-ABI with host buffers, and the CPU oracle's rate on a bounded sample.
+every iteration (the worst case of Sec. 5.2).  value = particle-iterations/s
+of the K timed iterations run by one smc_step call (the graph-replayed entry
+point a user calls).  A separate pass of smc_step_profile (the same iteration
+launched directly, with events between its stages) gives the per-stage times
+and the roofline of the dominant kernel.  The line also carries the
+stateless resample+redistribute microbenchmark at N = 2^24, D = 16 (the
+whole smc_redistribute_raw call and its copy kernel, GB/s against the
+measured HBM peak), an end-to-end figure through the C-ABI with host
+buffers, and the CPU oracle's rate on a bounded sample.
 
 --workload redistribute prints one line per case of the resample+redistribute
 microbenchmark (N in {2^16, 2^20, 2^24}, s in {0.5, 2, 8}, one-hot).
@@ -76,6 +81,8 @@ def parse():
     p.add_argument("--d", type=int, default=16)
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-redistribute", action="store_true",
+                   help="default workload: leave out the redistribute microbenchmark")
     p.add_argument("--sizes", default="16,20,24", help="redistribute workload: log2 N values")
     p.add_argument("--cases", default="s0.5,s2,s8,onehot", help="redistribute workload: weight cases")
     p.add_argument("--seeds", default="0,1,2,3,4", help="redistribute workload: input seeds")
@@ -311,6 +318,61 @@ def algorithmic_bytes(n: int, d: int, esize: int, survivors: float, est_in_move:
     }
 
 
+def time_redistribute(native, torch, nc, x, out, wsb, flush, warmup: int, reps: int):
+    """(call ms, copy-kernel ms) of smc_redistribute_raw_profile per timed
+    repetition, L2 flushed before each: the whole stateless call (its ncopies
+    scan, then the copy) and the copy kernel alone."""
+    res = []
+    for it in range(warmup + reps):
+        flush.zero_()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        native.smc_redistribute_raw_profile(nc, x, out, wsb, evs)
+        torch.cuda.synchronize()
+        if it >= warmup:
+            res.append((evs[0].elapsed_time(evs[2]), evs[1].elapsed_time(evs[2])))
+    return res
+
+
+def redistribute_summary(n: int, d: int, cases, seed: int, reps: int, peak: float):
+    """The resample+redistribute microbenchmark at one size for the default
+    line: per weight case, medians of the stateless call and of its copy
+    kernel; bytes = run starts / ncopies 4 + distinct source rows 64 rho +
+    written rows 64, per row."""
+    import torch
+
+    from paper_1905_10252_gb300 import inputs, native
+
+    x = torch.as_tensor(inputs.particles(n, d, seed=1), device="cuda")
+    out = torch.empty_like(x)
+    wsb = torch.empty(native.smc_redistribute_ws_bytes(n), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    nc = torch.empty(n, dtype=torch.int32, device="cuda")
+    row = d * 4
+    per_case = {}
+    for case in cases:
+        lw = inputs.one_hot_log_weights(n, seed) if case == "onehot" else inputs.log_weights(n, float(case[1:]), seed)
+        native.smc_resample_raw(torch.as_tensor(lw, device="cuda"), seed, 1, native.RESAMPLE_ALWAYS, ncopies=nc,
+                                ws=wsb)
+        nnz = int((nc > 0).sum().item())
+        byt = 4 * n + row * nnz + row * n
+        t = time_redistribute(native, torch, nc, x, out, wsb, flush, 3, reps)
+        call_ms = statistics.median(c for c, _ in t)
+        copy_ms = statistics.median(k for _, k in t)
+        per_case[case] = {"survivors": nnz, "bytes": byt,
+                          "call_ms": round(call_ms, 5), "call_gbs": round(byt / (call_ms * 1e-3) / 1e9, 1),
+                          "call_frac": round(byt / (call_ms * 1e-3) / 1e9 / peak, 4),
+                          "copy_ms": round(copy_ms, 5), "copy_gbs": round(byt / (copy_ms * 1e-3) / 1e9, 1),
+                          "copy_frac": round(byt / (copy_ms * 1e-3) / 1e9 / peak, 4)}
+    del x, out, wsb, flush, nc
+    torch.cuda.empty_cache()
+    return {"workload": f"stateless resample+redistribute N=2^{int(np.log2(n))} D={d} fp32 rows, seed {seed}",
+            "entry_point": "smc_redistribute_raw (ncopies scan + copy); copy = its copy kernel alone",
+            "bytes": "4 + 64 rho + 64 per row (rho = survivors / N)", "unit": "GB/s", "peak": peak,
+            "timing": f"median of {reps} calls per case, L2 flushed before each", "cases": per_case,
+            "min_call_frac": min(c["call_frac"] for c in per_case.values()),
+            "min_copy_frac": min(c["copy_frac"] for c in per_case.values())}
+
+
 def run_iteration(args):
     import torch
     import torch.distributed as dist
@@ -334,10 +396,20 @@ def run_iteration(args):
                        flags=native.FLAG_DEFER_REDISTRIBUTE if gather else 0)
     stream = S.stream
     K, W = args.steps, args.warmup
+    L = native.lib()
+    mean_d = torch.empty(d, dtype=torch.float64, device="cuda")
+
+    def product_step(k):
+        # the entry point a user calls: k iterations replayed from the
+        # sampler's CUDA graph, f_k into mean_d
+        S._enter()
+        native._check(L.smc_step(S.h, int(k), native._ptr(mean_d), None, None, None), S.h)
+        S._done()
+
     for _ in range(W):
-        S.step_profile()
+        product_step(1)
     torch.cuda.synchronize()
-    n_prof = min(K, 400)
+    n_prof = max(5, min(K, 50))
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(n_prof)]
     for row in ev:
         for e in row:
@@ -351,16 +423,26 @@ def run_iteration(args):
     torch.cuda.synchronize()
     t_host0 = time.time()
     start.record(stream)
-    for k in range(K):
-        S.step_profile(ev[k] if k < n_prof else None)
+    product_step(K)
     stop.record(stream)
     torch.cuda.synchronize()
     t_host1 = time.time()
     if ws > 1:
         dist.barrier()
+    # per-stage split: the same iteration launched directly with events
+    # between its stages (smc_step_profile), run right after the timed region
+    # on the same sampler (every one of these iterations resamples too)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for k in range(n_prof):
+        S.step_profile(ev[k])
+    p1.record(stream)
+    torch.cuda.synchronize()
+    t_host2 = time.time()
     time.sleep(0.15)
     clocks.stop()
     total_ms = max_over_ranks(start.elapsed_time(stop), ws, device="cuda")
+    prof_ms_per_iter = p0.elapsed_time(p1) / n_prof
     per_stage = {name: [] for name in STAGES}
     for row in ev:
         for j, name in enumerate(STAGES):
@@ -466,9 +548,14 @@ def run_iteration(args):
                "serial": serial}
     S.sync()
     value = job_value(n, K, ws, total_ms)
-    # step set-up, begin, move + reweight, max, quantise reduce / finalise,
-    # scan, (redistribute,) commit
-    launches_per_step = 8 if gather else 9
+    # the stateless resample+redistribute microbenchmark at N = 2^24, D = 16
+    # (the metric's redistribute GB/s), rank 0 of a single-GPU run
+    redist = None
+    if rank == 0 and ws == 1 and not args.no_redistribute:
+        redist = redistribute_summary(1 << 24, 16, ["s0.5", "s2", "s8", "onehot"], 0, 20, peak)
+    # one step set-up per smc_step call, then per iteration: begin, move +
+    # reweight, max, quantise reduce / finalise, scan, (redistribute,) commit
+    launches_per_step = 7 if gather else 8
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K, "warmup": W,
@@ -479,14 +566,20 @@ def run_iteration(args):
                        "l2": "inputs larger than L2 (particle state %.2f GB per buffer)" % (n * d * 4 / 1e9),
                        "redistribute": ("gathered by the next iteration's move (SMC_FLAG_DEFER_REDISTRIBUTE)"
                                         if gather else "copy kernel at the end of the iteration")},
+            "entry_point": f"smc_step (one call, {K} iterations replayed from the sampler's CUDA graph)",
             "roofline": roof(dominant) if dominant in byt else roof("move_reweight"),
             "dominant_kernel": dominant,
-            "redistribute": roof("redistribute"),
+            "profile_pass": {"entry_point": "smc_step_profile (direct launches, events between stages)",
+                             "iterations": n_prof, "ms_per_iteration": round(prof_ms_per_iter, 5),
+                             "ratio_to_timed": round(prof_ms_per_iter / (total_ms / K), 4),
+                             "note": "stage times, stage_roofline and roofline come from this pass"},
+            "redistribute": redist,
             "stages_ms": {k: round(v, 5) for k, v in stage_ms.items()},
             "stage_roofline": {k: roof(k) for k in byt},
             "survivors_last_iteration": int(survivors),
-            "gpu_launches": launches_per_step * K,
+            "gpu_launches": 1 + launches_per_step * K,
             "clocks": clocks.summary(t_host0, t_host1),
+            "clocks_profile_pass": clocks.summary(t_host1, t_host2),
             "e2e": e2e,
         }
         if not args.no_cpu_baseline and ws == 1:
