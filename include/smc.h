@@ -296,7 +296,11 @@ int smc_ws_status(void* ws_dev, smc_stream_t stream);
  *    GPU (streams with no ordering between them) race and give undefined
  *    results;
  *  - the first call on each device looks up the array's device address with
- *    that device current; make that first call before any stream capture.
+ *    that device current; make that first call before any stream capture;
+ *  - that address is kept for the life of the process: do not call this
+ *    entry point on a device after cudaDeviceReset (or any other reset of its
+ *    primary context) in the same process -- the kept address would then
+ *    name memory that no longer exists.
  * status_dev (device int32, may be NULL) receives SMC_OK, or SMC_EINVAL when
  * ncopies has a negative entry or does not sum to n (then out_dev is not
  * written).  The call allocates nothing: no cudaMalloc, no cudaFree, no

@@ -20,6 +20,10 @@
 //  * The first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
 //    before any stream capture.
+//  * That address is kept for the rest of the process.  A device reset
+//    (cudaDeviceReset, or any other reset of the primary context) frees the
+//    array's old storage, so this entry point must not be used on a device
+//    after such a reset.
 #include <mutex>
 #include <string>
 

@@ -46,7 +46,10 @@ import numpy as np
 
 @dataclass
 class Job:
-    """One sampler run: kind 'gauss' (mu, sigma) or 'logistic' (X, y)."""
+    """One sampler run: kind 'gauss' (mu, sigma) or 'logistic' (X, y);
+    dtype 'f32' (every kind) or 'f64' (Gaussian jobs, one launch per job).
+    keep = True also keeps the per-iteration statistics (``trace``) and the
+    final particles, log pi and log w (``state``) for inspection."""
 
     jid: int
     kind: str
@@ -63,11 +66,15 @@ class Job:
     step: float = 0.5
     init_scale: float = 2.0
     deadline: float = math.inf     # cancelled if not finished this long after arrival
+    dtype: str = "f32"
+    keep: bool = False
     # filled in by the scheduler
     admitted: float = math.nan
     finished: float = math.nan
     done_iters: int = 0
     result: np.ndarray | None = None
+    trace: np.ndarray | None = None  # (keep) K statistics records
+    state: dict | None = None        # (keep) final x, logpi, logw
     waited_rounds: int = 0
     status: str = "new"            # queued, resident, done or cancelled
 
@@ -253,6 +260,7 @@ class GpuEngine(Engine):
         self.device = device
         self.samplers: dict[int, object] = {}
         self.means: dict[int, object] = {}
+        self.traces: dict[int, object] = {}
         self.batch = None
         self.batch_ids: tuple = ()
         # short jobs first: Gaussian work (the batch, or each Gaussian job in
@@ -267,7 +275,7 @@ class GpuEngine(Engine):
     def bytes_needed(self, job: Job) -> int:
         # particle state (two buffers), log w, two log pi buffers, workspace
         # (its logistic data included) and the batch's per-member arguments
-        es = 4
+        es = 8 if job.dtype == "f64" else 4
         ws = 2 * job.n * job.d * es + job.n * 8 + 2 * job.n * es
         ws += 32 * job.n + 12 * job.n + 64 * job.d * job.d + (1 << 16)
         ws += min(304, -(-job.n // 128)) * job.d * (job.d + 1) // 2 * 8  # covariance partials
@@ -279,7 +287,8 @@ class GpuEngine(Engine):
     def admit(self, job: Job) -> None:
         nat = self.native
         if job.kind == "gauss":
-            s = nat.Sampler(job.n, job.d, dtype=self.torch.float32, seed=job.seed, mu=job.mu, sigma=job.sigma,
+            dt = self.torch.float64 if job.dtype == "f64" else self.torch.float32
+            s = nat.Sampler(job.n, job.d, dtype=dt, seed=job.seed, mu=job.mu, sigma=job.sigma,
                             step=job.step, init_scale=job.init_scale,
                             stream=self.torch.cuda.Stream(device=self.device, priority=self.hi_prio))
         else:
@@ -287,6 +296,15 @@ class GpuEngine(Engine):
                             y=job.y, prior_var=job.prior_var, step=job.step, init_scale=job.init_scale)
         self.samplers[job.jid] = s
         self.means[job.jid] = self.torch.empty(job.d, dtype=self.torch.float64, device=self.device)
+        if job.keep:
+            self.traces[job.jid] = self.torch.zeros(max(job.k, 1), nat.STATS_WORDS, dtype=self.torch.float64,
+                                                    device=self.device)
+
+    def _trace_ptr(self, job: Job):
+        """Device address of the job's trace record for its next iteration
+        (smc_step writes one record per iteration from there)."""
+        tr = self.traces.get(job.jid)
+        return None if tr is None else tr[job.done_iters:].data_ptr()
 
     def _batch_for(self, jobs: list[Job]):
         ids = tuple(sorted(j.jid for j in jobs))
@@ -302,8 +320,10 @@ class GpuEngine(Engine):
         nat = self.native
         L = nat.lib()
         torch = self.torch
-        gauss = [j for j in jobs if j.kind == "gauss"]
-        others = [j for j in jobs if j.kind != "gauss"]
+        # FP32 Gaussian jobs can share the batched launch; FP64 and logistic
+        # jobs take one launch per job
+        gauss = [j for j in jobs if j.kind == "gauss" and j.dtype == "f32" and not j.keep]
+        others = [j for j in jobs if j not in gauss]
         launched = []
         if self.batched and gauss and not self.batch_busy and len(gauss) >= self.min_batch:
             # the batch advances every member by the same count: jobs needing
@@ -329,7 +349,8 @@ class GpuEngine(Engine):
         for j in others:
             s = self.samplers[j.jid]
             s.stream.wait_stream(torch.cuda.current_stream(self.device))
-            nat._check(L.smc_step(s.h, int(iters[j.jid]), nat._ptr(self.means[j.jid]), None, None, None), s.h)
+            nat._check(L.smc_step(s.h, int(iters[j.jid]), nat._ptr(self.means[j.jid]), None, self._trace_ptr(j),
+                                  None), s.h)
             ev = torch.cuda.Event()
             ev.record(s.stream)
             self.pending.append((ev, [j.jid], False))
@@ -357,6 +378,12 @@ class GpuEngine(Engine):
         return [jid for _, ids, _ in done for jid in ids]
 
     def result(self, job: Job) -> np.ndarray:
+        if job.keep:
+            s = self.samplers[job.jid]
+            x, lp = s.current()
+            job.state = {"x": x.cpu().numpy().copy(), "logpi": lp.cpu().numpy().copy(),
+                         "logw": s.logw.cpu().numpy().copy()}
+            job.trace = self.traces[job.jid].cpu().numpy().copy()
         return self.means[job.jid].cpu().numpy().copy()
 
     def release(self, job: Job) -> None:
@@ -366,3 +393,4 @@ class GpuEngine(Engine):
             self.batch, self.batch_ids = None, ()
         self.samplers.pop(job.jid).close()
         self.means.pop(job.jid)
+        self.traces.pop(job.jid, None)

@@ -130,3 +130,74 @@ def test_tc_full_size_sampled(nat, orc):
         assert np.all(lw == lw[0]) and abs(lw[0] + np.log(N)) < 1e-12 * np.log(N)
     assert np.all(np.isfinite(lw))
     print(f"full size: max |d log pi| over 512 particles = {err.max():.3e} (|log pi| up to {np.abs(ref).max():.0f})")
+
+
+@pytest.mark.parametrize("warm,step", [(0, 0.5), (30, 0.05)])
+def test_tc_weights_and_resampling_against_fp64(nat, orc, warm, step):
+    """Reduced precision as resampling sees it (eq. (5), then Algorithm 4):
+    N = 2^16 particles, M = 8192 rows, D = 32, q_0 = N(0, 4I).  warm = 0:
+    the benchmark's step 0.5 from the initial draw; warm = 30: after 30
+    resampling iterations with step 0.05 (a settled cloud whose weights are
+    far less degenerate).  After one move and reweight, every particle's
+    log w from the tensor-core likelihood is compared with the FP64 log w of
+    the same particles (the oracle's log pi; log q_0 = -|x|^2 / 8 with
+    constants dropped, Algorithm 2 line 1), bounded per particle by the
+    arithmetic: the hi / lo split drops lo x lo (2^-18 of each product) and
+    rounds each operand's lo part (2^-18), and FP32 accumulation adds ~2^-24
+    per term, so |dz_m| <= 2^-16 sum_k |x_mk b_k| with margin; the epilogue's ex2 / lg2 add ~1e-7 per row; and
+    eq. (5) takes the difference of the two FP32 log pi values (half an FP32
+    ulp of the larger).  Then both weight vectors are resampled with the
+    same Philox draw, and the share of particles whose copy counts differ is
+    reported (printed with -s)."""
+    N, D, M = 1 << 16, 32, 8192
+    X, y, _ = inputs.logistic_data(M, D, seed=0)
+    Xd = X.astype(np.float64)
+    tgt = orc.Target.logistic(Xd, y.astype(np.float64), 4.0)
+    seed = 7
+    S = nat.Sampler(N, D, dtype=torch.float32, seed=seed, target="logistic", X=X, y=y, prior_var=4.0, step=step,
+                    init_scale=2.0, resample_mode=nat.RESAMPLE_ALWAYS if warm else nat.RESAMPLE_NEVER)
+    if warm:
+        S.step(warm)
+    x0, lp0 = [host(t).copy() for t in S.current()]
+    lw0 = host(S.logw).copy()
+    S.move()
+    S.reweight()
+    x1, lp1 = [host(t).copy() for t in S.current()]
+    lw1 = host(S.logw).copy()
+    S.sync()
+    x0d, x1d = x0.astype(np.float64), x1.astype(np.float64)
+    lp0_ref, lp1_ref = tgt.logpi(x0d), tgt.logpi(x1d)
+    if warm:
+        # the last warm-up iteration resampled: every log w is -log N
+        assert np.all(lw0 == orc.reset_logw(N))
+        lw0_ref = lw0
+    else:
+        q0 = -0.125 * np.sum(x0d * x0d, axis=1)
+        # the sampler's initial weights are log pi - log q_0 with this q_0
+        # (its log q_0 is formed in FP32)
+        assert np.all(np.abs((lw0 - lp0.astype(np.float64)) + q0) <= 1e-6 * (1 + np.abs(q0)))
+        lw0_ref = lp0_ref - q0
+    lw1_ref = lw0_ref + (lp1_ref - lp0_ref)
+    err = np.abs(lw1 - lw1_ref)
+    # per-particle bound from the arithmetic
+    abs_z = np.zeros(N)
+    absX = np.abs(Xd)
+    for a in range(0, N, 4096):
+        abs_z[a:a + 4096] = (absX @ np.abs(x0d[a:a + 4096]).T).sum(axis=0) + (absX @ np.abs(x1d[a:a + 4096]).T).sum(axis=0)
+    half_ulp = 0.5 * np.spacing(np.maximum(np.abs(lp0), np.abs(lp1)).astype(np.float32)).astype(np.float64)
+    bound = 2.0 ** -16 * abs_z + 2e-6 * M + half_ulp
+    assert np.all(err <= bound), (err.max(), float(np.argmax(err - bound)))
+    # resampling both weight vectors with the same draw (seed, t = 1)
+    nc_gpu, _ = nat.smc_resample_raw(torch.as_tensor(lw1, device="cuda"), seed, 1, nat.RESAMPLE_ALWAYS)
+    nc_gpu = host(nc_gpu)
+    nc_ref = orc.resample(lw1_ref, seed, 1, orc.RESAMPLE_ALWAYS)["ncopies"]
+    assert nc_gpu.sum() == N and nc_ref.sum() == N
+    differ = float(np.mean(nc_gpu != nc_ref))
+    tv = 0.5 * float(np.abs(nc_gpu.astype(np.int64) - nc_ref).sum()) / N
+    _, _, ess = orc.lse_ess(lw1_ref)
+    q = np.quantile(err, [0.5, 0.9, 0.99, 1.0])
+    print(f"\nwarm={warm} step={step}: |d log w| quantiles 50/90/99/100% = {q[0]:.3e} {q[1]:.3e} {q[2]:.3e} "
+          f"{q[3]:.3e}; max err/bound {float((err / bound).max()):.3f}; |log pi| up to {np.abs(lp1_ref).max():.0f}; "
+          f"N_eff (FP64) = {ess:.2f}; copy counts differ for {differ:.6f} of the particles "
+          f"(total-variation distance of ncopies / N = {tv:.6f}); survivors GPU {np.count_nonzero(nc_gpu)}, "
+          f"FP64 {np.count_nonzero(nc_ref)}")

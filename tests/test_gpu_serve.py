@@ -107,3 +107,43 @@ def test_cancelled_jobs_leave_the_others_unchanged(nat):
     assert sch.used_bytes == 0 and not eng.samplers and eng.batch is None
     for j in done:
         assert np.array_equal(j.result, alone(nat, j)), (j.jid, j.kind)
+
+
+def test_served_fp64_job_equals_oracle(nat, orc):
+    """One plain FP64 Gaussian job (N = 1024, D = 4, K = 20: the plain
+    sampler's configuration) served in the mixed stream, under the memory
+    budget, next to batched and logistic jobs: its trajectory is the
+    oracle's Algorithm 2 run -- particles, log pi and log w bit for bit, the
+    resampling decisions, maxima and survivors of every iteration exactly,
+    LSE and log c_t within 1e-10, and f_K within 1e-11."""
+    from paper_1905_10252_gb300.serve import GpuEngine, Job, Scheduler
+
+    jobs = make_jobs()
+    N, D, K, seed = 1024, 4, 20, 3
+    mu, Sigma = inputs.gaussian_target(D, seed=0)
+    jobs.append(Job(jid=99, kind="gauss", n=N, d=D, k=K, seed=seed, arrival=float(jobs[5].arrival),
+                    mu=mu, sigma=Sigma, step=0.5, init_scale=2.0, dtype="f64", keep=True))
+    eng = GpuEngine(batched=True, min_batch=1)
+    need = sum(eng.bytes_needed(j) for j in jobs)
+    sch = Scheduler(eng, budget_bytes=need // 3, round_iters=3)
+    done = {j.jid: j for j in sch.run(jobs)}
+    assert len(done) == len(jobs)
+    job = done[99]
+    ref = orc.run(orc.Target.gauss(mu, Sigma), N, seed, K, init_scale=2.0, step=0.5)
+    assert np.array_equal(job.state["x"], ref["x"])
+    assert np.array_equal(job.state["logpi"], ref["logpi"])
+    assert np.array_equal(job.state["logw"], ref["logw"])
+    tr = nat.trace_dicts(torch.as_tensor(job.trace))
+    assert len(tr) == K
+    for k, rec in enumerate(tr):
+        assert rec["t"] == k + 1
+        assert rec["resampled"] == int(ref["trace"][k, 4]), k
+        assert abs(rec["lse"] - ref["trace"][k, 0]) <= 1e-10, k
+        assert abs(rec["logc"] - ref["trace"][k, 1]) <= 1e-10, k
+        assert rec["max_logw"] == ref["trace"][k, 3], k
+        assert rec["survivors"] == int(ref["trace"][k, 5]), k
+    np.testing.assert_allclose(job.result, ref["means"][-1], rtol=0, atol=1e-11)
+    # the other jobs still give their solo answers
+    for j in done.values():
+        if j.jid != 99:
+            assert np.array_equal(j.result, alone(nat, j)), (j.jid, j.kind)
