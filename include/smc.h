@@ -375,6 +375,57 @@ int smc_batch_sync(smc_batch* b, int32_t* which_host);
 int smc_batch_destroy(smc_batch* b);
 const char* smc_batch_last_error(const smc_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Standing batches of slots (serving).  The batch above is laid out for one
+ * member list; a server whose jobs come and go would rebuild it (block maps,
+ * CUDA graph) at every change.  A standing batch is laid out once for `count`
+ * slots of fixed capacity: slot s holds one FP32 Gaussian sampler of at most
+ * cap_n[s] particles (any D), attached and detached between steps by editing
+ * a slot table in device memory, with no rebuild and no host
+ * synchronisation.  Each step runs, for every slot, the number of
+ * iterations (Algorithm 2, lines 3-10) the caller asks for that slot, all
+ * slots in one launch per stage (one CUDA graph replay per iteration);
+ * slots with fewer iterations, and empty slots, do nothing in the later
+ * launches.  A sampler's results in a slot are bit-identical to those of
+ * smc_step on it alone (its own blocks, tiles and reduction order).
+ *
+ * smc_slots_ws_bytes: device workspace for these capacities (1 <= count <=
+ *   512, 1 <= cap_n[s] < 2^31).
+ * smc_slots_create: ws_dev 256-byte aligned, owned by the caller, alive until
+ *   smc_slots_destroy; stream must not be NULL (the legacy default stream
+ *   cannot hold the graph).  Synchronises the stream once (layout upload).
+ * smc_slots_attach: puts h (an smc_init handle, SMC_F32, SMC_GAUSS, N <=
+ *   cap_n[slot], attached nowhere else) into the empty slot; mean_dev (D
+ *   doubles), trace_dev (one smc_iter_stats per iteration run in the slot)
+ *   and fhat_dev (D doubles) are device outputs with smc_step's meaning, each
+ *   may be NULL.  The slots' stream is ordered after the work already queued
+ *   on h's stream (device-side; a pending deferred copy is completed first).
+ *   h must not be stepped by itself while attached.
+ * smc_slots_detach: empties the slot; h's stream is ordered after the slots'
+ *   work queued so far, so h's own calls may follow at once.
+ * smc_slots_step: iters_host[count] (host array) gives each slot's
+ *   iterations for this call (0 for idle and empty slots; a positive count
+ *   for an empty slot is SMC_EINVAL); the call enqueues max(iters) batched
+ *   iterations on the slots' stream and returns.
+ * smc_slots_sync: synchronises the stream; returns (then clears) the first
+ *   device error of an attached sampler, its slot in which_host (-1 when
+ *   none; may be NULL).
+ * Errors: SMC_EINVAL (arguments, as above), SMC_ENOMEM (workspace too
+ * small), SMC_ECUDA; messages from smc_slots_last_error (NULL: the last
+ * handle-less call). */
+typedef struct smc_slots smc_slots;
+
+int smc_slots_ws_bytes(const int64_t* cap_n, int32_t count, size_t* bytes);
+int smc_slots_create(smc_slots** out, const int64_t* cap_n, int32_t count, void* ws_dev, size_t ws_bytes,
+                     smc_stream_t stream);
+int smc_slots_attach(smc_slots* b, int32_t slot, smc_sampler* h, double* mean_dev, smc_iter_stats* trace_dev,
+                     double* fhat_dev);
+int smc_slots_detach(smc_slots* b, int32_t slot);
+int smc_slots_step(smc_slots* b, const int32_t* iters_host);
+int smc_slots_sync(smc_slots* b, int32_t* which_host);
+int smc_slots_destroy(smc_slots* b);
+const char* smc_slots_last_error(const smc_slots* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -293,14 +293,61 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_logistic_tc(ParticleArgs a) {
       if (free_buf) {
         uint8_t* ahi = aimg + size_t(2 * ab) * kTcAImg;
         uint8_t* alo = ahi + kTcAImg;
-        for (int e = t; e < kTcPT * kLgK; e += kTcStageThreads) {
-          const int r = e / kLgK, k = e % kLgK;
-          const int64_t i = pt * kTcPT + r;
-          const float val = (i < n && k < d) ? x[i * d + k] : 0.0f;
-          const uint16_t hi = bf16_rn(val);
-          const uint16_t lo = bf16_rn(val - __uint_as_float(uint32_t(hi) << 16));
-          *reinterpret_cast<uint16_t*>(ahi + img_off(r, k)) = hi;
-          *reinterpret_cast<uint16_t*>(alo + img_off(r, k)) = lo;
+        // every load of the thread is issued before the conversions, so the
+        // tile's memory latency is paid about once (with few data tiles per
+        // particle tile -- small M -- this staging sets the kernel's pace)
+        if ((d & 3) == 0) {
+          // 16-byte loads: thread t takes the groups e = t + 64 u of four
+          // consecutive features (r = e / 8, k = 4 (e % 8)); a row of d
+          // features is d / 4 such groups, the rest of the 32 are zero
+          constexpr int kG = kTcPT * kLgK / 4 / kTcStageThreads;  // 16
+          float4 vals[kG];
+#pragma unroll
+          for (int u = 0; u < kG; ++u) {
+            const int e = t + kTcStageThreads * u;
+            const int r = e >> 3, k = (e & 7) << 2;
+            const int64_t i = pt * kTcPT + r;
+            vals[u] = (i < n && k < d) ? *reinterpret_cast<const float4*>(x + i * d + k)
+                                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          }
+#pragma unroll
+          for (int u = 0; u < kG; ++u) {
+            const int e = t + kTcStageThreads * u;
+            const int r = e >> 3, k = (e & 7) << 2;
+            const float f[4] = {vals[u].x, vals[u].y, vals[u].z, vals[u].w};
+            uint16_t hi[4], lo[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              hi[c] = bf16_rn(f[c]);
+              lo[c] = bf16_rn(f[c] - __uint_as_float(uint32_t(hi[c]) << 16));
+            }
+            // features k .. k + 3 are adjacent in the core-matrix image
+            *reinterpret_cast<uint2*>(ahi + img_off(r, k)) =
+                make_uint2(uint32_t(hi[0]) | (uint32_t(hi[1]) << 16), uint32_t(hi[2]) | (uint32_t(hi[3]) << 16));
+            *reinterpret_cast<uint2*>(alo + img_off(r, k)) =
+                make_uint2(uint32_t(lo[0]) | (uint32_t(lo[1]) << 16), uint32_t(lo[2]) | (uint32_t(lo[3]) << 16));
+          }
+        } else {
+          constexpr int kB = 8;  // loads in flight per thread
+          for (int e0 = t; e0 < kTcPT * kLgK; e0 += kTcStageThreads * kB) {
+            float vals[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+              const int e = e0 + kTcStageThreads * u;
+              const int r = e / kLgK, k = e % kLgK;
+              const int64_t i = pt * kTcPT + r;
+              vals[u] = (i < n && k < d) ? x[i * d + k] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+              const int e = e0 + kTcStageThreads * u;
+              const int r = e / kLgK, k = e % kLgK;
+              const uint16_t hi = bf16_rn(vals[u]);
+              const uint16_t lo = bf16_rn(vals[u] - __uint_as_float(uint32_t(hi) << 16));
+              *reinterpret_cast<uint16_t*>(ahi + img_off(r, k)) = hi;
+              *reinterpret_cast<uint16_t*>(alo + img_off(r, k)) = lo;
+            }
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }

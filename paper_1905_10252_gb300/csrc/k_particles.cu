@@ -899,10 +899,15 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleAr
 
 // Batched: block b runs block map[b].y of map[b].z of sampler map[b].x; the
 // sampler's factor is staged in shared memory (padded rows, 16-byte loads).
+// left (standing batches of slots; NULL otherwise): a member whose count is
+// not positive does nothing in this iteration, and its arguments are not
+// read (an empty slot's are not valid).
 __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_batch(const ParticleArgs* __restrict__ pa,
                                                                      const GaussParamsF32* __restrict__ gps,
-                                                                     const int4* __restrict__ map) {
+                                                                     const int4* __restrict__ map,
+                                                                     const int32_t* __restrict__ left) {
   const int4 m = map[blockIdx.x];
+  if (left && left[m.x] <= 0) return;
   const ParticleArgs a = pa[m.x];
   __shared__ float4 sfac[kPairedFactor / 2];
   __shared__ float smu[kTgtMaxD];
@@ -961,7 +966,9 @@ __global__ void __launch_bounds__(kFinThreads) k_max_finalize(const double* __re
 
 // Batched: block s finalises sampler s over its nb[s] move blocks.
 __global__ void __launch_bounds__(kFinBatchThreads) k_max_finalize_batch(const ParticleArgs* __restrict__ pa,
-                                                                   const int* __restrict__ nb) {
+                                                                   const int* __restrict__ nb,
+                                                                   const int32_t* __restrict__ left) {
+  if (left && left[blockIdx.x] <= 0) return;
   const ParticleArgs a = pa[blockIdx.x];
   max_finalize_body(a.part, nb[blockIdx.x], a.st);
 }
@@ -1059,15 +1066,19 @@ __global__ void k_settle(DevState* st) {
 }
 
 // Batched bookkeeping: thread s handles sampler s.
-__global__ void k_begin_batch(const ParticleArgs* __restrict__ pa, int count) {
+__global__ void k_begin_batch(const ParticleArgs* __restrict__ pa, int count, const int32_t* __restrict__ left) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < count) pa[s].st->t += 1;
+  if (s < count && (!left || left[s] > 0)) pa[s].st->t += 1;
 }
 
 // Batched: one warp (block) per sampler.
-__global__ void k_commit_batch(const ParticleArgs* __restrict__ pa, int count) {
+// (left: the member's count of iterations still to run is decremented here,
+// after every other kernel of the iteration has read it)
+__global__ void k_commit_batch(const ParticleArgs* __restrict__ pa, int count, int32_t* __restrict__ left) {
   const int s = blockIdx.x;
-  if (s < count) commit_warp(pa[s].st, pa[s].d, 0, 1);
+  if (s >= count || (left && left[s] <= 0)) return;
+  commit_warp(pa[s].st, pa[s].d, 0, 1);
+  if (left && threadIdx.x == 0) left[s] -= 1;
 }
 
 // Points every sampler's step outputs; outs holds three arrays of count
@@ -1201,16 +1212,17 @@ cudaError_t launch_cov(const ParticleArgs& a, double* cov, double* covpart, int 
 }
 
 cudaError_t launch_move_reweight_batch(const ParticleArgs* pa, const GaussParamsF32* gps, const int4* map, int nblocks,
-                                       cudaStream_t s) {
-  k_move_reweight_batch<<<nblocks, kPThreads, 0, s>>>(pa, gps, map);
+                                       cudaStream_t s, const int32_t* left) {
+  k_move_reweight_batch<<<nblocks, kPThreads, 0, s>>>(pa, gps, map, left);
   return cudaGetLastError();
 }
-cudaError_t launch_max_finalize_batch(const ParticleArgs* pa, const int* nb, int count, cudaStream_t s) {
-  k_max_finalize_batch<<<count, kFinBatchThreads, 0, s>>>(pa, nb);
+cudaError_t launch_max_finalize_batch(const ParticleArgs* pa, const int* nb, int count, cudaStream_t s,
+                                      const int32_t* left) {
+  k_max_finalize_batch<<<count, kFinBatchThreads, 0, s>>>(pa, nb, left);
   return cudaGetLastError();
 }
-cudaError_t launch_begin_batch(const ParticleArgs* pa, int count, cudaStream_t s) {
-  k_begin_batch<<<(count + 127) / 128, 128, 0, s>>>(pa, count);
+cudaError_t launch_begin_batch(const ParticleArgs* pa, int count, cudaStream_t s, const int32_t* left) {
+  k_begin_batch<<<(count + 127) / 128, 128, 0, s>>>(pa, count, left);
   return cudaGetLastError();
 }
 cudaError_t launch_step_setup_batch(const ParticleArgs* pa, void* const* outs, int count, cudaStream_t s) {
@@ -1221,8 +1233,8 @@ cudaError_t launch_take_errors_batch(const ParticleArgs* pa, int32_t* errs, int 
   k_take_errors_batch<<<(count + 127) / 128, 128, 0, s>>>(pa, errs, count);
   return cudaGetLastError();
 }
-cudaError_t launch_commit_batch(const ParticleArgs* pa, int count, cudaStream_t s) {
-  k_commit_batch<<<count, 32, 0, s>>>(pa, count);
+cudaError_t launch_commit_batch(const ParticleArgs* pa, int count, cudaStream_t s, int32_t* left) {
+  k_commit_batch<<<count, 32, 0, s>>>(pa, count, left);
   return cudaGetLastError();
 }
 

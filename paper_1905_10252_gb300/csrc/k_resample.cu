@@ -846,11 +846,16 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute_commit(RedistArgs a,
 // sampler's blocks, reductions and results are those of its own launch.
 __device__ __forceinline__ int dclass(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : (d <= 16 ? 2 : 3)); }
 
+// left (standing batches of slots; NULL otherwise): see k_move_reweight_batch.
+// A slot's map covers its capacity; blocks past the member's own count exit.
 __global__ void __launch_bounds__(kQThreads) k_quant_reduce_batch(const QuantArgs* __restrict__ qa,
-                                                                 const int4* __restrict__ map) {
+                                                                 const int4* __restrict__ map,
+                                                                 const int32_t* __restrict__ left) {
   __shared__ QuantReduceSmem sm;
   const int4 m = map[blockIdx.x];
+  if (left && left[m.x] <= 0) return;
   const QuantArgs a = qa[m.x];
+  if (m.y >= a.nblocks) return;
   switch (dclass(a.d)) {
     case 0: quant_reduce_body<float, 4, true>(a, m.y, sm); break;
     case 1: quant_reduce_body<float, 8, true>(a, m.y, sm); break;
@@ -859,24 +864,32 @@ __global__ void __launch_bounds__(kQThreads) k_quant_reduce_batch(const QuantArg
   }
 }
 
-__global__ void __launch_bounds__(kFinBatchThreads) k_quant_finalize_batch(const QuantArgs* __restrict__ qa) {
+__global__ void __launch_bounds__(kFinBatchThreads) k_quant_finalize_batch(const QuantArgs* __restrict__ qa,
+                                                                     const int32_t* __restrict__ left) {
+  if (left && left[blockIdx.x] <= 0) return;
   const QuantArgs a = qa[blockIdx.x];
   quant_finalize_body(a, 0);
 }
 
 __global__ void __launch_bounds__(kQThreads) k_quant_scan_batch(const QuantArgs* __restrict__ qa,
-                                                               const int4* __restrict__ map) {
+                                                               const int4* __restrict__ map,
+                                                               const int32_t* __restrict__ left) {
   const int4 m = map[blockIdx.x];
+  if (left && left[m.x] <= 0) return;
   const QuantArgs a = qa[m.x];
+  if (m.y >= a.nblocks) return;
   quant_scan_body(a, m.y);
 }
 
 template <int KU>
 __global__ void __launch_bounds__(kRThreads) k_redistribute_batch(const RedistArgs* __restrict__ ra,
-                                                                 const int4* __restrict__ map) {
+                                                                 const int4* __restrict__ map,
+                                                                 const int32_t* __restrict__ left) {
   __shared__ RedistSmem sm;
   const int4 m = map[blockIdx.x];
+  if (left && left[m.x] <= 0) return;
   const RedistArgs a = ra[m.x];
+  if (m.y >= a.ntiles) return;
   switch (a.row_bytes) {
     case 8: redistribute_body<uint2, 1, KU>(a, m.y, sm); break;
     case 16: redistribute_body<uint4, 1, KU>(a, m.y, sm); break;
@@ -908,24 +921,26 @@ __global__ void __launch_bounds__(kRThreads) k_identity_runs_batch(const RedistA
   if (threadIdx.x == 0) const_cast<int32_t*>(a.tile_src)[m.y] = int32_t(k0);
 }
 
-cudaError_t launch_quant_reduce_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s) {
-  k_quant_reduce_batch<<<nblocks, kQThreads, 0, s>>>(qa, map);
+cudaError_t launch_quant_reduce_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s,
+                                      const int32_t* left) {
+  k_quant_reduce_batch<<<nblocks, kQThreads, 0, s>>>(qa, map, left);
   return cudaGetLastError();
 }
-cudaError_t launch_quant_finalize_batch(const QuantArgs* qa, int count, cudaStream_t s) {
-  k_quant_finalize_batch<<<count, kFinBatchThreads, 0, s>>>(qa);
+cudaError_t launch_quant_finalize_batch(const QuantArgs* qa, int count, cudaStream_t s, const int32_t* left) {
+  k_quant_finalize_batch<<<count, kFinBatchThreads, 0, s>>>(qa, left);
   return cudaGetLastError();
 }
-cudaError_t launch_quant_scan_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s) {
-  k_quant_scan_batch<<<nblocks, kQThreads, 0, s>>>(qa, map);
+cudaError_t launch_quant_scan_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s,
+                                    const int32_t* left) {
+  k_quant_scan_batch<<<nblocks, kQThreads, 0, s>>>(qa, map, left);
   return cudaGetLastError();
 }
 cudaError_t launch_redistribute_batch(const RedistArgs* ra, const int4* map, int nblocks, int copy_variant,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, const int32_t* left) {
   switch (copy_variant) {
-    case 0: k_redistribute_batch<4><<<nblocks, kRThreads, 0, s>>>(ra, map); break;
-    case 1: k_redistribute_batch<8><<<nblocks, kRThreads, 0, s>>>(ra, map); break;
-    case 2: k_redistribute_batch<16><<<nblocks, kRThreads, 0, s>>>(ra, map); break;
+    case 0: k_redistribute_batch<4><<<nblocks, kRThreads, 0, s>>>(ra, map, left); break;
+    case 1: k_redistribute_batch<8><<<nblocks, kRThreads, 0, s>>>(ra, map, left); break;
+    case 2: k_redistribute_batch<16><<<nblocks, kRThreads, 0, s>>>(ra, map, left); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -123,7 +123,9 @@ int cuda_fail(smc_sampler* h, cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return cuda_fail((h), _e, #expr); \
   } while (0)
 
-const GaussParamsF32* gauss_params(const smc_sampler* h) { return h->have_gp ? &h->gp : nullptr; }
+// (fetch_gp must have run: an FP32 Gaussian sampler launched without its
+// factor would take the generic kernel)
+const GaussParamsF32* gauss_params(const smc_sampler* h) { return h->gp_ready ? &h->gp : nullptr; }
 
 }  // namespace
 
@@ -193,6 +195,26 @@ cudaError_t materialize(smc_sampler* h) {
   cudaError_t e = launch_redistribute(r, h->stream);
   if (e == cudaSuccess) e = launch_settle(h->st, h->stream);
   return e;
+}
+
+// The FP32 factor of an FP32 Gaussian sampler as host-side kernel
+// parameters (mu and the interleaved row pairs of L^-1), copied from the
+// device the first time a direct launch needs it: synchronises h's stream
+// that once.  Never called during stream capture.
+cudaError_t fetch_gp(smc_sampler* h) {
+  if (!h->have_gp || h->gp_ready) return cudaSuccess;
+  static thread_local float Pf[kTgtMaxD * kTgtMaxD], muf[kTgtMaxD];
+  cudaError_t e = cudaMemcpyAsync(Pf, h->tg->Pf, sizeof Pf, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(muf, h->tg->muf, sizeof muf, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  for (int c = 0; c < kTgtMaxD; ++c) h->gp.mu[c] = muf[c];
+  for (int p = 0; p < kTgtMaxD / 2; ++p)
+    for (int c = 0; c < kTgtMaxD; ++c)
+      h->gp.P2[p * kTgtMaxD + c] = make_float2(c <= 2 * p ? Pf[2 * p * kTgtMaxD + c] : 0.0f,
+                                               c <= 2 * p + 1 ? Pf[(2 * p + 1) * kTgtMaxD + c] : 0.0f);
+  h->gp_ready = true;
+  return cudaSuccess;
 }
 
 RedistArgs redist_args(const smc_sampler* h, int force) {
@@ -394,6 +416,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   h->grid_lg = logistic_tc_grid(h->n, sm_count());
   h->g_iter[0] = h->g_iter[1] = nullptr;
   h->have_gp = false;
+  h->gp_ready = false;
   h->err = "ok";
 
   // Algorithm 2, line 1, then the statistics of w_0 (LSE_0 becomes LSE_{t-1})
@@ -418,21 +441,12 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   if (e == cudaSuccess) e = launch_particles(OP_INIT, ia, h->grid_p, h->threads_p, h->stream);
   if (e == cudaSuccess && h->lg_tc) e = launch_logistic_tc(particle_args(h), h->grid_lg, h->stream);
   if (e == cudaSuccess) e = launch_stats(h, 1, h->lg_tc ? h->grid_lg : h->grid_p);
-  if (e == cudaSuccess && cfg->target == SMC_GAUSS && h->dtype == SMC_F32) {
-    // the FP32 factor becomes a kernel parameter of the move / reweight kernel
-    static thread_local float Pf[kTgtMaxD * kTgtMaxD], muf[kTgtMaxD];
-    e = cudaMemcpyAsync(Pf, h->tg->Pf, sizeof Pf, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(muf, h->tg->muf, sizeof muf, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e == cudaSuccess) {
-      for (int c = 0; c < kTgtMaxD; ++c) h->gp.mu[c] = muf[c];
-      for (int p = 0; p < kTgtMaxD / 2; ++p)
-        for (int c = 0; c < kTgtMaxD; ++c)
-          h->gp.P2[p * kTgtMaxD + c] = make_float2(c <= 2 * p ? Pf[2 * p * kTgtMaxD + c] : 0.0f,
-                                                   c <= 2 * p + 1 ? Pf[(2 * p + 1) * kTgtMaxD + c] : 0.0f);
-      h->have_gp = true;
-    }
-  }
+  // FP32 Gaussian samplers: the FP32 factor the set-up kernel wrote becomes
+  // a kernel parameter of the move / reweight kernel; it is fetched by the
+  // first direct launch that needs it (fetch_gp), so smc_init returns
+  // without waiting for its own work
+  h->have_gp = cfg->target == SMC_GAUSS && h->dtype == SMC_F32;
+  h->gp_ready = false;
   // deferred redistribution: the gathering move is the records kernel's, and
   // the quantise and copy passes span several blocks
   h->defer = (cfg->flags & SMC_FLAG_DEFER_REDISTRIBUTE) && est_in_move(h) && h->L.qblocks > 1 && h->L.ntiles > 1;
@@ -448,6 +462,7 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
 int smc_move(smc_sampler* h) {
   SMC_RANGE("smc_move");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, fetch_gp(h));
   SMC_TRY(h, materialize(h));
   SMC_TRY(h, launch_begin(h->st, h->stream));
   SMC_TRY(h, launch_particles(OP_MOVE, particle_args(h), h->grid_p, h->threads_p, h->stream, gauss_params(h)));
@@ -457,6 +472,7 @@ int smc_move(smc_sampler* h) {
 int smc_reweight(smc_sampler* h) {
   SMC_RANGE("smc_reweight");
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
+  SMC_TRY(h, fetch_gp(h));
   SMC_TRY(h, materialize(h));
   if (h->lg_tc) {
     SMC_TRY(h, launch_logistic_tc(particle_args(h), h->grid_lg, h->stream));
@@ -520,6 +536,7 @@ int smc_step(smc_sampler* h, int32_t k, double* mean_dev, double* cov_dev, smc_i
   if (!h) return fail(nullptr, SMC_EINVAL, "null handle");
   if (k < 0) return fail(h, SMC_EINVAL, "k must be >= 0");
   if (k == 0) return SMC_OK;
+  SMC_TRY(h, fetch_gp(h));  // (before any stream capture)
   SMC_TRY(h, launch_step_setup(h->st, trace_dev, mean_dev, fhat_dev, cov_dev, h->stream));
   const bool use_graph = h->stream != nullptr;
   for (int32_t it = 0; it < k; ++it) {
@@ -544,6 +561,7 @@ int smc_step_profile(smc_sampler* h, double* mean_dev, void* const* events_host,
   auto rec = [&](int j) -> cudaError_t {
     return n_events ? cudaEventRecord(static_cast<cudaEvent_t>(events_host[j]), s) : cudaSuccess;
   };
+  SMC_TRY(h, fetch_gp(h));
   SMC_TRY(h, launch_step_setup(h->st, nullptr, mean_dev, nullptr, nullptr, s));
   const ParticleArgs a = particle_args(h);
   QuantArgs q = quant_args(h, 0, nullptr);

@@ -251,6 +251,7 @@ int smc_batch_create(smc_batch** out, smc_sampler* const* members, int32_t count
   {
     cudaEvent_t ev = nullptr;
     cudaError_t e = cudaSuccess;
+    for (int s = 0; s < count && e == cudaSuccess; ++s) e = fetch_gp(members[s]);
     for (int s = 0; s < count && e == cudaSuccess; ++s) e = materialize(members[s]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     const cudaStream_t bs = reinterpret_cast<cudaStream_t>(stream);

@@ -47,9 +47,11 @@ struct smc_sampler {
   // FP32 logistic samplers: likelihood on the tensor cores (its own grid)
   bool lg_tc;
   int grid_lg;
-  // FP32 Gaussian factor for the move / reweight kernel's parameters
+  // FP32 Gaussian samplers (have_gp): the factor for the move / reweight
+  // kernel's parameters, valid once gp_ready (smc::fetch_gp)
   smc::GaussParamsF32 gp;
   bool have_gp;
+  bool gp_ready;
   // SMC_FLAG_DEFER_REDISTRIBUTE honoured: resampled rows are gathered by the next move
   bool defer;
   // CUDA graph of one iteration (with and without the covariance stage)
@@ -64,6 +66,9 @@ QuantArgs quant_args(const smc_sampler* h, int force, int32_t* ncopies);
 RedistArgs redist_args(const smc_sampler* h, int force);
 // Completes a deferred redistribution on h's stream (no-op without the flag).
 cudaError_t materialize(smc_sampler* h);
+// Makes h->gp valid (FP32 Gaussian samplers; synchronises h's stream the
+// first time; not during stream capture).
+cudaError_t fetch_gp(smc_sampler* h);
 int sm_count();
 
 }  // namespace smc

@@ -202,17 +202,23 @@ cudaError_t launch_step_setup(DevState* st, smc_iter_stats* trace, double* mean_
 int logistic_tc_grid(int64_t n, int sms);
 cudaError_t launch_logistic_tc(const ParticleArgs& a, int grid, cudaStream_t s);
 
-// batched launches (one per stage for many samplers; int4 map = {sampler, block, blocks, 0})
+// batched launches (one per stage for many samplers; int4 map = {sampler, block, blocks, 0}).
+// left (standing batches of slots, k_slots): per-member count of iterations
+// still to run in this call; members at 0 do nothing, and the commit
+// decrements it.  NULL for plain batches (every member runs).
 cudaError_t launch_move_reweight_batch(const ParticleArgs* pa, const GaussParamsF32* gps, const int4* map, int nblocks,
-                                       cudaStream_t s);
-cudaError_t launch_max_finalize_batch(const ParticleArgs* pa, const int* nb, int count, cudaStream_t s);
-cudaError_t launch_begin_batch(const ParticleArgs* pa, int count, cudaStream_t s);
-cudaError_t launch_commit_batch(const ParticleArgs* pa, int count, cudaStream_t s);
-cudaError_t launch_quant_reduce_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s);
-cudaError_t launch_quant_finalize_batch(const QuantArgs* qa, int count, cudaStream_t s);
-cudaError_t launch_quant_scan_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s);
+                                       cudaStream_t s, const int32_t* left = nullptr);
+cudaError_t launch_max_finalize_batch(const ParticleArgs* pa, const int* nb, int count, cudaStream_t s,
+                                      const int32_t* left = nullptr);
+cudaError_t launch_begin_batch(const ParticleArgs* pa, int count, cudaStream_t s, const int32_t* left = nullptr);
+cudaError_t launch_commit_batch(const ParticleArgs* pa, int count, cudaStream_t s, int32_t* left = nullptr);
+cudaError_t launch_quant_reduce_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s,
+                                      const int32_t* left = nullptr);
+cudaError_t launch_quant_finalize_batch(const QuantArgs* qa, int count, cudaStream_t s, const int32_t* left = nullptr);
+cudaError_t launch_quant_scan_batch(const QuantArgs* qa, const int4* map, int nblocks, cudaStream_t s,
+                                    const int32_t* left = nullptr);
 cudaError_t launch_redistribute_batch(const RedistArgs* ra, const int4* map, int nblocks, int copy_variant,
-                                      cudaStream_t s);  // copy_variant: 4, 8, 16 loads in flight per thread
+                                      cudaStream_t s, const int32_t* left = nullptr);  // copy_variant: 4, 8, 16 loads in flight per thread
 cudaError_t launch_identity_runs_batch(const RedistArgs* ra, const int4* map, int nblocks, cudaStream_t s);
 cudaError_t launch_step_setup_batch(const ParticleArgs* pa, void* const* outs, int count, cudaStream_t s);
 cudaError_t launch_take_errors_batch(const ParticleArgs* pa, int32_t* errs, int count, cudaStream_t s);

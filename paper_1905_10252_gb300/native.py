@@ -31,7 +31,10 @@ EXPORTED = [
     "smc_batch_step_profile", "smc_batch_set_variant", "smc_batch_tune", "smc_batch_sync", "smc_batch_destroy", "smc_batch_last_error",
     "smc_checkpoint_bytes", "smc_checkpoint_save", "smc_checkpoint_load",
     "smc_nearly_sort_ws_bytes", "smc_nearly_sort_raw", "smc_redistribute_raw_profile",
+    "smc_slots_ws_bytes", "smc_slots_create", "smc_slots_attach", "smc_slots_detach", "smc_slots_step",
+    "smc_slots_sync", "smc_slots_destroy", "smc_slots_last_error",
 ]
+LAST_ERROR = ("smc_last_error", "smc_batch_last_error", "smc_slots_last_error")
 
 BATCH_MOVE_VARIANTS, BATCH_COPY_VARIANTS = 5, 3  # SMC_BATCH_MOVE_VARIANTS, SMC_BATCH_COPY_VARIANTS
 
@@ -127,8 +130,17 @@ def _declare(L: C.CDLL) -> None:
     L.smc_checkpoint_bytes.argtypes = [vp, C.POINTER(sz)]
     L.smc_checkpoint_save.argtypes = [vp, vp, sz]
     L.smc_checkpoint_load.argtypes = [vp, vp, sz]
+    L.smc_slots_ws_bytes.argtypes = [C.POINTER(i64), i32, C.POINTER(sz)]
+    L.smc_slots_create.argtypes = [C.POINTER(vp), C.POINTER(i64), i32, vp, sz, vp]
+    L.smc_slots_attach.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.smc_slots_detach.argtypes = [vp, i32]
+    L.smc_slots_step.argtypes = [vp, C.POINTER(i32)]
+    L.smc_slots_sync.argtypes = [vp, C.POINTER(i32)]
+    L.smc_slots_destroy.argtypes = [vp]
+    L.smc_slots_last_error.argtypes = [vp]
+    L.smc_slots_last_error.restype = C.c_char_p
     for name in EXPORTED:
-        if name not in ("smc_last_error", "smc_batch_last_error"):
+        if name not in LAST_ERROR:
             getattr(L, name).restype = C.c_int
 
 
@@ -512,6 +524,68 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lib().smc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_slots(rc: int, handle=None) -> None:
+    if rc != SMC_OK:
+        msg = lib().smc_slots_last_error(handle).decode(errors="replace")
+        raise SmcError(rc, msg)
+
+
+class Slots:
+    """A standing batch of slots of fixed capacity (cap[s] particles): FP32
+    Gaussian samplers are attached to and detached from slots between steps
+    without rebuilding the launch layout, and each step runs a per-slot
+    number of iterations in one launch per stage.  Results per sampler equal
+    those of ``Sampler.step`` alone."""
+
+    def __init__(self, caps, stream: torch.cuda.Stream | None = None, device="cuda"):
+        L = lib()
+        self.caps = [int(c) for c in caps]
+        self.count = len(self.caps)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        arr = (C.c_int64 * self.count)(*self.caps)
+        nbytes = C.c_size_t()
+        _check_slots(L.smc_slots_ws_bytes(arr, self.count, C.byref(nbytes)))
+        self.ws = _alloc_ws(nbytes.value, self.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        h = C.c_void_p()
+        _check_slots(L.smc_slots_create(C.byref(h), arr, self.count, _ptr(self.ws), nbytes.value,
+                                        self.stream.cuda_stream))
+        self.h = h
+        self.members: list = [None] * self.count
+
+    def attach(self, slot: int, sampler: Sampler, mean: torch.Tensor | None = None,
+               trace: torch.Tensor | None = None, fhat: torch.Tensor | None = None) -> None:
+        _check_slots(lib().smc_slots_attach(self.h, int(slot), sampler.h, _ptr(mean), _ptr(trace), _ptr(fhat)),
+                     self.h)
+        self.members[slot] = sampler
+
+    def detach(self, slot: int) -> None:
+        _check_slots(lib().smc_slots_detach(self.h, int(slot)), self.h)
+        self.members[slot] = None
+
+    def step(self, iters) -> None:
+        """iters: per-slot iteration counts (0 for idle and empty slots)."""
+        arr = (C.c_int32 * self.count)(*[int(v) for v in iters])
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        _check_slots(lib().smc_slots_step(self.h, arr), self.h)
+
+    def sync(self) -> None:
+        which = C.c_int32(-1)
+        _check_slots(lib().smc_slots_sync(self.h, C.byref(which)), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().smc_slots_destroy(self.h)
             self.h = None
 
     def __del__(self):

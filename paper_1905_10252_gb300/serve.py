@@ -100,9 +100,10 @@ class Engine:
         returns the ids it launched (the others stay idle for now)."""
         raise NotImplementedError
 
-    def completed(self) -> list[int]:
+    def completed(self, block: bool = True) -> list[int]:
         """Ids of jobs whose launched iterations have all completed since the
-        last call; blocks until at least one has, when any work is pending."""
+        last call; with block, waits until at least one has, when any work
+        is pending."""
         raise NotImplementedError
 
     def result(self, job: Job) -> np.ndarray:
@@ -118,6 +119,7 @@ class Scheduler:
     budget_bytes: int
     round_iters: int = 5
     max_wait_rounds: int = 50
+    admit_per_pass: int = 32       # jobs admitted per pass of the loop, so that launches start early
     clock: callable = time.perf_counter
     queue: list[Job] = field(default_factory=list)
     active: list[Job] = field(default_factory=list)
@@ -127,6 +129,7 @@ class Scheduler:
     rounds: int = 0
     _cancel_ids: set = field(default_factory=set)
     _lock: threading.Lock = field(default_factory=threading.Lock)
+    _capped: bool = False          # the last admission pass stopped at admit_per_pass
 
     def cancel(self, jid: int) -> None:
         """Requests the cancellation of job jid (takes effect in the serving
@@ -171,7 +174,13 @@ class Scheduler:
     def _admit(self, now: float) -> None:
         blocked = False
         still = []
+        admitted = 0
+        self._capped = False
         for job in self.queue:
+            if admitted >= self.admit_per_pass:
+                still.append(job)  # (considered again at the next pass)
+                self._capped = True
+                continue
             need = self.engine.bytes_needed(job)
             if need > self.budget_bytes:
                 raise ValueError(f"job {job.jid} needs {need} bytes, more than the whole budget")
@@ -181,6 +190,7 @@ class Scheduler:
                 job.status = "resident"
                 self.used_bytes += need
                 self.active.append(job)
+                admitted += 1
             else:
                 job.waited_rounds += 1
                 still.append(job)
@@ -216,7 +226,9 @@ class Scheduler:
                     if wait > 0:
                         time.sleep(min(wait, 0.005))
                 continue
-            done_ids = set(self.engine.completed())
+            # (jobs left queued by the per-pass cap: admit them without
+            # waiting for a completion)
+            done_ids = set(self.engine.completed(block=not self._capped))
             still = []
             for j in self.active:
                 if j.jid in done_ids:
@@ -246,6 +258,31 @@ def poisson_arrivals(count: int, rate: float, seed: int = 0) -> np.ndarray:
     return np.cumsum(g.exponential(1.0 / rate, size=count))
 
 
+_STREAMS: dict = {}  # (device, priority) -> streams free for reuse by new jobs
+
+
+class _DeviceCopies:
+    """Device copies of the host arrays jobs bring (targets, data), made once
+    per array: a cache entry keeps its array alive, so its id() stays unique
+    while cached (least recently used entries dropped beyond ``size``)."""
+
+    def __init__(self, torch, device, size: int = 256):
+        self.torch, self.device, self.size = torch, device, size
+        self.entries: dict = {}
+
+    def get(self, a, dtype):
+        if a is None:
+            return None
+        key = (id(a), dtype)
+        hit = self.entries.pop(key, None)
+        if hit is None:
+            hit = (a, self.torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).to(self.device))
+        self.entries[key] = hit  # most recent last
+        while len(self.entries) > self.size:
+            self.entries.pop(next(iter(self.entries)))
+        return hit[1]
+
+
 class GpuEngine(Engine):
     """Jobs as libsmc samplers on one GPU (see the module docstring)."""
 
@@ -271,6 +308,16 @@ class GpuEngine(Engine):
         self.stream = torch.cuda.Stream(device=device, priority=hi_prio)
         self.pending: list = []  # (event, job ids, is the batch) of launched work
         self.batch_busy = False
+        self.copies = _DeviceCopies(torch, device)
+        self.job_stream: dict[int, object] = {}
+
+    def _stream(self, job: Job):
+        """A stream of its own for the job, reused from released jobs."""
+        key = (str(self.device), self.hi_prio if job.kind == "gauss" else 0)
+        pool = _STREAMS.setdefault(key, [])
+        st = pool.pop() if pool else self.torch.cuda.Stream(device=self.device, priority=key[1])
+        self.job_stream[job.jid] = (key, st)
+        return st
 
     def bytes_needed(self, job: Job) -> int:
         # particle state (two buffers), log w, two log pi buffers, workspace
@@ -286,14 +333,17 @@ class GpuEngine(Engine):
 
     def admit(self, job: Job) -> None:
         nat = self.native
+        torch = self.torch
         if job.kind == "gauss":
-            dt = self.torch.float64 if job.dtype == "f64" else self.torch.float32
-            s = nat.Sampler(job.n, job.d, dtype=dt, seed=job.seed, mu=job.mu, sigma=job.sigma,
-                            step=job.step, init_scale=job.init_scale,
-                            stream=self.torch.cuda.Stream(device=self.device, priority=self.hi_prio))
+            dt = torch.float64 if job.dtype == "f64" else torch.float32
+            s = nat.Sampler(job.n, job.d, dtype=dt, seed=job.seed, mu=self.copies.get(job.mu, torch.float64),
+                            sigma=self.copies.get(job.sigma, torch.float64), step=job.step,
+                            init_scale=job.init_scale, stream=self._stream(job))
         else:
-            s = nat.Sampler(job.n, job.d, dtype=self.torch.float32, seed=job.seed, target="logistic", X=job.X,
-                            y=job.y, prior_var=job.prior_var, step=job.step, init_scale=job.init_scale)
+            s = nat.Sampler(job.n, job.d, dtype=torch.float32, seed=job.seed, target="logistic",
+                            X=self.copies.get(job.X, torch.float32), y=self.copies.get(job.y, torch.float32),
+                            prior_var=job.prior_var, step=job.step, init_scale=job.init_scale,
+                            stream=self._stream(job))
         self.samplers[job.jid] = s
         self.means[job.jid] = self.torch.empty(job.d, dtype=self.torch.float64, device=self.device)
         if job.keep:
@@ -357,21 +407,17 @@ class GpuEngine(Engine):
             launched.append(j.jid)
         return launched
 
-    def completed(self) -> list[int]:
+    def completed(self, block: bool = True) -> list[int]:
         if not self.pending:
             return []
-        # poll every launch: blocking on one long logistic run would leave
-        # the (short) batch idle until it ends; the batch's own event is the
-        # one worth waiting on directly
+        # poll every launch, with a short sleep between polls: blocking on any
+        # one event would hold up the relaunch of the others (and the
+        # admission of arrivals) until it completes
         while True:
             done = [p for p in self.pending if p[0].query()]
-            if done:
+            if done or not block:
                 break
-            batch = [p for p in self.pending if p[2]]
-            if batch:
-                batch[0][0].synchronize()
-            else:
-                time.sleep(50e-6)
+            time.sleep(20e-6)
         self.pending = [p for p in self.pending if p not in done]
         if any(p[2] for p in done):
             self.batch_busy = False
@@ -394,3 +440,81 @@ class GpuEngine(Engine):
         self.samplers.pop(job.jid).close()
         self.means.pop(job.jid)
         self.traces.pop(job.jid, None)
+        key, st = self.job_stream.pop(job.jid)
+        _STREAMS[key].append(st)
+
+
+class SlotEngine(GpuEngine):
+    """GpuEngine whose FP32 Gaussian jobs live in a standing batch of slots
+    (``native.Slots``): the launch layout -- block maps and the CUDA graph of
+    one batched iteration -- is built once, for slots of capacities 2^10 ..
+    2^18 particles (``per_class`` slots each), and admitting or retiring a
+    job only edits the slot table on the device.  Every round advances all
+    idle slotted jobs together (each by its own count) in one launch per
+    stage.  An FP32 Gaussian job that fits no free slot waits for one
+    (batched iterations are several times cheaper than its own); one larger
+    than every slot, FP64 and logistic jobs, and jobs whose statistics are
+    kept run one launch per job as in GpuEngine."""
+
+    def __init__(self, device: str = "cuda", caps=None, per_class: int = 32):
+        super().__init__(batched=False, device=device)
+        self.caps = list(caps) if caps is not None else [1 << c for c in range(10, 19) for _ in range(per_class)]
+        self.slots = self.native.Slots(self.caps, stream=self.stream, device=device)
+        self.slot_of: dict[int, int] = {}
+        self.free = set(range(len(self.caps)))
+        self.slots_busy = False
+
+    def _slotted_kind(self, job: Job) -> bool:
+        return job.kind == "gauss" and job.dtype == "f32" and not job.keep and job.n <= max(self.caps)
+
+    def _try_attach(self, job: Job) -> bool:
+        fits = [s for s in self.free if self.caps[s] >= job.n]
+        if not fits:
+            return False
+        s = min(fits, key=lambda q: (self.caps[q], q))
+        self.free.discard(s)
+        self.slots.attach(s, self.samplers[job.jid], mean=self.means[job.jid])
+        self.slot_of[job.jid] = s
+        return True
+
+    def admit(self, job: Job) -> None:
+        super().admit(job)
+        if self._slotted_kind(job):
+            self._try_attach(job)
+
+    def step(self, jobs: list[Job], iters: dict[int, int]) -> list[int]:
+        torch = self.torch
+        # jobs still waiting for a slot take one that has freed
+        for j in jobs:
+            if j.jid not in self.slot_of and self._slotted_kind(j):
+                self._try_attach(j)
+        slotted = [j for j in jobs if j.jid in self.slot_of]
+        others = [j for j in jobs if j.jid not in self.slot_of and not self._slotted_kind(j)]
+        launched = []
+        if slotted and not self.slots_busy:
+            counts = [0] * len(self.caps)
+            for j in slotted:
+                counts[self.slot_of[j.jid]] = int(iters[j.jid])
+            self.slots.step(counts)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            self.pending.append((ev, [j.jid for j in slotted], True))
+            self.slots_busy = True
+            launched += [j.jid for j in slotted]
+        if others:
+            launched += super().step(others, iters)
+        return launched
+
+    def completed(self, block: bool = True) -> list[int]:
+        self.batch_busy = self.slots_busy
+        out = super().completed(block)
+        self.slots_busy = self.batch_busy
+        return out
+
+    def release(self, job: Job) -> None:
+        s = self.slot_of.pop(job.jid, None)
+        if s is not None:
+            self.slots.detach(s)
+            self.free.add(s)
+        super().release(job)
+

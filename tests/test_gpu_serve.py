@@ -147,3 +147,23 @@ def test_served_fp64_job_equals_oracle(nat, orc):
     for j in done.values():
         if j.jid != 99:
             assert np.array_equal(j.result, alone(nat, j)), (j.jid, j.kind)
+
+
+@pytest.mark.parametrize("per_class", [1, 4])
+def test_slot_engine_results_equal_alone(nat, per_class):
+    """The served engine: FP32 Gaussian jobs in a standing batch of slots
+    (attached on admission, detached on completion, never rebuilt), under a
+    memory budget that forces queueing; with one slot per capacity class
+    some jobs find no free slot and run one launch per job.  Every job's
+    f_K equals its solo run bit for bit."""
+    from paper_1905_10252_gb300.serve import Scheduler, SlotEngine
+
+    jobs = make_jobs()
+    eng = SlotEngine(per_class=per_class)
+    need = sum(eng.bytes_needed(j) for j in jobs)
+    sch = Scheduler(eng, budget_bytes=need // 3, round_iters=3)
+    done = sch.run(jobs)
+    assert len(done) == len(jobs)
+    assert not eng.slot_of and len(eng.free) == len(eng.caps)
+    for j in done:
+        assert np.array_equal(j.result, alone(nat, j)), (j.jid, j.kind)

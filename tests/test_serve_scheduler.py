@@ -42,7 +42,7 @@ class FakeEngine(Engine):
         self.pending = [j.jid for j in jobs]
         return list(self.pending)
 
-    def completed(self):
+    def completed(self, block=True):
         out, self.pending = self.pending, []
         return out
 
@@ -173,3 +173,24 @@ def test_deadline_cancels_jobs_that_would_finish_late():
     assert [j.jid for j in sch.cancelled] == [1]
     assert jobs[1].finished - jobs[1].arrival > 0.01
     assert sch.used_bytes == 0 and not eng.resident
+
+
+def test_admission_is_spread_over_passes():
+    """At most admit_per_pass jobs are admitted per pass of the loop (so that
+    launches start while the rest are admitted); every job still runs."""
+    class Counting(FakeEngine):
+        def __init__(self):
+            super().__init__()
+            self.steps = []
+
+        def step(self, jobs, iters):
+            self.steps.append(len(self.resident))
+            return super().step(jobs, iters)
+
+    eng = Counting()
+    jobs = make_jobs([1] * 50, [3] * 50, [0.0] * 50)
+    sch = Scheduler(eng, budget_bytes=10 ** 6, round_iters=1, admit_per_pass=8)
+    done = sch.run(jobs)
+    assert len(done) == 50
+    assert eng.steps[0] == 8  # the first launch came after 8 admissions
+    assert max(eng.steps) <= 50
