@@ -495,6 +495,47 @@ __global__ void __launch_bounds__(kFinThreads) k_quant_finalize(QuantArgs a, int
   quant_finalize_body(a, set_lse_prev);
 }
 
+// ---------------------------------------------------------------- copy-tile sources
+// Every redistribute tile whose first output row k lies in a survivor's run
+// [lo, hi) gets src = that survivor.  A thread writes the tile starts of its
+// own short runs; a run spanning more than kBigRun tile starts (a heavily
+// copied particle: in the one-hot case one run covers all N rows) is queued
+// and written by the whole block after a barrier.  Every thread of the block
+// must call tile_starts_flush.
+constexpr int kBigRun = 4;
+constexpr int kBigRuns = 64;
+struct BigRuns {
+  int count;
+  int32_t src[kBigRuns];
+  int64_t first[kBigRuns];  // first tile index
+  int64_t tiles[kBigRuns];  // tile starts in the run
+};
+
+__device__ __forceinline__ void tile_starts_of_run(int32_t* __restrict__ tile_src, uint64_t lo, uint64_t hi,
+                                                   uint64_t n, int32_t i, BigRuns& big) {
+  const uint64_t kb0 = ((lo + kRTile - 1) / kRTile) * kRTile;
+  const uint64_t end = hi < n ? hi : n;
+  if (kb0 >= end) return;
+  const uint64_t tiles = (end - kb0 + kRTile - 1) / kRTile;
+  if (tiles > uint64_t(kBigRun)) {
+    const int slot = atomicAdd(&big.count, 1);
+    if (slot < kBigRuns) {
+      big.src[slot] = i;
+      big.first[slot] = int64_t(kb0 / kRTile);
+      big.tiles[slot] = int64_t(tiles);
+      return;
+    }
+  }
+  for (uint64_t kb = kb0; kb < end; kb += kRTile) tile_src[kb / kRTile] = i;  // (short run, or the queue is full)
+}
+
+__device__ __forceinline__ void tile_starts_flush(int32_t* __restrict__ tile_src, BigRuns& big) {
+  __syncthreads();
+  const int nb = min(big.count, kBigRuns);
+  for (int r = 0; r < nb; ++r)
+    for (int64_t t = threadIdx.x; t < big.tiles[r]; t += blockDim.x) tile_src[big.first[r] + t] = big.src[r];
+}
+
 // ---------------------------------------------------------------- quantise: scan + ncopies
 __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int blk) {
   const DevState* st = a.st;
@@ -504,6 +545,8 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
     uint32_t o[kQThreads * 17];
   } buf;
   __shared__ uint64_t scratch[33];
+  __shared__ BigRuns big;
+  if (threadIdx.x == 0) big.count = 0;
   const int64_t n = a.n;
   const int64_t base = int64_t(blk) * kQTile;
   // the quantised weights of the reduce pass, staged for a blocked layout
@@ -559,10 +602,10 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
       ++nsurv;
       if (a.write_rs) rs_now(a.runstart, a.runstart_alt, st)[lo] = int32_t(i);
       // every redistribute tile whose first output row lies in [lo, hi)
-      for (uint64_t kb = ((lo + kRTile - 1) / kRTile) * kRTile; kb < hi && kb < uint64_t(n); kb += kRTile)
-        a.tile_src[kb / kRTile] = int32_t(i);
+      tile_starts_of_run(a.tile_src, lo, hi, uint64_t(n), int32_t(i), big);
     }
   }
+  tile_starts_flush(a.tile_src, big);
   {
     unsigned v = nsurv;
 #pragma unroll
@@ -607,6 +650,23 @@ __device__ __forceinline__ void load_counts(const int32_t* __restrict__ nc, int6
   }
 }
 
+// Exclusive prefix of the block sums (cbase) and the check sum == n.
+__device__ __forceinline__ void nc_finalize_body(const NcScanArgs& a) {
+  __shared__ uint64_t scratch[33];
+  const int nb = a.nblocks;
+  const int chunk = (nb + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * chunk, b1 = min(nb, b0 + chunk);
+  uint64_t local = 0;
+  for (int b = b0; b < b1; ++b) local += a.part[b];
+  uint64_t total;
+  uint64_t pre = block_excl_scan_u64(local, scratch, &total);
+  for (int b = b0; b < b1; ++b) {
+    a.cbase[b] = pre;
+    pre += a.part[b];
+  }
+  if (threadIdx.x == 0 && total != uint64_t(a.n)) record_error(a.st, SMC_EINVAL);
+}
+
 __global__ void __launch_bounds__(kQThreads) k_nc_reduce(NcScanArgs a) {
   __shared__ uint64_t sh[kQThreads / 32];
   __shared__ int bad;
@@ -615,6 +675,21 @@ __global__ void __launch_bounds__(kQThreads) k_nc_reduce(NcScanArgs a) {
   const int64_t first = int64_t(blockIdx.x) * kQTile + int64_t(threadIdx.x) * kQItems;
   int32_t c[kQItems];
   load_counts(a.ncopies, a.n, first, c);
+  if (a.clear_rs) {
+    // the run-start array starts at -1 for the scan: this block's slice
+    // [4096 b, 4096 b + 4096) of it, with 16-byte stores (the array is
+    // 256-byte aligned) and single stores for a partial last vector
+    int4* rs4 = reinterpret_cast<int4*>(a.runstart);
+    const int64_t v0 = int64_t(blockIdx.x) * (kQTile / 4);
+#pragma unroll
+    for (int u = 0; u < kQTile / 4 / kQThreads; ++u) {
+      const int64_t v = v0 + u * kQThreads + threadIdx.x;
+      if (4 * v + 3 < a.n)
+        rs4[v] = make_int4(-1, -1, -1, -1);
+      else
+        for (int64_t k = 4 * v; k < a.n; ++k) a.runstart[k] = -1;
+    }
+  }
   uint64_t s = 0;
   bool neg = false;
 #pragma unroll
@@ -634,34 +709,40 @@ __global__ void __launch_bounds__(kQThreads) k_nc_reduce(NcScanArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kFinThreads) k_nc_finalize(NcScanArgs a) {
-  __shared__ uint64_t scratch[33];
-  const int nb = a.nblocks;
-  const int chunk = (nb + blockDim.x - 1) / blockDim.x;
-  const int b0 = threadIdx.x * chunk, b1 = min(nb, b0 + chunk);
-  uint64_t local = 0;
-  for (int b = b0; b < b1; ++b) local += a.part[b];
-  uint64_t total;
-  uint64_t pre = block_excl_scan_u64(local, scratch, &total);
-  for (int b = b0; b < b1; ++b) {
-    a.cbase[b] = pre;
-    pre += a.part[b];
-  }
-  if (threadIdx.x == 0 && total != uint64_t(a.n)) record_error(a.st, SMC_EINVAL);
-}
+__global__ void __launch_bounds__(kFinThreads) k_nc_finalize(NcScanArgs a) { nc_finalize_body(a); }
 
-// Run starts of the block's items: the block's outputs form the window
-// [cbase, cbase + total); when it fits in shared memory it is assembled
-// there (-1, then the run starts) and written out with coalesced stores,
-// otherwise the run starts are stored one by one into the already cleared
-// array.
+// Run starts of the block's items.  The block's outputs form the window
+// [cbase, cbase + total); the windows of the blocks are disjoint and tile
+// [0, n).  A window that fits shared memory is assembled there (-1, then the
+// run starts) and written out with coalesced stores.  A larger one, when the
+// run-start array holds -1 everywhere on entry (a sampler's, kept clean by
+// the copy that consumes it), gets its run starts stored one by one.
+// Stamped calls (a.stamps set; the stateless entry points, whose array is
+// not cleared): every copy tile that receives a run start is stamped, and
+// the copy reads the run starts of stamped tiles only, so a larger window
+// sets -1 over all of itself when it has at most kFillAll rows, else over
+// its part of its two edge copy tiles and of every copy tile where it puts a
+// run start (over all of itself if those overflow a queue), before its run
+// starts -- every slice the copy reads is then written in this call.
 constexpr int kNcWin = 8192;
+constexpr int kFillTiles = 128;
+constexpr uint64_t kFillAll = 1u << 17;
 
 __global__ void __launch_bounds__(kQThreads) k_nc_scan(NcScanArgs a) {
   if (a.st->err) return;
   __shared__ int32_t win[kNcWin];
   __shared__ uint64_t scratch[33];
+  __shared__ BigRuns big;
+  __shared__ int s_nfill;
+  __shared__ int64_t s_fill[kFillTiles];
+  __shared__ int s_has[kNcWin / kRTile + 2];  // staged window: its tiles that receive a run start
+  if (threadIdx.x == 0) {
+    big.count = 0;
+    s_nfill = 0;
+  }
+  if (threadIdx.x < kNcWin / kRTile + 2) s_has[threadIdx.x] = 0;
   const int64_t n = a.n;
+  const uint64_t un = uint64_t(n);
   const int64_t base = int64_t(blockIdx.x) * kQTile;
   const int64_t i0 = base + int64_t(threadIdx.x) * kQItems;
   int32_t c[kQItems];
@@ -671,31 +752,72 @@ __global__ void __launch_bounds__(kQThreads) k_nc_scan(NcScanArgs a) {
   for (int q = 0; q < kQItems; ++q) tsum += uint32_t(c[q]);
   uint64_t btot;
   const uint64_t w0 = a.cbase[blockIdx.x];
-  const uint64_t o0 = w0 + block_excl_scan_u64(tsum, scratch, &btot);
+  const uint64_t excl = block_excl_scan_u64(tsum, scratch, &btot);  // (block barriers inside)
+  const uint64_t wend = min(w0 + btot, un);
   const bool staged = btot <= uint64_t(kNcWin);
+  const bool stamped = a.stamps != nullptr;
+  const bool fill_all = stamped && !staged && btot <= kFillAll;
+  int32_t* __restrict__ rsa = rs_now(a.runstart, a.runstart_alt, a.st);
   if (staged) {
     for (int k = threadIdx.x; k < int(btot); k += blockDim.x) win[k] = -1;
-    __syncthreads();
+  } else if (stamped && !fill_all && threadIdx.x == 0 && w0 < wend) {
+    s_fill[0] = int64_t(w0 / kRTile);  // the edge tiles, shared with the neighbouring windows
+    s_fill[1] = int64_t((wend - 1) / kRTile);
+    s_nfill = 2;
   }
-  int32_t* __restrict__ rsa = rs_now(a.runstart, a.runstart_alt, a.st);
-  uint64_t o = o0;
+  __syncthreads();
+  uint64_t o = w0 + excl;
+  if (stamped && !staged) {
+    if (!fill_all) {
+      int64_t last = -1;
+#pragma unroll
+      for (int q = 0; q < kQItems; ++q) {
+        if (c[q] > 0 && i0 + q < n && o < un && int64_t(o / kRTile) != last) {
+          last = int64_t(o / kRTile);
+          const int slot = atomicAdd(&s_nfill, 1);
+          if (slot < kFillTiles) s_fill[slot] = last;
+        }
+        o += uint32_t(c[q]);
+      }
+      __syncthreads();
+    }
+    if (fill_all || s_nfill > kFillTiles) {
+      for (uint64_t k = w0 + threadIdx.x; k < wend; k += blockDim.x) rsa[k] = -1;
+    } else {
+      for (int f = 0; f < s_nfill; ++f) {
+        const uint64_t t0 = max(w0, uint64_t(s_fill[f]) * kRTile);
+        const uint64_t t1 = min(wend, uint64_t(s_fill[f]) * kRTile + kRTile);
+        for (uint64_t k = t0 + threadIdx.x; k < t1; k += blockDim.x) rsa[k] = -1;
+      }
+    }
+    __syncthreads();  // every -1 before any run start
+    o = w0 + excl;
+  }
+  const uint64_t tfirst = w0 / kRTile;
+  int64_t stamped_tile = -1;  // (a thread's items are consecutive: one stamp per tile it reaches)
 #pragma unroll
   for (int q = 0; q < kQItems; ++q) {
     const int64_t i = i0 + q;
-    if (c[q] > 0 && i < n && o < uint64_t(n)) {
-      if (staged)
+    if (c[q] > 0 && i < n && o < un) {
+      if (staged) {
         win[o - w0] = int32_t(i);
-      else
+        if (stamped) s_has[o / kRTile - tfirst] = 1;
+      } else {
         rsa[o] = int32_t(i);
-      for (uint64_t kb = ((o + kRTile - 1) / kRTile) * kRTile; kb < o + uint32_t(c[q]) && kb < uint64_t(n); kb += kRTile)
-        a.tile_src[kb / kRTile] = int32_t(i);
+        if (stamped && int64_t(o / kRTile) != stamped_tile) {
+          stamped_tile = int64_t(o / kRTile);
+          a.stamps[stamped_tile] = 1;
+        }
+      }
+      tile_starts_of_run(a.tile_src, o, o + uint32_t(c[q]), un, int32_t(i), big);
     }
     o += uint32_t(c[q]);
   }
+  tile_starts_flush(a.tile_src, big);  // (block barrier inside)
   if (staged) {
-    __syncthreads();
     int32_t* __restrict__ rs = rsa + w0;
-    for (int k = threadIdx.x; k < int(btot); k += blockDim.x) rs[k] = win[k];
+    for (int k = threadIdx.x; w0 + uint64_t(k) < wend; k += blockDim.x) rs[k] = win[k];
+    if (stamped && threadIdx.x < kNcWin / kRTile + 2 && s_has[threadIdx.x]) a.stamps[tfirst + threadIdx.x] = 1;
   }
 }
 
@@ -724,20 +846,23 @@ __device__ __forceinline__ void redistribute_body(const RedistArgs& a, const int
   // this tile's slice of runstart (survivor runs starting here), reset to -1
   // for the next resampling
   int32_t* __restrict__ rs = rs_now(a.runstart, a.runstart_alt, a.st) + k0;
+  // (a stamped stateless call: an unstamped tile has no run starts, and its
+  // slice is neither read nor reset)
+  const bool read = !a.stamps || a.stamps[blk];
   {
     constexpr int kItems = kRTile / kRThreads;
     int32_t v[kItems];
 #pragma unroll
     for (int u = 0; u < kItems; ++u) {
       const int k = threadIdx.x + u * kRThreads;
-      v[u] = k < len ? rs[k] : -1;
+      v[u] = (read && k < len) ? rs[k] : -1;
     }
 #pragma unroll
     for (int u = 0; u < kItems; ++u) {
       const int k = threadIdx.x + u * kRThreads;
-      // reset only the entries that were set (measured: rewriting the whole
-      // slice costs ~0.15 ms more at N = 2^24)
-      if (k < len && v[u] >= 0) rs[k] = -1;
+      // reset only the entries that were set (rewriting the whole slice was
+      // measured slower); stamped calls need no reset
+      if (!a.stamps && k < len && v[u] >= 0) rs[k] = -1;
       mark[k] = v[u] < int32_t(n) ? v[u] : int32_t(n - 1);
     }
   }

@@ -657,7 +657,7 @@ const char* smc_last_error(const smc_sampler* h) { return h ? h->err.c_str() : g
 // ------------------------------------------------------------------ stateless
 namespace {
 struct RawLayout {
-  size_t st, part, qpart, cbase, rs, wbuf, tile_src, total;
+  size_t st, part, qpart, cbase, rs, wbuf, tile_src, stamps, total;
   int qblocks, ntiles;
 };
 RawLayout raw_layout(int64_t n) {
@@ -679,6 +679,10 @@ RawLayout raw_layout(int64_t n) {
   p = align_up(p + size_t(n) * sizeof(uint64_t));
   L.tile_src = p;
   p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
+  // per copy tile: run starts were written there (zeroed by each
+  // redistribute call)
+  L.stamps = p;
+  p = align_up(p + size_t(L.ntiles) * sizeof(int32_t));
   L.total = p;
   return L;
 }
@@ -721,6 +725,9 @@ int redistribute_raw_impl(int64_t n, int32_t row_bytes, const int32_t* ncopies_d
   a.nblocks = L.qblocks;
   a.ntiles = L.ntiles;
   a.st = st;
+  // stamped: the run-start array is not cleared; the copy reads the slices
+  // of the stamped tiles only, which the scan writes whole
+  a.stamps = reinterpret_cast<int32_t*>(ws + L.stamps);
   RedistArgs r{};
   r.n = n;
   r.row_bytes = row_bytes;
@@ -734,9 +741,10 @@ int redistribute_raw_impl(int64_t n, int32_t row_bytes, const int32_t* ncopies_d
   r.logw = nullptr;
   r.st = st;
   r.stateful = 0;
+  r.stamps = a.stamps;
   cudaError_t e = rec(0);
   if (e == cudaSuccess) e = cudaMemsetAsync(&st->err, 0, sizeof(int32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.runstart, 0xFF, size_t(n) * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.stamps, 0, size_t(L.ntiles) * sizeof(int32_t), s);
   if (e == cudaSuccess) e = launch_nc_reduce(a, s);
   if (e == cudaSuccess) e = launch_nc_finalize(a, s);
   if (e == cudaSuccess) e = launch_nc_scan(a, s);

@@ -154,6 +154,10 @@ struct RedistArgs {
   DevState* st;
   int32_t stateful;      // 1: choose buffers by st->cur, honour st->flag / st->err
   int32_t use_pending;   // stateful: copy iff st->pending (a deferred resampling), not st->flag
+  // stamped calls (see NcScanArgs::stamps): per tile, nonzero when the tile
+  // has run starts (its runstart slice is then fully written; otherwise the
+  // slice is not read and means -1 throughout); NULL: read every slice
+  const int32_t* stamps;
 };
 
 struct NcScanArgs {
@@ -161,12 +165,19 @@ struct NcScanArgs {
   const int32_t* ncopies;
   uint64_t* part;       // per-block sums
   uint64_t* cbase;      // exclusive block prefixes
-  int32_t* runstart;    // must hold -1 everywhere on entry
+  int32_t* runstart;    // must hold -1 everywhere on entry, unless clear_rs
   int32_t* runstart_alt;  // second run-start array (NULL: one array); st->rs_w picks
   int32_t* tile_src;
   int32_t nblocks;
   int32_t ntiles;
   DevState* st;
+  int32_t clear_rs;     // the reduce pass sets runstart[0, n) to -1 first (runstart_alt NULL)
+  int32_t pad;
+  // stamped calls (the stateless entry points; zeroed by the caller before
+  // each call): per copy tile, set when a run start lands in it -- runstart
+  // then need not be clean on entry (k_nc_scan writes every slice the copy
+  // reads); NULL: runstart must hold -1 everywhere on entry
+  int32_t* stamps;
 };
 
 size_t devstate_bytes();

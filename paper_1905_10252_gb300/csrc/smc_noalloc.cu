@@ -105,6 +105,7 @@ extern "C" int smc_redistribute_raw_noalloc(int64_t n, int32_t row_bytes, const 
   a.cbase = reinterpret_cast<uint64_t*>(ws + kAtBase);
   a.runstart = reinterpret_cast<int32_t*>(ws + kAtRun);
   a.tile_src = reinterpret_cast<int32_t*>(ws + kAtTile);
+  a.clear_rs = 1;  // (the reduce pass resets the run starts: no separate pass)
   a.nblocks = int32_t((n + kQTile - 1) / kQTile);
   a.ntiles = int32_t((n + kRTile - 1) / kRTile);
   a.st = st;
@@ -122,7 +123,6 @@ extern "C" int smc_redistribute_raw_noalloc(int64_t n, int32_t row_bytes, const 
   r.st = st;
   r.stateful = 0;
   e = cudaMemsetAsync(&st->err, 0, sizeof(int32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.runstart, 0xFF, size_t(n) * sizeof(int32_t), s);
   if (e == cudaSuccess) e = launch_nc_reduce(a, s);
   if (e == cudaSuccess) e = launch_nc_finalize(a, s);
   if (e == cudaSuccess) e = launch_nc_scan(a, s);

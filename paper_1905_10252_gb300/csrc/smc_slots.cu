@@ -2,10 +2,14 @@
 // of smc_batch.cu with a fixed launch layout, for serving.
 //
 // Each slot has a capacity (the most particles a sampler in it may have).
-// The block maps of every stage are laid out once, at creation, from the
+// The block maps of every stage are sized once, at creation, from the
 // capacities -- a slot's quantise, scan and copy blocks cover its capacity,
 // its move blocks are a share of a fixed budget -- and one batched iteration
-// is captured in a CUDA graph then.  Samplers are attached to and detached
+// is captured in a CUDA graph then.  While membership is unchanged the maps
+// and the graph are reused as they are; after an attach or detach the next
+// step writes compact maps of the attached slots' own blocks (from pinned
+// staging, double buffered) and sets the grid sizes of the graph's four
+// map-driven kernel nodes to match (no re-instantiation).  Samplers are attached to and detached
 // from slots afterwards by editing the slot table in device memory (their
 // kernel arguments, an attached flag, their outputs); a step sets, per slot,
 // how many iterations to run, and replays the graph.  Every kernel reads a
@@ -176,8 +180,16 @@ struct smc_slots {
   SlotsLayout L;
   char* ws;
   cudaStream_t stream;
+  cudaGraph_t tmpl;             // the captured iteration (kept: its nodes are updated)
   cudaGraphExec_t graph;
+  cudaGraphNode_t map_node[4];  // move, quantise reduce, scan, copy: kernels launched over a map
   cudaEvent_t ev;
+  // compact maps: pinned staging (two buffers of qmap | rmap | mmap, each at
+  // its full size) and the event after each buffer's last upload
+  int4* stage[2];
+  cudaEvent_t stage_ev[2];
+  int stage_next;
+  bool dirty;                   // membership changed since the maps were written
   std::vector<int32_t> errs_host;
   std::string err;
 
@@ -239,8 +251,74 @@ cudaError_t build_slots_graph(smc_slots* b) {
     return le;
   }
   if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(&b->graph, g, 0);
-  cudaGraphDestroy(g);
+  // the captured launches form one chain in launch order: begin, move, max,
+  // quantise reduce, quantise finalise, scan, copy, commit
+  cudaGraphNode_t chain[8];
+  size_t nroot = 1;
+  e = cudaGraphGetRootNodes(g, chain, &nroot);
+  for (int k = 1; e == cudaSuccess && k < 8; ++k) {
+    size_t nd = 1;
+    e = cudaGraphNodeGetDependentNodes(chain[k - 1], &chain[k], nullptr, &nd);
+    if (e == cudaSuccess && nd != 1) e = cudaErrorInvalidValue;
+  }
+  if (e == cudaSuccess && nroot != 1) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess) {
+    b->map_node[0] = chain[1];
+    b->map_node[1] = chain[3];
+    b->map_node[2] = chain[5];
+    b->map_node[3] = chain[6];
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  b->tmpl = g;
+  return cudaSuccess;
+}
+
+// Compact maps of the attached slots (their own quantise / copy blocks and
+// the slot's move blocks), uploaded on the slots' stream, and the grid sizes
+// of the map-driven kernel nodes set to the new entry counts.
+cudaError_t write_compact_maps(smc_slots* b) {
+  const size_t fq = b->plan.qmap.size(), fr = b->plan.rmap.size(), fm = b->plan.mmap.size();
+  const int sb = b->stage_next;
+  b->stage_next ^= 1;
+  cudaError_t e = cudaEventSynchronize(b->stage_ev[sb]);  // (that buffer's previous upload is done)
+  if (e != cudaSuccess) return e;
+  int4* q = b->stage[sb];
+  int4* r = q + fq;
+  int4* m = r + fr;
+  size_t nq = 0, nr = 0, nm = 0;
+  // the creation order (largest capacity first), attached slots only
+  std::vector<int> order(b->count);
+  for (int s = 0; s < b->count; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->cap[x] > b->cap[y]; });
+  for (int s : order) {
+    const smc_sampler* h = b->m[s];
+    if (!h) continue;
+    const int hq = h->L.qblocks, hr = h->L.ntiles, hm = b->plan.nb[s];
+    for (int j = 0; j < hq; ++j) q[nq++] = make_int4(s, j, hq, 0);
+    for (int j = 0; j < hr; ++j) r[nr++] = make_int4(s, j, hr, 0);
+    for (int j = 0; j < hm; ++j) m[nm++] = make_int4(s, j, hm, 0);
+  }
+  if (nq == 0) {  // (no slot attached: the maps are not launched)
+    b->dirty = false;
+    return cudaSuccess;
+  }
+  e = cudaMemcpyAsync(b->ws + b->L.qmap, q, nq * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->ws + b->L.rmap, r, nr * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->ws + b->L.mmap, m, nm * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->stage_ev[sb], b->stream);
+  const size_t counts[4] = {nm, nq, nq, nr};
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+    cudaKernelNodeParams kp{};
+    e = cudaGraphKernelNodeGetParams(b->map_node[k], &kp);
+    if (e != cudaSuccess) break;
+    kp.gridDim = dim3(unsigned(counts[k]), 1, 1);
+    e = cudaGraphExecKernelNodeSetParams(b->graph, b->map_node[k], &kp);
+  }
+  if (e == cudaSuccess) b->dirty = false;
   return e;
 }
 
@@ -278,8 +356,13 @@ int smc_slots_create(smc_slots** out, const int64_t* cap_n, int32_t count, void*
   b->L = L;
   b->ws = static_cast<char*>(ws_dev);
   b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->tmpl = nullptr;
   b->graph = nullptr;
   b->ev = nullptr;
+  b->stage[0] = b->stage[1] = nullptr;
+  b->stage_ev[0] = b->stage_ev[1] = nullptr;
+  b->stage_next = 0;
+  b->dirty = true;
   b->errs_host.assign(count, 0);
   b->err = "ok";
   cudaStream_t st = b->stream;
@@ -297,10 +380,20 @@ int smc_slots_create(smc_slots** out, const int64_t* cap_n, int32_t count, void*
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // (the host vectors are pageable)
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+  const size_t maps = b->plan.qmap.size() + b->plan.rmap.size() + b->plan.mmap.size();
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaHostAlloc(reinterpret_cast<void**>(&b->stage[k]), maps * sizeof(int4), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev[k], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = build_slots_graph(b);
   if (e != cudaSuccess) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->tmpl) cudaGraphDestroy(b->tmpl);
     if (b->ev) cudaEventDestroy(b->ev);
+    for (int k = 0; k < 2; ++k) {
+      if (b->stage[k]) cudaFreeHost(b->stage[k]);
+      if (b->stage_ev[k]) cudaEventDestroy(b->stage_ev[k]);
+    }
     delete b;
     return sfail(nullptr, SMC_ECUDA, std::string("smc_slots_create: ") + cudaGetErrorString(e));
   }
@@ -337,6 +430,7 @@ int smc_slots_attach(smc_slots* b, int32_t slot, smc_sampler* h, double* mean_de
   SLOTS_TRY(b, cudaGetLastError());
   SLOTS_TRY(b, launch_step_setup(h->st, trace_dev, mean_dev, fhat_dev, nullptr, b->stream));
   b->m[slot] = h;
+  b->dirty = true;
   return SMC_OK;
 }
 
@@ -352,6 +446,7 @@ int smc_slots_detach(smc_slots* b, int32_t slot) {
   SLOTS_TRY(b, cudaEventRecord(b->ev, b->stream));
   SLOTS_TRY(b, cudaStreamWaitEvent(h->stream, b->ev, 0));
   b->m[slot] = nullptr;
+  b->dirty = true;
   return SMC_OK;
 }
 
@@ -369,6 +464,7 @@ int smc_slots_step(smc_slots* b, const int32_t* iters_host) {
     k = std::max(k, int(v));
   }
   if (k == 0) return SMC_OK;
+  if (b->dirty) SLOTS_TRY(b, write_compact_maps(b));
   k_slots_set_left<<<1, 256, 0, b->stream>>>(b->at<int32_t>(b->L.left), b->count, c);
   SLOTS_TRY(b, cudaGetLastError());
   for (int it = 0; it < k; ++it) SLOTS_TRY(b, cudaGraphLaunch(b->graph, b->stream));
@@ -399,8 +495,14 @@ int smc_slots_sync(smc_slots* b, int32_t* which_host) {
 
 int smc_slots_destroy(smc_slots* b) {
   if (!b) return SMC_OK;
+  cudaStreamSynchronize(b->stream);  // (the pinned staging may still feed an upload)
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->tmpl) cudaGraphDestroy(b->tmpl);
   if (b->ev) cudaEventDestroy(b->ev);
+  for (int k = 0; k < 2; ++k) {
+    if (b->stage[k]) cudaFreeHost(b->stage[k]);
+    if (b->stage_ev[k]) cudaEventDestroy(b->stage_ev[k]);
+  }
   delete b;
   return SMC_OK;
 }

@@ -445,37 +445,47 @@ class GpuEngine(Engine):
 
 
 class SlotEngine(GpuEngine):
-    """GpuEngine whose FP32 Gaussian jobs live in a standing batch of slots
+    """GpuEngine whose FP32 Gaussian jobs live in standing batches of slots
     (``native.Slots``): the launch layout -- block maps and the CUDA graph of
-    one batched iteration -- is built once, for slots of capacities 2^10 ..
-    2^18 particles (``per_class`` slots each), and admitting or retiring a
-    job only edits the slot table on the device.  Every round advances all
-    idle slotted jobs together (each by its own count) in one launch per
-    stage.  An FP32 Gaussian job that fits no free slot waits for one
-    (batched iterations are several times cheaper than its own); one larger
-    than every slot, FP64 and logistic jobs, and jobs whose statistics are
-    kept run one launch per job as in GpuEngine."""
+    one batched iteration -- is built once per batch, and admitting or
+    retiring a job only edits the slot table on the device.  Slots are
+    grouped by capacity into independent batches (by default one per power
+    of two from 2^10 to 2^18 particles, ``per_class`` slots each), each with
+    its own high-priority stream, so that small jobs do not wait for large
+    ones at every stage; every round of a batch advances all its idle jobs
+    together (each by its own count) in one launch per stage.  An
+    FP32 Gaussian job that fits no free slot waits for one (batched
+    iterations are several times cheaper than its own); one larger than
+    every slot, FP64 and logistic jobs, and jobs whose statistics are kept
+    run one launch per job as in GpuEngine."""
 
-    def __init__(self, device: str = "cuda", caps=None, per_class: int = 32):
+    GROUPS = tuple((c, c) for c in range(10, 19))  # log2 capacity classes per batch: one power of two each
+
+    def __init__(self, device: str = "cuda", per_class: int = 32, groups=GROUPS):
         super().__init__(batched=False, device=device)
-        self.caps = list(caps) if caps is not None else [1 << c for c in range(10, 19) for _ in range(per_class)]
-        self.slots = self.native.Slots(self.caps, stream=self.stream, device=device)
-        self.slot_of: dict[int, int] = {}
-        self.free = set(range(len(self.caps)))
-        self.slots_busy = False
+        torch = self.torch
+        self.groups = []
+        for lo, hi in groups:
+            caps = [1 << c for c in range(lo, hi + 1) for _ in range(per_class)]
+            st = torch.cuda.Stream(device=device, priority=self.hi_prio)
+            self.groups.append({"caps": caps, "slots": self.native.Slots(caps, stream=st, device=device),
+                                "stream": st, "free": set(range(len(caps))), "busy": False})
+        self.slot_of: dict[int, tuple] = {}  # jid -> (group, slot)
+        self.max_cap = max(max(g["caps"]) for g in self.groups)
 
     def _slotted_kind(self, job: Job) -> bool:
-        return job.kind == "gauss" and job.dtype == "f32" and not job.keep and job.n <= max(self.caps)
+        return job.kind == "gauss" and job.dtype == "f32" and not job.keep and job.n <= self.max_cap
 
     def _try_attach(self, job: Job) -> bool:
-        fits = [s for s in self.free if self.caps[s] >= job.n]
-        if not fits:
-            return False
-        s = min(fits, key=lambda q: (self.caps[q], q))
-        self.free.discard(s)
-        self.slots.attach(s, self.samplers[job.jid], mean=self.means[job.jid])
-        self.slot_of[job.jid] = s
-        return True
+        for gi, g in enumerate(self.groups):
+            fits = [s for s in g["free"] if g["caps"][s] >= job.n]
+            if fits:
+                s = min(fits, key=lambda q: (g["caps"][q], q))
+                g["free"].discard(s)
+                g["slots"].attach(s, self.samplers[job.jid], mean=self.means[job.jid])
+                self.slot_of[job.jid] = (gi, s)
+                return True
+        return False
 
     def admit(self, job: Job) -> None:
         super().admit(job)
@@ -488,33 +498,43 @@ class SlotEngine(GpuEngine):
         for j in jobs:
             if j.jid not in self.slot_of and self._slotted_kind(j):
                 self._try_attach(j)
-        slotted = [j for j in jobs if j.jid in self.slot_of]
-        others = [j for j in jobs if j.jid not in self.slot_of and not self._slotted_kind(j)]
         launched = []
-        if slotted and not self.slots_busy:
-            counts = [0] * len(self.caps)
-            for j in slotted:
-                counts[self.slot_of[j.jid]] = int(iters[j.jid])
-            self.slots.step(counts)
+        for gi, g in enumerate(self.groups):
+            mine = [j for j in jobs if self.slot_of.get(j.jid, (-1,))[0] == gi]
+            if not mine or g["busy"]:
+                continue
+            counts = [0] * len(g["caps"])
+            for j in mine:
+                counts[self.slot_of[j.jid][1]] = int(iters[j.jid])
+            g["slots"].step(counts)
             ev = torch.cuda.Event()
-            ev.record(self.stream)
-            self.pending.append((ev, [j.jid for j in slotted], True))
-            self.slots_busy = True
-            launched += [j.jid for j in slotted]
+            ev.record(g["stream"])
+            self.pending.append((ev, [j.jid for j in mine], gi))
+            g["busy"] = True
+            launched += [j.jid for j in mine]
+        others = [j for j in jobs if j.jid not in self.slot_of and not self._slotted_kind(j)]
         if others:
             launched += super().step(others, iters)
         return launched
 
     def completed(self, block: bool = True) -> list[int]:
-        self.batch_busy = self.slots_busy
-        out = super().completed(block)
-        self.slots_busy = self.batch_busy
-        return out
+        if not self.pending:
+            return []
+        while True:
+            done = [p for p in self.pending if p[0].query()]
+            if done or not block:
+                break
+            time.sleep(20e-6)
+        self.pending = [p for p in self.pending if p not in done]
+        for _, _, tag in done:
+            if isinstance(tag, int) and not isinstance(tag, bool):
+                self.groups[tag]["busy"] = False
+        return [jid for _, ids, _ in done for jid in ids]
 
     def release(self, job: Job) -> None:
-        s = self.slot_of.pop(job.jid, None)
-        if s is not None:
-            self.slots.detach(s)
-            self.free.add(s)
+        where = self.slot_of.pop(job.jid, None)
+        if where is not None:
+            gi, s = where
+            self.groups[gi]["slots"].detach(s)
+            self.groups[gi]["free"].add(s)
         super().release(job)
-

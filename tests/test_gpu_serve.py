@@ -164,6 +164,6 @@ def test_slot_engine_results_equal_alone(nat, per_class):
     sch = Scheduler(eng, budget_bytes=need // 3, round_iters=3)
     done = sch.run(jobs)
     assert len(done) == len(jobs)
-    assert not eng.slot_of and len(eng.free) == len(eng.caps)
+    assert not eng.slot_of and all(len(g["free"]) == len(g["caps"]) for g in eng.groups)
     for j in done:
         assert np.array_equal(j.result, alone(nat, j)), (j.jid, j.kind)
