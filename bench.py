@@ -980,7 +980,7 @@ def run_serve(args):
             "config": {"workload": f"serve Poisson {args.rate:g} jobs/s x {args.jobs}: gauss (batched workload, "
                                    f"K=50) + {args.logistic_frac:.0%} logistic (N=2^18, M in {{1024,8192}}, D=32, "
                                    "K=100)", "budget_bytes": budget, "round_iters": 5,
-                       "engine": "standing batch of slots (9 capacity classes 2^10..2^18 x 16 slots)",
+                       "engine": "standing batches of slots (one per capacity class 2^10..2^18, 32 slots each)",
                        "parallelism": f"replicas x{ws}"},
             "p50_s": b["p50_s"], "p99_s": b["p99_s"],
             "serving": out,
