@@ -661,7 +661,10 @@ __device__ __forceinline__ void tile_sources_finish(const int32_t* __restrict__ 
   __syncwarp();  // out[] written, stage[] read: the next issue may overwrite it
 }
 
-template <int DPL, bool MOVE, bool REWEIGHT, typename FS, bool EST = false, bool GATHER = false>
+// FULL: the sampler's D equals DPL, so every coordinate loop, row test and
+// store width is known at compile time (the same arithmetic in the same
+// order as the general kernel: the results are bit for bit the same).
+template <int DPL, bool MOVE, bool REWEIGHT, typename FS, bool EST = false, bool GATHER = false, bool FULL = false>
 __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const FS gp, const int blk, const int nblk) {
   constexpr int DMAX = DPL;
   static_assert(!EST || DPL <= 16, "eq. (7) records: D <= 16");
@@ -710,7 +713,7 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       if (a.rs_alt && a.st->rs_dirty) rs_clr = a.st->rs_w ? a.rs : a.rs_alt;
     }
   }
-  const int d = a.d;
+  const int d = FULL ? DPL : a.d;
   constexpr int q = 0, c0 = 0;  // one lane per particle: it owns coordinates [0, d)
   const int nvalid = d;
   const bool vec = ((d & 3) == 0) && (nvalid >= DPL);
@@ -892,9 +895,9 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
 
 // One sampler per launch: the factor's entries are kernel parameters, read by
 // the FMAs straight from the constant bank.
-template <int DPL, bool MOVE, bool REWEIGHT, bool EST = false, bool GATHER = false>
+template <int DPL, bool MOVE, bool REWEIGHT, bool EST = false, bool GATHER = false, bool FULL = false>
 __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_lanes(ParticleArgs a, const GaussParamsF32 gp) {
-  move_reweight_body<DPL, MOVE, REWEIGHT, FactorParam, EST, GATHER>(a, FactorParam{gp}, blockIdx.x, gridDim.x);
+  move_reweight_body<DPL, MOVE, REWEIGHT, FactorParam, EST, GATHER, FULL>(a, FactorParam{gp}, blockIdx.x, gridDim.x);
 }
 
 // Batched: block b runs block map[b].y of map[b].z of sampler map[b].x; the
@@ -914,6 +917,8 @@ __global__ void __launch_bounds__(kPThreads, 2) k_move_reweight_batch(const Part
   stage_pairs(gps[m.x].P2, gps[m.x].mu, a.d, reinterpret_cast<float2*>(sfac), smu);
   __syncthreads();
   const FactorSmem fs{sfac, smu};
+  // (no D-exact instances here: with them this kernel needs more registers
+  // than it has and spills, and ran slower)
   if (a.d <= 8)
     move_reweight_body<8, true, true, FactorSmem, true>(a, fs, m.y, m.z);
   else if (a.d <= 16)
@@ -1141,23 +1146,37 @@ static cudaError_t launch_particles_d(int op, const ParticleArgs& a, int grid, i
   return launch_particles_t<T, 32>(op, a, grid, threads, s);
 }
 
+// The iteration's kernels (move + reweight, with the eq. (7) records, with the
+// gather) have a FULL instance for D equal to the width class.
 template <int DPL>
 static cudaError_t launch_lanes(int op, const ParticleArgs& a, int grid, int threads, cudaStream_t s,
                                 const GaussParamsF32& gp) {
+  const bool full = a.d == DPL;
   switch (op) {
     case OP_MOVE: k_move_reweight_lanes<DPL, true, false><<<grid, threads, 0, s>>>(a, gp); break;
     case OP_REWEIGHT: k_move_reweight_lanes<DPL, false, true><<<grid, threads, 0, s>>>(a, gp); break;
-    case OP_MOVE_REWEIGHT: k_move_reweight_lanes<DPL, true, true><<<grid, threads, 0, s>>>(a, gp); break;
+    case OP_MOVE_REWEIGHT:
+      if (full)
+        k_move_reweight_lanes<DPL, true, true, false, false, true><<<grid, threads, 0, s>>>(a, gp);
+      else
+        k_move_reweight_lanes<DPL, true, true><<<grid, threads, 0, s>>>(a, gp);
+      break;
     case OP_MOVE_REWEIGHT_EST:  // D <= 16 only (register room)
       if constexpr (DPL <= 16) {
-        k_move_reweight_lanes<DPL, true, true, true><<<grid, threads, 0, s>>>(a, gp);
+        if (full)
+          k_move_reweight_lanes<DPL, true, true, true, false, true><<<grid, threads, 0, s>>>(a, gp);
+        else
+          k_move_reweight_lanes<DPL, true, true, true><<<grid, threads, 0, s>>>(a, gp);
         break;
       } else {
         return cudaErrorInvalidValue;
       }
     case OP_MOVE_REWEIGHT_GATHER:  // (the same, and gathers a pending resampling's rows)
       if constexpr (DPL <= 16) {
-        k_move_reweight_lanes<DPL, true, true, true, true><<<grid, threads, 0, s>>>(a, gp);
+        if (full)
+          k_move_reweight_lanes<DPL, true, true, true, true, true><<<grid, threads, 0, s>>>(a, gp);
+        else
+          k_move_reweight_lanes<DPL, true, true, true, true><<<grid, threads, 0, s>>>(a, gp);
         break;
       } else {
         return cudaErrorInvalidValue;
