@@ -121,9 +121,12 @@ def measured_traffic():
         if len(cells) != 7 or cells[0] not in STAGE_SOURCES:
             continue
         h = hashlib.sha256()
-        for f in STAGE_SOURCES[cells[0]]:
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+        try:
+            for f in STAGE_SOURCES[cells[0]]:
+                with open(os.path.join(csrc, f), "rb") as fh:
+                    h.update(fh.read())
+        except OSError:
+            continue
         if h.hexdigest()[:16] == cells[2]:
             out[cells[0]] = float(cells[6])
     return out

@@ -83,6 +83,12 @@ typedef enum { SMC_RESAMPLE_ESS = 0, SMC_RESAMPLE_ALWAYS = 1, SMC_RESAMPLE_NEVER
  * without the flag.  Honoured by FP32 Gaussian samplers with D <= 16 and
  * N > 4096 (whose move kernel forms the eq. (7) sums); ignored otherwise. */
 #define SMC_FLAG_DEFER_REDISTRIBUTE 4
+/* Test hook for the failure path of the fused small-sampler iterations (see
+ * smc_step): their grid barrier waits for one block more than the launch
+ * has, so every wait runs out (after about half a second), the kernel
+ * returns, and the next smc_sync reports SMC_ETIMEOUT.  The GPU context stays
+ * usable. */
+#define SMC_FLAG_TEST_STALL_BARRIER 8
 
 typedef struct {
   int64_t n;              /* N particles */
@@ -166,7 +172,11 @@ int smc_redistribute(smc_sampler* h, const int32_t* ncopies_dev);
 /* K iterations of Algorithm 2 (lines 3-10): move, reweight, normalise,
  * estimate, N_eff, and resample + redistribute + reset when N_eff < N*,
  * with no host synchronisation between iterations (the decision stays on the
- * device; the launches of an iteration are replayed from a CUDA graph).
+ * device; the launches of an iteration are replayed from a CUDA graph).  An
+ * FP64 sampler with N <= 2048 (Gaussian or Student-t target) runs the K
+ * iterations in one cooperative launch instead, with the same per-stage
+ * arithmetic (bit-identical results); if its grid cannot be resident it uses
+ * the graph. 
  * mean_dev[D] receives f_K, cov_dev[D*D] (may be NULL) the final weighted
  * covariance, trace_dev (may be NULL) K smc_iter_stats records, and
  * fhat_dev[D] (may be NULL) the recycled estimate of eq. (6) over all

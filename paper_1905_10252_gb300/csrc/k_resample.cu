@@ -21,6 +21,7 @@
 //    (Sec. 4) with O(1) passes over the data.
 #include <cmath>
 
+#include "particle_bodies.cuh"
 #include "smc_internal.cuh"
 #include "smc_kernels.h"
 
@@ -537,15 +538,23 @@ __device__ __forceinline__ void tile_starts_flush(int32_t* __restrict__ tile_src
 }
 
 // ---------------------------------------------------------------- quantise: scan + ncopies
-__device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int blk) {
-  const DevState* st = a.st;
-  if (st->err || !(a.force || st->flag)) return;
-  __shared__ union {
+// Shared memory of the scan: the block's W staged for a blocked layout (then
+// its copy counts), the block scan's scratch and the long-run queue.
+struct ScanSmem {
+  union {
     uint64_t w[kQThreads * 17];
     uint32_t o[kQThreads * 17];
   } buf;
-  __shared__ uint64_t scratch[33];
-  __shared__ BigRuns big;
+  uint64_t scratch[33];
+  BigRuns big;
+};
+
+__device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int blk, ScanSmem& sm) {
+  const DevState* st = a.st;
+  if (st->err || !(a.force || st->flag)) return;
+  auto& buf = sm.buf;
+  uint64_t* const scratch = sm.scratch;
+  BigRuns& big = sm.big;
   if (threadIdx.x == 0) big.count = 0;
   const int64_t n = a.n;
   const int64_t base = int64_t(blk) * kQTile;
@@ -626,7 +635,10 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
   }
 }
 
-__global__ void __launch_bounds__(kQThreads, 3) k_quant_scan(QuantArgs a) { quant_scan_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(kQThreads, 3) k_quant_scan(QuantArgs a) {
+  __shared__ ScanSmem sm;
+  quant_scan_body(a, blockIdx.x, sm);
+}
 
 // ---------------------------------------------------------------- standalone ncopies scan
 // Thread t of a block owns the 16 consecutive entries [base + 16 t, +16) of
@@ -954,7 +966,8 @@ __global__ void __launch_bounds__(kQThreads) k_quant_small(QuantArgs a) {
   __syncthreads();  // the block's sums, W and estimate partials are written
   quant_finalize_body(a, 0);
   __syncthreads();  // S, U, the decision and the block base are written
-  quant_scan_body(a, 0);
+  __shared__ ScanSmem ssm;
+  quant_scan_body(a, 0, ssm);
 }
 
 template <typename V, int CPR>
@@ -963,6 +976,130 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute_commit(RedistArgs a,
   redistribute_body<V, CPR>(a, 0, sm);
   __syncthreads();
   if (threadIdx.x < 32) commit_warp(a.st, d, force_flip, recycle);
+}
+
+// ---------------------------------------------------------------- fused small-sampler iterations
+// FP64 samplers of one quantise block and one copy tile (N <= 2048): k
+// iterations of Algorithm 2 in one cooperative launch.  Every block runs its
+// share of the move + reweight with the particle-to-thread map of the
+// separate move launch (move_threads per block own particles); then block 0
+// alone runs, in the order of the separate launches, t += 1, the maximum, the
+// quantise reduce / finalise / scan, the copy and the commit -- the bodies of
+// k_max_finalize, k_quant_small and k_redistribute_commit -- so the results
+// are bit for bit those of the separate launches.  At this size an iteration
+// is a chain of dependent FP64 operations (tens to thousands of cycles each
+// on this GPU) and kernel boundaries; two grid barriers per iteration replace
+// the five boundaries.
+//
+// The grid barrier (every block is resident: cooperative launch): the last
+// block to arrive resets the count and advances the generation; the others
+// wait for the generation to change -- for at most half a second of the
+// global timer (and at most 2^24 polls), after which they record
+// SMC_ETIMEOUT and the kernel returns.  extra: arrivals expected beyond the
+// grid (0; 1 only in the stall test, where every wait runs out).
+constexpr unsigned long long kBarrierNs = 500000000ull;
+constexpr long long kBarrierPolls = 1ll << 24;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+}
+
+__device__ __forceinline__ bool grid_barrier(uint32_t* bar, DevState* st, unsigned extra) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = ld_acquire_u32(bar + 1);
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x + extra - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      for (long long polls = 0; ld_acquire_u32(bar + 1) == g; ++polls) {
+        if (polls > kBarrierPolls || global_ns() - t0 > kBarrierNs) {
+          record_error(st, SMC_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The stages' shared memory overlaps (each phase writes what it reads before
+// reading it, and phases are separated by block barriers).
+union SmallIterSmem {
+  TargetSmem<double> ts;
+  QuantReduceSmem q;
+  ScanSmem sc;
+  RedistSmem r;
+};
+
+template <int DMAX, typename V>
+__global__ void __launch_bounds__(kQThreads) k_iterate_small(SmallIterArgs s) {
+  __shared__ SmallIterSmem sm;
+  TargetSmem<double>& ts = sm.ts;
+  QuantReduceSmem& qsm = sm.q;
+  RedistSmem& rsm = sm.r;
+  DevState* st = s.a.st;
+  for (int it = 0; it < s.k; ++it) {
+    move_reweight_generic_body<double, DMAX, true, true>(s.a, ts, blockIdx.x, gridDim.x, s.move_threads, 1);
+    if (!grid_barrier(s.bar, st, s.stall ? 1u : 0u)) return;
+    if (blockIdx.x == 0) {
+      if (threadIdx.x == 0) st->t += 1;
+      __syncthreads();
+      max_finalize_body(s.a.part, gridDim.x, st);
+      __syncthreads();
+      quant_reduce_body<double, DMAX, true>(s.q, 0, qsm);
+      __syncthreads();
+      quant_finalize_body(s.q, 0);
+      __syncthreads();
+      quant_scan_body(s.q, 0, sm.sc);
+      if (!(s.stop_last && it + 1 == s.k)) {
+        __syncthreads();
+        redistribute_body<V, 0>(s.r, 0, rsm);
+        __syncthreads();
+        if (threadIdx.x < 32) commit_warp(st, s.d, 0, 1);
+      }
+    }
+    if (it + 1 < s.k && !grid_barrier(s.bar, st, s.stall ? 1u : 0u)) return;
+  }
+}
+
+bool small_iter_fits(int64_t n, int dtype) { return dtype == SMC_F64 && n <= kRTile && n <= kQTile; }
+
+template <int DMAX>
+static cudaError_t iterate_small_d(const SmallIterArgs& s, int blocks, cudaStream_t st) {
+  SmallIterArgs a = s;
+  void* args[] = {&a};
+  const void* fn = (s.r.row_bytes % 16 == 0) ? reinterpret_cast<const void*>(&k_iterate_small<DMAX, uint4>)
+                                             : reinterpret_cast<const void*>(&k_iterate_small<DMAX, uint2>);
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kQThreads), args, 0, st);
+}
+
+cudaError_t launch_iterate_small(const SmallIterArgs& s, int move_blocks, cudaStream_t st) {
+  if (!small_iter_fits(s.a.n, s.a.dtype) || s.k < 1 || move_blocks < 1 || s.move_threads < 1 ||
+      s.move_threads > kQThreads || s.d < 1 || s.d > kMaxD || s.r.row_bytes % 8 != 0)
+    return cudaErrorInvalidValue;
+  if (s.d <= 4) return iterate_small_d<4>(s, move_blocks, st);
+  if (s.d <= 8) return iterate_small_d<8>(s, move_blocks, st);
+  if (s.d <= 16) return iterate_small_d<16>(s, move_blocks, st);
+  return iterate_small_d<32>(s, move_blocks, st);
 }
 
 // ---------------------------------------------------------------- batched launches
@@ -1003,7 +1140,8 @@ __global__ void __launch_bounds__(kQThreads) k_quant_scan_batch(const QuantArgs*
   if (left && left[m.x] <= 0) return;
   const QuantArgs a = qa[m.x];
   if (m.y >= a.nblocks) return;
-  quant_scan_body(a, m.y);
+  __shared__ ScanSmem sm;
+  quant_scan_body(a, m.y, sm);
 }
 
 template <int KU>

@@ -65,6 +65,9 @@ Layout layout_for(int64_t n, int d, int m = 0, bool two_rs = false) {
   p = align_up(p + size_t(n) * sizeof(uint64_t));
   L.tile_src = p;
   p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
+  // the grid barrier of the fused small-sampler iterations (two words)
+  L.gbar = p;
+  p = align_up(p + 2 * sizeof(uint32_t));
   // logistic data: X, y and the BF16 tile images
   const size_t m_pad = size_t(m + kLgRows - 1) / kLgRows * kLgRows;
   L.lg_x = p;
@@ -309,6 +312,31 @@ cudaError_t launch_iteration(smc_sampler* h, bool with_cov) {
   return e;
 }
 
+// k iterations of a small FP64 sampler in one cooperative launch: the bodies
+// of launch_iteration's kernels in its order (bit-identical results); with
+// the covariance, the last iteration's copy and commit follow the covariance
+// as separate launches, as in launch_iteration.  Returns
+// cudaErrorCooperativeLaunchTooLarge (nothing launched but the barrier reset)
+// when the grid cannot be resident.
+cudaError_t launch_small_iterations(smc_sampler* h, int32_t k, bool with_cov) {
+  SmallIterArgs s{};
+  s.a = particle_args(h);
+  s.q = quant_args(h, 0, nullptr);
+  s.r = redist_args(h, 0);
+  s.bar = reinterpret_cast<uint32_t*>(h->ws + h->L.gbar);
+  s.k = k;
+  s.move_threads = h->threads_p;
+  s.d = h->d;
+  s.stop_last = with_cov ? 1 : 0;
+  s.stall = (h->cfg.flags & SMC_FLAG_TEST_STALL_BARRIER) ? 1 : 0;
+  cudaError_t e = cudaMemsetAsync(s.bar, 0, 2 * sizeof(uint32_t), h->stream);
+  if (e == cudaSuccess) e = launch_iterate_small(s, h->grid_p, h->stream);
+  if (e == cudaSuccess && with_cov)
+    e = launch_cov(s.a, nullptr, reinterpret_cast<double*>(h->ws + h->L.covpart), h->L.cov_blocks, h->stream);
+  if (e == cudaSuccess && with_cov) e = launch_redistribute_commit(redist_args(h, 0), h->d, 0, 1, h->stream);
+  return e;
+}
+
 cudaError_t build_graph(smc_sampler* h, bool with_cov, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
@@ -450,6 +478,10 @@ int smc_init(smc_sampler** out, const smc_config* cfg, void* x_dev, void* x_alt_
   // deferred redistribution: the gathering move is the records kernel's, and
   // the quantise and copy passes span several blocks
   h->defer = (cfg->flags & SMC_FLAG_DEFER_REDISTRIBUTE) && est_in_move(h) && h->L.qblocks > 1 && h->L.ntiles > 1;
+  // small FP64 samplers (generic move kernel, one quantise block, one copy
+  // tile): smc_step fuses their iterations into one cooperative launch
+  h->small_iter = small_iter_fits(h->n, h->dtype) && cfg->target != SMC_LOGISTIC && !h->defer &&
+                  h->L.qblocks == 1 && h->L.ntiles == 1;
   if (e != cudaSuccess) {
     int r = cuda_fail(nullptr, e, "smc_init launch");
     delete h;
@@ -538,6 +570,14 @@ int smc_step(smc_sampler* h, int32_t k, double* mean_dev, double* cov_dev, smc_i
   if (k == 0) return SMC_OK;
   SMC_TRY(h, fetch_gp(h));  // (before any stream capture)
   SMC_TRY(h, launch_step_setup(h->st, trace_dev, mean_dev, fhat_dev, cov_dev, h->stream));
+  if (h->small_iter) {
+    const cudaError_t e = launch_small_iterations(h, k, cov_dev != nullptr);
+    if (e != cudaErrorCooperativeLaunchTooLarge) {
+      SMC_TRY(h, e);
+      return SMC_OK;
+    }
+    (void)cudaGetLastError();  // the grid cannot be resident here: separate launches below
+  }
   const bool use_graph = h->stream != nullptr;
   for (int32_t it = 0; it < k; ++it) {
     const bool with_cov = cov_dev && it == k - 1;

@@ -11,7 +11,7 @@ namespace smc {
 
 // Byte offsets of the stateful sampler's workspace.
 struct Layout {
-  size_t st, tg, part, epart, qpart, cbase, xpart, rs, rs_alt, wbuf, tile_src, lg_x, lg_y, lg_img, covpart, total;
+  size_t st, tg, part, epart, qpart, cbase, xpart, rs, rs_alt, wbuf, tile_src, gbar, lg_x, lg_y, lg_img, covpart, total;
   int qblocks, ntiles, cov_blocks;
 };
 
@@ -54,6 +54,9 @@ struct smc_sampler {
   bool gp_ready;
   // SMC_FLAG_DEFER_REDISTRIBUTE honoured: resampled rows are gathered by the next move
   bool defer;
+  // FP64 sampler of one quantise block and one copy tile: smc_step runs its
+  // iterations in one cooperative launch (k_iterate_small)
+  bool small_iter;
   // CUDA graph of one iteration (with and without the covariance stage)
   cudaGraphExec_t g_iter[2];
   std::string err;

@@ -248,6 +248,26 @@ cudaError_t launch_redistribute(const RedistArgs& a, cudaStream_t s);
 // redistribute + commit (N <= 2048), each as one launch
 cudaError_t launch_quant_small(const QuantArgs& a, cudaStream_t s);
 cudaError_t launch_redistribute_commit(const RedistArgs& a, int d, int force_flip, int recycle, cudaStream_t s);
+
+// k iterations of an FP64 sampler of one quantise block and one copy tile
+// (N <= 2048) in one cooperative launch of move_blocks blocks (see
+// k_iterate_small).  bar: two zeroed words (the grid barrier).  stop_last: the
+// last iteration ends after its scan (its copy and commit follow as separate
+// launches, after the covariance).
+struct SmallIterArgs {
+  ParticleArgs a;
+  QuantArgs q;
+  RedistArgs r;
+  uint32_t* bar;
+  int32_t k;
+  int32_t move_threads;  // threads per block that own particles (the separate move launch's block size)
+  int32_t d;
+  int32_t stop_last;
+  int32_t stall;  // test hook (SMC_FLAG_TEST_STALL_BARRIER): the barrier waits for one block more than the grid
+  int32_t pad;
+};
+bool small_iter_fits(int64_t n, int dtype);
+cudaError_t launch_iterate_small(const SmallIterArgs& s, int move_blocks, cudaStream_t st);
 int nearly_sort_tiles(int64_t n);
 cudaError_t launch_nearly_sort(const NearlySortArgs& a, cudaStream_t s);
 cudaError_t launch_state_init(DevState* st, int64_t n, int64_t t, int F, cudaStream_t s);

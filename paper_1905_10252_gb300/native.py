@@ -21,6 +21,7 @@ RESAMPLE_ESS, RESAMPLE_ALWAYS, RESAMPLE_NEVER = 0, 1, 2
 FLAG_LOGISTIC_CUDA_CORES = 1  # SMC_FLAG_LOGISTIC_CUDA_CORES
 FLAG_TEST_STALL_LIKELIHOOD = 2  # SMC_FLAG_TEST_STALL_LIKELIHOOD
 FLAG_DEFER_REDISTRIBUTE = 4  # SMC_FLAG_DEFER_REDISTRIBUTE
+FLAG_TEST_STALL_BARRIER = 8  # SMC_FLAG_TEST_STALL_BARRIER
 
 EXPORTED = [
     "smc_workspace_bytes", "smc_init", "smc_move", "smc_reweight", "smc_estimate", "smc_resample",
