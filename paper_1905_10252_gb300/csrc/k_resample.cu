@@ -79,8 +79,6 @@ __device__ __forceinline__ void load_table(uint64_t* T) {
   __syncthreads();
 }
 
-// padded shared-memory index: 16 items per thread, stride 17 (bank spread)
-__device__ __forceinline__ int pad_idx(int idx) { return (idx >> 4) * 17 + (idx & 15); }
 
 // ---------------------------------------------------------------- state init
 // reset value of Algorithm 4 line 3, -log N, from the exact log so that both
@@ -169,6 +167,24 @@ __device__ __forceinline__ float u64_to_float_trunc(uint64_t v) {
 __device__ __forceinline__ void weight_of(uint64_t E, float* w) { *w = u64_to_float_trunc(E); }
 __device__ __forceinline__ void weight_of(uint64_t E, double* w) { *w = __ull2double_rn(E); }
 
+// Loads of rows the kernel only reads (read-only path), or, in a kernel whose
+// other blocks wrote them before a grid barrier, at the coherent level (L2).
+template <bool COH, typename V>
+__device__ __forceinline__ V ld_rows(const V* p) {
+  if constexpr (COH)
+    return __ldcg(p);
+  else
+    return __ldg(p);
+}
+
+template <bool COH, typename V>
+__device__ __forceinline__ V ld_plain(const V* p) {
+  if constexpr (COH)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
 // Shared memory of one quantise-reduce block (declared by the calling kernel).
 struct QuantReduceSmem {
   uint64_t T[128];
@@ -176,7 +192,7 @@ struct QuantReduceSmem {
   double shx[kQThreads / 32][32];
 };
 
-template <typename ST, int DMAX, bool EST>
+template <typename ST, int DMAX, bool EST, bool COH = false>
 __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int blk, QuantReduceSmem& sm) {
   uint64_t* const T = sm.T;
   uint64_t (*const sh)[5] = sm.sh;
@@ -223,12 +239,49 @@ __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int 
         done = true;
       }
     }
+    if constexpr (COH && EST && DMAX <= 8) {
+      // (the fused small-sampler iteration, rows written by other blocks of
+      // the same launch: coherent loads, latency-bound) each group of four
+      // items' log w and rows loaded first, then the arithmetic in the
+      // same order as below
+      if (!done && !use_rec) {
+        for (int k0 = 0; k0 < kQItems; k0 += 4) {
+          double lv[4];
+          ST xr[4][DMAX];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t i = base + (k0 + u) * kQThreads + threadIdx.x;
+            lv[u] = i < a.n ? __ldcg(a.logw + i) : 0.0;
+#pragma unroll
+            for (int c = 0; c < DMAX; ++c) xr[u][c] = (i < a.n && c < d) ? __ldcg(x + i * d + c) : ST(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t i = base + (k0 + u) * kQThreads + threadIdx.x;
+            if (i < a.n) {
+              const uint64_t E = expfx_a(__dsub_rn(m, lv[u]), T);
+              const uint64_t W = E >> sh_w;
+              a.wbuf[i] = W;
+              sw += W;
+              sw2 += u128(W) * W;
+              se += E;
+              ST w;
+              weight_of(E, &w);
+#pragma unroll
+              for (int c = 0; c < DMAX; ++c)
+                if (c < d) acc[c] = fma(w, xr[u][c], acc[c]);
+            }
+          }
+        }
+        done = true;
+      }
+    }
     if (!done)
 #pragma unroll 4
     for (int k = 0; k < kQItems; ++k) {
       const int64_t i = base + k * kQThreads + threadIdx.x;
       if (i < a.n) {
-        const uint64_t E = expfx_a(__dsub_rn(m, a.logw[i]), T);
+        const uint64_t E = expfx_a(__dsub_rn(m, ld_plain<COH>(a.logw + i)), T);
         const uint64_t W = E >> sh_w;
         a.wbuf[i] = W;
         sw += W;
@@ -241,7 +294,7 @@ __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int 
           if (d == DMAX && (DMAX * sizeof(ST)) % 16 == 0) {
 #pragma unroll
             for (int v = 0; v < int(DMAX * sizeof(ST) / 16); ++v) {
-              const float4 f = __ldg(reinterpret_cast<const float4*>(row) + v);
+              const float4 f = ld_rows<COH>(reinterpret_cast<const float4*>(row) + v);
               const ST* fv = reinterpret_cast<const ST*>(&f);
 #pragma unroll
               for (int u = 0; u < int(16 / sizeof(ST)); ++u) {
@@ -252,7 +305,7 @@ __device__ __forceinline__ void quant_reduce_body(const QuantArgs& a, const int 
           } else {
 #pragma unroll
             for (int c = 0; c < DMAX; ++c)
-              if (c < d) acc[c] = fma(w, row[c], acc[c]);
+              if (c < d) acc[c] = fma(w, ld_plain<COH>(row + c), acc[c]);
           }
         }
       }
@@ -430,7 +483,11 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
       if (st->mean_out) st->mean_out[threadIdx.x] = mc;
     }
   }
-  if (threadIdx.x != 0) return;
+  // the totals, then three independent chains on three lanes of warp 0 (the
+  // same operations as one thread would do: the 128-bit division for the
+  // copy counts, the logarithm of LSE, the division of N_eff), each a long
+  // latency chain on this GPU
+  if (threadIdx.x >= 32) return;
   uint64_t S = 0;
   u128 sw2 = 0, se = 0;
   for (int w = 0; w < nw; ++w) {
@@ -439,6 +496,23 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
     se += (u128(sheh[w]) << 64) | shel[w];
   }
   const uint64_t n = uint64_t(a.n);
+  const int lane0 = threadIdx.x;
+  uint64_t R = 0;
+  double lse = 0.0, se_d = 0.0, ess = 0.0;
+  if (lane0 == 0) {
+    // S >= 2^F = 2^(63 - ceil(log2 N)), so floor(N 2^64 / S) <= 2^(2 ceil(log2 N) + 1) fits 64 bits
+    R = S ? uint64_t((u128(n) << 64) / S) : 0;
+  } else if (lane0 == 1) {
+    se_d = u128_to_double(se);
+    lse = st->m + log(se_d * 0x1p-62);
+  } else if (lane0 == 2) {
+    const double Sd = double(S);
+    ess = (S && sw2) ? Sd * Sd / u128_to_double(sw2) : 0.0;
+  }
+  lse = __shfl_sync(0xffffffffu, lse, 1);
+  se_d = __shfl_sync(0xffffffffu, se_d, 1);
+  ess = __shfl_sync(0xffffffffu, ess, 2);
+  if (lane0 != 0) return;
   int flag = 0;
   if (!st->err && S > 0) {
     if (a.mode == SMC_RESAMPLE_ALWAYS)
@@ -454,14 +528,8 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
   const uint64_t r64 = (uint64_t(r.v[0]) << 32) | r.v[1];
   const uint64_t U = S ? __umul64hi(r64, S) : 0;
   const int L = S ? 64 - __clzll((long long)S) : 1;
-  // S >= 2^F = 2^(63 - ceil(log2 N)), so floor(N 2^64 / S) <= 2^(2 ceil(log2 N) + 1) fits 64 bits
-  const uint64_t R = S ? uint64_t((u128(n) << 64) / S) : 0;
   const double m = st->m;
-  const double se_d = u128_to_double(se);
-  const double lse = m + log(se_d * 0x1p-62);
   st->est_s = se_d * 0x1p-62;
-  const double Sd = double(S);
-  const double ess = (S && sw2) ? Sd * Sd / u128_to_double(sw2) : 0.0;
   st->S = S;
   st->U = U;
   st->L = L;
@@ -549,7 +617,13 @@ struct ScanSmem {
   BigRuns big;
 };
 
+// ITEMS consecutive items per thread (a block covers kQThreads ITEMS items):
+// kQItems for the quantise blocks of kQTile; fewer for a sampler whose N fits
+// one block of kQThreads ITEMS items (shorter per-thread chains, the same
+// exact integers).
+template <int ITEMS = kQItems>
 __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int blk, ScanSmem& sm) {
+  static_assert(ITEMS >= 1 && ITEMS <= kQItems, "items per thread");
   const DevState* st = a.st;
   if (st->err || !(a.force || st->flag)) return;
   auto& buf = sm.buf;
@@ -560,36 +634,36 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
   const int64_t base = int64_t(blk) * kQTile;
   // the quantised weights of the reduce pass, staged for a blocked layout
 #pragma unroll 4
-  for (int k = 0; k < kQItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     const int idx = k * kQThreads + threadIdx.x;
     const int64_t i = base + idx;
-    buf.w[pad_idx(idx)] = i < n ? a.wbuf[i] : 0ull;
+    buf.w[(idx / ITEMS) * (ITEMS + 1) + idx % ITEMS] = i < n ? a.wbuf[i] : 0ull;
   }
   __syncthreads();
   const uint64_t S = st->S, U = st->U;
-  uint64_t W[kQItems];
+  uint64_t W[ITEMS];
   uint64_t tsum = 0;
 #pragma unroll
-  for (int q = 0; q < kQItems; ++q) {
-    W[q] = buf.w[threadIdx.x * 17 + q];
+  for (int q = 0; q < ITEMS; ++q) {
+    W[q] = buf.w[threadIdx.x * (ITEMS + 1) + q];
     tsum += W[q];
   }
   uint64_t btot;
   uint64_t C = a.cbase[blk] + block_excl_scan_u64(tsum, scratch, &btot);
-  uint32_t ncv[kQItems];
+  uint32_t ncv[ITEMS];
   unsigned nsurv = 0;
   // off_i = floor((N C_{i-1} + U) / S) for every item independently (no
   // serial dependency between items): the estimate mulhi(C, floor(N 2^64/S))
   // is at most 2 below floor(N C / S), and floor((N C + U)/S) is at most 1
   // above that; exact 128-bit comparisons fix the result.
   const uint64_t Rn = st->recip;  // floor(N 2^64 / S)
-  uint64_t Cx[kQItems + 1];
+  uint64_t Cx[ITEMS + 1];
   Cx[0] = C;
 #pragma unroll
-  for (int q = 0; q < kQItems; ++q) Cx[q + 1] = Cx[q] + W[q];
-  uint64_t offs[kQItems + 1];
+  for (int q = 0; q < ITEMS; ++q) Cx[q + 1] = Cx[q] + W[q];
+  uint64_t offs[ITEMS + 1];
 #pragma unroll
-  for (int q = 0; q <= kQItems; ++q) {
+  for (int q = 0; q <= ITEMS; ++q) {
     const u128 X = u128(n) * Cx[q] + U;
     uint64_t qq = __umul64hi(Cx[q], Rn);
     u128 nxt = u128(qq + 1) * S;
@@ -601,9 +675,9 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
       }
     offs[q] = qq;
   }
-  const int64_t i0 = base + int64_t(threadIdx.x) * kQItems;
+  const int64_t i0 = base + int64_t(threadIdx.x) * ITEMS;
 #pragma unroll
-  for (int q = 0; q < kQItems; ++q) {
+  for (int q = 0; q < ITEMS; ++q) {
     const uint64_t lo = offs[q], hi = offs[q + 1];
     ncv[q] = uint32_t(hi - lo);
     const int64_t i = i0 + q;
@@ -624,13 +698,13 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
   __syncthreads();  // buf.w no longer read
   if (a.ncopies) {
 #pragma unroll
-    for (int q = 0; q < kQItems; ++q) buf.o[threadIdx.x * 17 + q] = ncv[q];
+    for (int q = 0; q < ITEMS; ++q) buf.o[threadIdx.x * (ITEMS + 1) + q] = ncv[q];
     __syncthreads();
 #pragma unroll 4
-    for (int k = 0; k < kQItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const int idx = k * kQThreads + threadIdx.x;
       const int64_t i = base + idx;
-      if (i < n) a.ncopies[i] = int32_t(buf.o[pad_idx(idx)]);
+      if (i < n) a.ncopies[i] = int32_t(buf.o[(idx / ITEMS) * (ITEMS + 1) + idx % ITEMS]);
     }
   }
 }
@@ -841,7 +915,7 @@ struct RedistSmem {
   int32_t wsc[kRThreads / 32];
 };
 
-template <typename V, int CPR, int KU = 8>
+template <typename V, int CPR, int KU = 8, bool COH = false>
 __device__ __forceinline__ void redistribute_body(const RedistArgs& a, const int blk, RedistSmem& sm) {
   int cur = 0;
   if (a.stateful) {
@@ -922,7 +996,7 @@ __device__ __forceinline__ void redistribute_body(const RedistArgs& a, const int
       const int e = e0 + u * kRThreads;
       if (e < total) {
         const int k = e / cpr, c = e - k * cpr;
-        v[u] = __ldg(in + int64_t(mark[k]) * cpr + c);
+        v[u] = ld_rows<COH>(in + int64_t(mark[k]) * cpr + c);
       }
     }
 #pragma unroll
@@ -934,11 +1008,11 @@ __device__ __forceinline__ void redistribute_body(const RedistArgs& a, const int
   if (a.lp_bytes == 4) {
     const uint32_t* __restrict__ li = static_cast<const uint32_t*>(cur ? a.lp_in[1] : a.lp_in[0]);
     uint32_t* __restrict__ lo = static_cast<uint32_t*>(cur ? a.lp_out[1] : a.lp_out[0]) + k0;
-    for (int k = threadIdx.x; k < len; k += kRThreads) lo[k] = li[mark[k]];
+    for (int k = threadIdx.x; k < len; k += kRThreads) lo[k] = ld_plain<COH>(li + mark[k]);
   } else if (a.lp_bytes == 8) {
     const uint64_t* __restrict__ li = static_cast<const uint64_t*>(cur ? a.lp_in[1] : a.lp_in[0]);
     uint64_t* __restrict__ lo = static_cast<uint64_t*>(cur ? a.lp_out[1] : a.lp_out[0]) + k0;
-    for (int k = threadIdx.x; k < len; k += kRThreads) lo[k] = li[mark[k]];
+    for (int k = threadIdx.x; k < len; k += kRThreads) lo[k] = ld_plain<COH>(li + mark[k]);
   }
   if (a.logw) {
     const double reset = a.stateful ? a.st->reset_logw : a.reset_logw;
@@ -991,19 +1065,25 @@ __global__ void __launch_bounds__(kRThreads) k_redistribute_commit(RedistArgs a,
 // on this GPU) and kernel boundaries; two grid barriers per iteration replace
 // the five boundaries.
 //
-// The grid barrier (every block is resident: cooperative launch): the last
-// block to arrive resets the count and advances the generation; the others
-// wait for the generation to change -- for at most half a second of the
-// global timer (and at most 2^24 polls), after which they record
-// SMC_ETIMEOUT and the kernel returns.  extra: arrivals expected beyond the
-// grid (0; 1 only in the stall test, where every wait runs out).
+// The grid barrier (every block is resident: cooperative launch): one 64-bit
+// count of arrivals, zeroed before the launch; a block's b-th barrier of the
+// launch (b = 1, 2, ...) completes when the count reaches b (grid + extra).
+// A block adds its arrival (release) and polls the count (acquire) -- for at
+// most half a second of the global timer (and at most 2^24 polls), after
+// which it records SMC_ETIMEOUT and the kernel returns.  extra: arrivals
+// expected beyond the grid (0; 1 only in the stall test, where every wait
+// runs out).
 constexpr unsigned long long kBarrierNs = 500000000ull;
 constexpr long long kBarrierPolls = 1ll << 24;
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -1012,27 +1092,23 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(uint32_t* bar, DevState* st, unsigned extra) {
+__device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned long long& nbar, DevState* st,
+                                             unsigned extra) {
   __shared__ int s_ok;
+  ++nbar;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = ld_acquire_u32(bar + 1);
-    __threadfence();
+    const unsigned long long target = nbar * (gridDim.x + extra);
+    red_release_add_u64(bar, 1ull);
     int ok = 1;
-    if (atomicAdd(bar, 1u) == gridDim.x + extra - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      for (long long polls = 0; ld_acquire_u32(bar + 1) == g; ++polls) {
-        if (polls > kBarrierPolls || global_ns() - t0 > kBarrierNs) {
-          record_error(st, SMC_ETIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(128);
+    const unsigned long long t0 = global_ns();
+    for (long long polls = 0; ld_acquire_u64(bar) < target; ++polls) {
+      if (polls > kBarrierPolls || global_ns() - t0 > kBarrierNs) {
+        record_error(st, SMC_ETIMEOUT);
+        ok = 0;
+        break;
       }
+      __nanosleep(64);
     }
     __threadfence();
     s_ok = ok;
@@ -1057,27 +1133,33 @@ __global__ void __launch_bounds__(kQThreads) k_iterate_small(SmallIterArgs s) {
   QuantReduceSmem& qsm = sm.q;
   RedistSmem& rsm = sm.r;
   DevState* st = s.a.st;
+  unsigned long long* const bar = s.bar;
+  unsigned long long nbar = 0;
+  const unsigned extra = s.stall ? 1u : 0u;
   for (int it = 0; it < s.k; ++it) {
     move_reweight_generic_body<double, DMAX, true, true>(s.a, ts, blockIdx.x, gridDim.x, s.move_threads, 1);
-    if (!grid_barrier(s.bar, st, s.stall ? 1u : 0u)) return;
+    if (!grid_barrier(bar, nbar, st, extra)) return;
     if (blockIdx.x == 0) {
       if (threadIdx.x == 0) st->t += 1;
       __syncthreads();
       max_finalize_body(s.a.part, gridDim.x, st);
       __syncthreads();
-      quant_reduce_body<double, DMAX, true>(s.q, 0, qsm);
+      quant_reduce_body<double, DMAX, true, true>(s.q, 0, qsm);
       __syncthreads();
       quant_finalize_body(s.q, 0);
       __syncthreads();
-      quant_scan_body(s.q, 0, sm.sc);
+      if (s.a.n <= kQThreads * 4)
+        quant_scan_body<4>(s.q, 0, sm.sc);
+      else
+        quant_scan_body<8>(s.q, 0, sm.sc);
       if (!(s.stop_last && it + 1 == s.k)) {
         __syncthreads();
-        redistribute_body<V, 0>(s.r, 0, rsm);
+        redistribute_body<V, 0, 8, true>(s.r, 0, rsm);
         __syncthreads();
         if (threadIdx.x < 32) commit_warp(st, s.d, 0, 1);
       }
     }
-    if (it + 1 < s.k && !grid_barrier(s.bar, st, s.stall ? 1u : 0u)) return;
+    if (it + 1 < s.k && !grid_barrier(bar, nbar, st, extra)) return;
   }
 }
 

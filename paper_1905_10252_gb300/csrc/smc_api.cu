@@ -65,9 +65,9 @@ Layout layout_for(int64_t n, int d, int m = 0, bool two_rs = false) {
   p = align_up(p + size_t(n) * sizeof(uint64_t));
   L.tile_src = p;
   p = align_up(p + size_t(L.ntiles + 1) * sizeof(int32_t));
-  // the grid barrier of the fused small-sampler iterations (two words)
+  // the grid barrier of the fused small-sampler iterations (a 64-bit count)
   L.gbar = p;
-  p = align_up(p + 2 * sizeof(uint32_t));
+  p = align_up(p + sizeof(unsigned long long));
   // logistic data: X, y and the BF16 tile images
   const size_t m_pad = size_t(m + kLgRows - 1) / kLgRows * kLgRows;
   L.lg_x = p;
@@ -323,13 +323,13 @@ cudaError_t launch_small_iterations(smc_sampler* h, int32_t k, bool with_cov) {
   s.a = particle_args(h);
   s.q = quant_args(h, 0, nullptr);
   s.r = redist_args(h, 0);
-  s.bar = reinterpret_cast<uint32_t*>(h->ws + h->L.gbar);
+  s.bar = reinterpret_cast<unsigned long long*>(h->ws + h->L.gbar);
   s.k = k;
   s.move_threads = h->threads_p;
   s.d = h->d;
   s.stop_last = with_cov ? 1 : 0;
   s.stall = (h->cfg.flags & SMC_FLAG_TEST_STALL_BARRIER) ? 1 : 0;
-  cudaError_t e = cudaMemsetAsync(s.bar, 0, 2 * sizeof(uint32_t), h->stream);
+  cudaError_t e = cudaMemsetAsync(s.bar, 0, sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess) e = launch_iterate_small(s, h->grid_p, h->stream);
   if (e == cudaSuccess && with_cov)
     e = launch_cov(s.a, nullptr, reinterpret_cast<double*>(h->ws + h->L.covpart), h->L.cov_blocks, h->stream);

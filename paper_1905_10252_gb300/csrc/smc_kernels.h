@@ -251,14 +251,14 @@ cudaError_t launch_redistribute_commit(const RedistArgs& a, int d, int force_fli
 
 // k iterations of an FP64 sampler of one quantise block and one copy tile
 // (N <= 2048) in one cooperative launch of move_blocks blocks (see
-// k_iterate_small).  bar: two zeroed words (the grid barrier).  stop_last: the
+// k_iterate_small).  bar: the grid barrier's zeroed 64-bit count.  stop_last: the
 // last iteration ends after its scan (its copy and commit follow as separate
 // launches, after the covariance).
 struct SmallIterArgs {
   ParticleArgs a;
   QuantArgs q;
   RedistArgs r;
-  uint32_t* bar;
+  unsigned long long* bar;
   int32_t k;
   int32_t move_threads;  // threads per block that own particles (the separate move launch's block size)
   int32_t d;
