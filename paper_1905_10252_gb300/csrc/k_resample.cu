@@ -657,15 +657,9 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
   // is at most 2 below floor(N C / S), and floor((N C + U)/S) is at most 1
   // above that; exact 128-bit comparisons fix the result.
   const uint64_t Rn = st->recip;  // floor(N 2^64 / S)
-  uint64_t Cx[ITEMS + 1];
-  Cx[0] = C;
-#pragma unroll
-  for (int q = 0; q < ITEMS; ++q) Cx[q + 1] = Cx[q] + W[q];
-  uint64_t offs[ITEMS + 1];
-#pragma unroll
-  for (int q = 0; q <= ITEMS; ++q) {
-    const u128 X = u128(n) * Cx[q] + U;
-    uint64_t qq = __umul64hi(Cx[q], Rn);
+  auto quot = [&](uint64_t c) -> uint64_t {
+    const u128 X = u128(n) * c + U;
+    uint64_t qq = __umul64hi(c, Rn);
     u128 nxt = u128(qq + 1) * S;
 #pragma unroll
     for (int it = 0; it < 3; ++it)
@@ -673,8 +667,42 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
         ++qq;
         nxt += S;
       }
-    offs[q] = qq;
+    return qq;
+  };
+  if (!a.ncopies) {
+    // no copy counts to return (the sampler's own resampling): the items
+    // one after another, each offset computed as it is needed -- the same
+    // integers as below, from a short loop instead of ITEMS + 1 unrolled
+    // quotients (which overflowed the instruction cache)
+    const int64_t i0 = base + int64_t(threadIdx.x) * ITEMS;
+    uint64_t cp = C, op = quot(C);
+#pragma unroll 4
+    for (int q = 0; q < ITEMS; ++q) {
+      const uint64_t cn = cp + buf.w[threadIdx.x * (ITEMS + 1) + q];
+      const uint64_t on = quot(cn);
+      const int64_t i = i0 + q;
+      if (on > op && i < n) {
+        ++nsurv;
+        if (a.write_rs) rs_now(a.runstart, a.runstart_alt, st)[op] = int32_t(i);
+        tile_starts_of_run(a.tile_src, op, on, uint64_t(n), int32_t(i), big);
+      }
+      cp = cn;
+      op = on;
+    }
+    tile_starts_flush(a.tile_src, big);
+    unsigned v = nsurv;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&const_cast<DevState*>(st)->survivors, (unsigned long long)v);
+    return;
   }
+  uint64_t Cx[ITEMS + 1];
+  Cx[0] = C;
+#pragma unroll
+  for (int q = 0; q < ITEMS; ++q) Cx[q + 1] = Cx[q] + W[q];
+  uint64_t offs[ITEMS + 1];
+#pragma unroll
+  for (int q = 0; q <= ITEMS; ++q) offs[q] = quot(Cx[q]);
   const int64_t i0 = base + int64_t(threadIdx.x) * ITEMS;
 #pragma unroll
   for (int q = 0; q < ITEMS; ++q) {
@@ -709,7 +737,7 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
   }
 }
 
-__global__ void __launch_bounds__(kQThreads, 3) k_quant_scan(QuantArgs a) {
+__global__ void __launch_bounds__(kQThreads, 4) k_quant_scan(QuantArgs a) {
   __shared__ ScanSmem sm;
   quant_scan_body(a, blockIdx.x, sm);
 }
