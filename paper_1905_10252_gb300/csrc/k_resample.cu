@@ -1243,7 +1243,7 @@ __global__ void __launch_bounds__(kFinBatchThreads) k_quant_finalize_batch(const
   quant_finalize_body(a, 0);
 }
 
-__global__ void __launch_bounds__(kQThreads) k_quant_scan_batch(const QuantArgs* __restrict__ qa,
+__global__ void __launch_bounds__(kQThreads, 4) k_quant_scan_batch(const QuantArgs* __restrict__ qa,
                                                                const int4* __restrict__ map,
                                                                const int32_t* __restrict__ left) {
   const int4 m = map[blockIdx.x];
