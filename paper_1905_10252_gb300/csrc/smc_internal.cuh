@@ -421,40 +421,59 @@ __device__ __forceinline__ long long warp_max_ll(long long v) {
 // (the same bits whichever kernel runs it).
 // defer: a resampled iteration leaves its rows in place and marks them
 // pending instead of swapping (the next move gathers them).
+// Every field the commit reads is loaded before its first store (one round
+// trip to memory instead of a chain of them; the values are those the
+// original order reads, as no field is read after the commit writes it).
 __device__ __forceinline__ void commit_warp(DevState* st, int d, int force_flip, int recycle, int defer = 0) {
   const int lane = threadIdx.x & 31;
-  const int err = st->err, flag = st->flag;
+  const int err = st->err, flag = st->flag, cur = st->cur;
+  const double lc = st->logc, rmax = st->rc_max, rden = st->rc_den, lse = st->lse;
+  double* const fh = st->fhat_out;
+  smc_iter_stats* const trace = st->trace;
+  const int64_t t = st->t, t0 = st->trace_t0;
+  const unsigned long long surv = st->survivors;
+  constexpr int kLanesD = kMaxD / 32;  // columns per lane
+  double rnum[kLanesD], mc[kLanesD];
+#pragma unroll
+  for (int j = 0; j < kLanesD; ++j) {
+    const int c = lane + 32 * j;
+    rnum[j] = c < d ? st->rc_num[c] : 0.0;
+    mc[j] = c < d ? st->mean[c] : 0.0;
+  }
   const bool pend = defer && flag && !err;
   const bool flip = force_flip || (flag && !err && !defer);
+  double M = 0.0, den = 0.0;
   if (recycle && !err) {
-    const double lc = st->logc, rmax = st->rc_max;
-    const double M = fmax(rmax, lc);
+    M = fmax(rmax, lc);
     const double sc = (rmax == -INFINITY) ? 0.0 : exp(__dsub_rn(rmax, M));
     const double e = exp(__dsub_rn(lc, M));
-    const double den = __fma_rn(st->rc_den, sc, e);
-    double* fh = st->fhat_out;
-    for (int c = lane; c < d; c += 32) {
-      const double num = __fma_rn(st->rc_num[c], sc, __dmul_rn(e, st->mean[c]));
-      st->rc_num[c] = num;
-      if (fh) fh[c] = __ddiv_rn(num, den);
-    }
-    __syncwarp();  // every lane has read rc_max and rc_den
-    if (lane == 0) {
-      st->rc_den = den;
-      st->rc_max = M;
+    den = __fma_rn(rden, sc, e);
+#pragma unroll
+    for (int j = 0; j < kLanesD; ++j) {
+      const int c = lane + 32 * j;
+      if (c < d) {
+        const double num = __fma_rn(rnum[j], sc, __dmul_rn(e, mc[j]));
+        st->rc_num[c] = num;
+        if (fh) fh[c] = __ddiv_rn(num, den);
+      }
     }
   }
+  __syncwarp();  // every lane has read the state before lane 0 writes it
   if (lane != 0) return;
+  if (recycle && !err) {
+    st->rc_den = den;
+    st->rc_max = M;
+  }
   if (flag && !err) {
-    st->last.survivors = (int64_t)st->survivors;
-    if (st->trace) {
-      const int64_t idx = st->t - st->trace_t0 - 1;
-      if (idx >= 0) st->trace[idx].survivors = (int64_t)st->survivors;
+    st->last.survivors = (int64_t)surv;
+    if (trace) {
+      const int64_t idx = t - t0 - 1;
+      if (idx >= 0) trace[idx].survivors = (int64_t)surv;
     }
   }
-  if (flip) st->cur ^= 1;
+  if (flip) st->cur = cur ^ 1;
   st->pending = pend ? 1 : 0;
-  st->lse_prev = (flip || pend) ? 0.0 : st->lse;
+  st->lse_prev = (flip || pend) ? 0.0 : lse;
   // a resampled iteration leaves every log w at reset_logw
   st->w_uniform = ((flip || pend) && !err) ? 1 : 0;
 }
