@@ -488,6 +488,13 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
   // copy counts, the logarithm of LSE, the division of N_eff), each a long
   // latency chain on this GPU
   if (threadIdx.x >= 32) return;
+  // the state the record needs, loaded before the first store (one round
+  // trip, overlapping the chains below; nothing else writes these fields
+  // while this block finalises)
+  const int err0 = st->err;
+  const int64_t t_now = st->t, trace_t0 = st->trace_t0;
+  const double m = st->m, lse_prev = st->lse_prev;
+  smc_iter_stats* const trace = st->trace;
   uint64_t S = 0;
   u128 sw2 = 0, se = 0;
   for (int w = 0; w < nw; ++w) {
@@ -504,7 +511,7 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
     R = S ? uint64_t((u128(n) << 64) / S) : 0;
   } else if (lane0 == 1) {
     se_d = u128_to_double(se);
-    lse = st->m + log(se_d * 0x1p-62);
+    lse = m + log(se_d * 0x1p-62);
   } else if (lane0 == 2) {
     const double Sd = double(S);
     ess = (S && sw2) ? Sd * Sd / u128_to_double(sw2) : 0.0;
@@ -514,7 +521,7 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
   ess = __shfl_sync(0xffffffffu, ess, 2);
   if (lane0 != 0) return;
   int flag = 0;
-  if (!st->err && S > 0) {
+  if (!err0 && S > 0) {
     if (a.mode == SMC_RESAMPLE_ALWAYS)
       flag = 1;
     else if (a.mode == SMC_RESAMPLE_NEVER)
@@ -524,11 +531,10 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
     else  // N* = N/2
       flag = (u128(S) * S * 2) < u128(n) * sw2;
   }
-  const P4 r = stream_block(a.seed, uint64_t(st->t), kPurposeResample, 0xFFFFFFFFull, 0);
+  const P4 r = stream_block(a.seed, uint64_t(t_now), kPurposeResample, 0xFFFFFFFFull, 0);
   const uint64_t r64 = (uint64_t(r.v[0]) << 32) | r.v[1];
   const uint64_t U = S ? __umul64hi(r64, S) : 0;
   const int L = S ? 64 - __clzll((long long)S) : 1;
-  const double m = st->m;
   st->est_s = se_d * 0x1p-62;
   st->S = S;
   st->U = U;
@@ -541,21 +547,22 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
   st->flag = flag;
   st->lse = lse;
   st->ess = ess;
-  st->logc = lse - st->lse_prev;
+  const double logc = lse - lse_prev;
+  st->logc = logc;
   if (set_lse_prev) st->lse_prev = lse;
   smc_iter_stats rec;
   rec.lse = lse;
-  rec.logc = st->logc;
+  rec.logc = logc;
   rec.ess = ess;
   rec.max_logw = m;
   rec.resampled = flag;
-  rec.t = st->t;
+  rec.t = t_now;
   rec.survivors = 0;
   st->survivors = 0;
   st->last = rec;
-  if (st->trace) {
-    const int64_t idx = st->t - st->trace_t0 - 1;
-    if (idx >= 0) st->trace[idx] = rec;
+  if (trace) {
+    const int64_t idx = t_now - trace_t0 - 1;
+    if (idx >= 0) trace[idx] = rec;
   }
   if (a.stats_out) *a.stats_out = rec;
 }

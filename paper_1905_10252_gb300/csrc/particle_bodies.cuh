@@ -244,6 +244,14 @@ __device__ __forceinline__ void move_reweight_generic_body(const ParticleArgs& a
 __device__ __forceinline__ void max_finalize_body(const double* __restrict__ part, int nb, DevState* st) {
   __shared__ long long shm[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // (thread 0 loads the flags it updates now, overlapping the reduction)
+  int wu = 0, pend = 0, cur = 0, rsw = 0;
+  if (threadIdx.x == 0) {
+    wu = st->w_uniform;
+    pend = st->pending;
+    cur = st->cur;
+    rsw = st->rs_w;
+  }
   long long m = ordered_key(-INFINITY);
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     const long long k = ordered_key(part[2 * b]);
@@ -260,16 +268,16 @@ __device__ __forceinline__ void max_finalize_body(const double* __restrict__ par
     if (!(M > -INFINITY && M < INFINITY)) record_error(st, SMC_ENONFINITE);
     // the move kernel that just ran wrote eq. (7) records iff the weights it
     // started from were uniform; after its reweight they are not
-    st->est_ready = st->w_uniform;
+    st->est_ready = wu;
     st->w_uniform = 0;
     // a move that gathered a deferred resampling's rows wrote them to the
     // other buffer, which is now current; the run starts it read stay set,
     // so the next scan writes the other array (which that move reset if it
     // was dirty) and this one is marked dirty
-    if (st->pending) {
-      st->cur ^= 1;
+    if (pend) {
+      st->cur = cur ^ 1;
       st->pending = 0;
-      st->rs_w ^= 1;
+      st->rs_w = rsw ^ 1;
       st->rs_dirty = 1;
     }
   }
