@@ -478,9 +478,10 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
     for (int w = 0; w < nw; ++w) se_all += (u128(sheh[w]) << 64) | shel[w];
     const double se_all_d = u128_to_double(se_all);
     if (est && !st->err && se_all_d > 0.0 && int(threadIdx.x) < a.d) {
+      double* const mean_out = st->mean_out;  // (loaded before the store below)
       const double mc = sxsum[threadIdx.x] / se_all_d;
       st->mean[threadIdx.x] = mc;
-      if (st->mean_out) st->mean_out[threadIdx.x] = mc;
+      if (mean_out) mean_out[threadIdx.x] = mc;
     }
   }
   // the totals, then three independent chains on three lanes of warp 0 (the
@@ -664,6 +665,9 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
   // is at most 2 below floor(N C / S), and floor((N C + U)/S) is at most 1
   // above that; exact 128-bit comparisons fix the result.
   const uint64_t Rn = st->recip;  // floor(N 2^64 / S)
+  // the run-start array, chosen once (its choice does not change during the
+  // pass; read per store, it was a load after every store)
+  int32_t* const rsa = rs_now(a.runstart, a.runstart_alt, st);
   auto quot = [&](uint64_t c) -> uint64_t {
     const u128 X = u128(n) * c + U;
     uint64_t qq = __umul64hi(c, Rn);
@@ -690,7 +694,7 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
       const int64_t i = i0 + q;
       if (on > op && i < n) {
         ++nsurv;
-        if (a.write_rs) rs_now(a.runstart, a.runstart_alt, st)[op] = int32_t(i);
+        if (a.write_rs) rsa[op] = int32_t(i);
         tile_starts_of_run(a.tile_src, op, on, uint64_t(n), int32_t(i), big);
       }
       cp = cn;
@@ -718,7 +722,7 @@ __device__ __forceinline__ void quant_scan_body(const QuantArgs& a, const int bl
     const int64_t i = i0 + q;
     if (hi > lo && i < n) {
       ++nsurv;
-      if (a.write_rs) rs_now(a.runstart, a.runstart_alt, st)[lo] = int32_t(i);
+      if (a.write_rs) rsa[lo] = int32_t(i);
       // every redistribute tile whose first output row lies in [lo, hi)
       tile_starts_of_run(a.tile_src, lo, hi, uint64_t(n), int32_t(i), big);
     }
