@@ -445,9 +445,21 @@ __device__ __forceinline__ void quant_finalize_body(const QuantArgs& a, const in
           const float* xp = static_cast<const float*>(a.xpart);
           float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
           int64_t j = lt;
-          for (; j + 7 * int64_t(stride) < total_words; j += 8 * int64_t(stride)) {
+          const int64_t s1 = int64_t(stride), s8 = 8 * s1;
+          // four rounds' loads in flight at once, then their additions in
+          // round order (the same sums as one round at a time)
+          for (; j + 3 * s8 + 7 * s1 < total_words; j += 4 * s8) {
+            float tv[32];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] += xp[j + u * int64_t(stride)];
+            for (int r = 0; r < 32; ++r) tv[r] = xp[j + r * s1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int u = 0; u < 8; ++u) v[u] += tv[8 * q + u];
+          }
+          for (; j + 7 * s1 < total_words; j += s8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] += xp[j + u * s1];
           }
           for (; j < total_words; j += stride) v[0] += xp[j];
           part = double(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
