@@ -473,6 +473,9 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
   const bool est_on = EST && a.st->w_uniform;
   const double R = a.st->reset_logw;
   float em = -INFINITY;
+  // (est_on: the maximum of log w from the FP32 differences, see below)
+  int dkey = __float_as_int(-INFINITY) ^ 0x7FFFFFFF;
+  bool dnan = false;
   float eacc[EST ? DMAX : 1];
 #pragma unroll
   for (int c = 0; c < (EST ? DMAX : 1); ++c) eacc[c] = 0.0f;
@@ -636,16 +639,27 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
       // eq. (5): the log-target difference in FP32 (exact when the two
       // values are within a factor of two), one FP64 addition
       const float lpi = -0.5f * qs;
-      const double lw = lwc + double(lpi - lpc);
+      const float dlt = lpi - lpc;
+      const double lw = lwc + double(dlt);
       lpd[i] = lpi;
       logw[i] = lw;
       if constexpr (GATHER) {
         if (rs_clr) rs_clr[i] = -1;
       }
-      mt.add(lw);
+      if (EST && est_on) {
+        // every log w started at R: max lw = R + double(max dlt) (R + double(x)
+        // does not decrease with x), so the maximum is tracked on the FP32
+        // differences with integer-ordered keys -- the same value
+        const int b = __float_as_int(dlt);
+        if (dlt != dlt)
+          dnan = true;
+        else
+          dkey = max(dkey, b >= 0 ? b : (b ^ 0x7FFFFFFF));
+      } else {
+        mt.add(lw);
+      }
       if constexpr (EST) {
         if (est_on) {
-          const float dlt = lpi - lpc;
           float dl = dlt - em;
           if (dl > 16.0f) {  // the lane's reference exceeded by e^16 (always for its first particle)
             const float sc = __expf(-dl);
@@ -678,7 +692,14 @@ __device__ __forceinline__ void move_reweight_body(const ParticleArgs& a, const 
     r = rn;
     j = jn;
   }
-  if (REWEIGHT) block_write_max(mt, a.part + 2 * blk, a.st);
+  if (REWEIGHT) {
+    if (EST && est_on) {
+      const int b = dkey >= 0 ? dkey : (dkey ^ 0x7FFFFFFF);
+      mt.add(R + double(__int_as_float(b)));
+      mt.nan = mt.nan || dnan;
+    }
+    block_write_max(mt, a.part + 2 * blk, a.st);
+  }
 }
 
 // One sampler per launch: the factor's entries are kernel parameters, read by
