@@ -34,7 +34,8 @@
  *   logistic logpi          pinned: b = 0 closed form (-M log 2), scipy Bernoulli log-likelihood
  *                           + normal prior, closed-form gradient by central differences,
  *                           label-flip symmetry
- *   orc_run (logistic)      parity unpinned beyond the logpi pins (no closed-form posterior)
+ *   orc_run (logistic)      pinned: posterior mean and variance against grid quadrature of
+ *                           the posterior density (D = 1, 2), within MC error
  */
 #include <math.h>
 #include <stdint.h>
